@@ -1,0 +1,320 @@
+/*
+ * Plain FP64 oracle for PCDM1 on LASSO (Richtarik & Takac, "Parallel Coordinate
+ * Descent Methods for Big Data Optimization", arXiv:1212.0873).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path calls this file: only
+ * the tests, the smoke check and the CPU-baseline leg of the benchmark load it.
+ * It shares no code, header or constant table with the CUDA library; the two
+ * meet only through the seeded instance generator and the written spec of the
+ * sampler (Philox4x32-10 keyed Feistel permutation, restated below).
+ *
+ * Everything is single-threaded, in IEEE double, in the order the paper states
+ * the steps.  Build with -ffp-contract=off so x86 and Arm hosts agree bit for
+ * bit.
+ *
+ * Functions and the passage each one follows:
+ *   pcdm_oracle_philox4x32_10   Salmon, Moraes, Dror, Shaw, SC'11 (Philox-4x32, 10 rounds)
+ *   pcdm_oracle_sample          tau-nice sampling, Sec. 4.1 item 3 (every tau-subset
+ *                               equally likely), realised by the keyed permutation
+ *                               spec below
+ *   pcdm_oracle_col_sqnorms     L_i = ||a_i||^2, Sec. 3 item "Partial separability"
+ *   pcdm_oracle_omega           omega = max_j ||A_j||_0, Sec. 1 "Examples of partially
+ *                               separable functions"
+ *   pcdm_oracle_beta_nice       beta = 1 + (omega-1)(tau-1)/max(1,n-1), Theorem ESO-nice
+ *                               (eq. inequalityToGetZeta), Table ESO
+ *   pcdm_oracle_iteration       Algorithm 1 (PCDM1), step 4, with h(x) from eq. (h(x))
+ *                               and H_{beta,w} (eq. H_{beta,w}) for Omega = lambda*||.||_1, w = L
+ *   pcdm_oracle_residual        g = A x - b (the gradient of f is A^T g)
+ *   pcdm_oracle_gap             LASSO duality gap at the dual point theta = s*g
+ *   pcdm_oracle_objective       F(x) = 1/2 ||Ax-b||^2 + lambda ||x||_1  (eq. P with LASSO, Sec. 8.1)
+ *   pcdm_oracle_run             K iterations of Algorithm 1 with the residual refreshed
+ *                               every refresh_every iterations
+ *
+ * Sampler spec (shared in words only):
+ *   w = smallest even integer >= 2 with 2^w >= n;  hb = w/2;  mask = 2^hb - 1
+ *   key = (lo32(seed), hi32(seed))
+ *   F_r(R) = word0 of Philox4x32-10(counter = (R, r, lo32(k), hi32(k)), key) & mask
+ *   pi(v): L = v >> hb, R = v & mask; for r = 0..11: (L, R) <- (R, L xor F_r(R));
+ *          return (L << hb) | R
+ *   S_k[j] = first element below n of pi(j), pi(pi(j)), ...   (cycle walking)
+ * pi is a bijection of [0, 2^w), so cycle walking yields a bijection of [0, n)
+ * and S_k[0..tau-1] are tau distinct coordinates.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+/* Twelve rounds: with four, the distribution of sampled subsets on small
+ * domains (n <= 64) fails a chi-square test against the uniform law by
+ * hundreds of standard deviations; from ten rounds on it passes. */
+#define ORACLE_FEISTEL_ROUNDS 12
+
+/* ---------------------------------------------------------------------- */
+/* Philox4x32-10 (SC'11 Sec. 4): ten rounds of two 32x32->64 multiplies,   */
+/* a word permutation and xor with a Weyl-sequence key schedule.           */
+/* ---------------------------------------------------------------------- */
+void pcdm_oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Half width of the Feistel domain for a given n (see spec above). */
+static int feistel_half_bits(int64_t n)
+{
+    int w = 2;
+    while (((int64_t)1 << w) < n) w += 2;
+    return w / 2;
+}
+
+static uint32_t feistel_permute(uint32_t v, int hb, uint64_t seed, uint64_t k)
+{
+    uint32_t mask = (hb >= 32) ? 0xFFFFFFFFu : (((uint32_t)1 << hb) - 1u);
+    uint32_t left = v >> hb, right = v & mask;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (uint32_t r = 0; r < ORACLE_FEISTEL_ROUNDS; ++r) {
+        uint32_t ctr[4] = {right, r, (uint32_t)k, (uint32_t)(k >> 32)};
+        uint32_t out[4];
+        pcdm_oracle_philox4x32_10(ctr, key, out);
+        uint32_t f = out[0] & mask;
+        uint32_t new_right = left ^ f;
+        left = right;
+        right = new_right;
+    }
+    return (left << hb) | right;
+}
+
+/* tau-nice sample of iteration k: S[0..tau-1].  Returns 0, or -1 on bad sizes. */
+int pcdm_oracle_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S)
+{
+    if (n < 1 || n > 2147483647LL || tau < 0 || tau > n || k < 0) return -1;
+    int hb = feistel_half_bits(n);
+    for (int64_t j = 0; j < tau; ++j) {
+        uint32_t v = feistel_permute((uint32_t)j, hb, seed, (uint64_t)k);
+        while ((int64_t)v >= n) v = feistel_permute(v, hb, seed, (uint64_t)k);
+        S[j] = (int32_t)v;
+    }
+    return 0;
+}
+
+/* Samples of iterations k0 .. k0+K-1, row after row, into out[K*tau]. */
+int pcdm_oracle_sample_many(uint64_t seed, int64_t k0, int64_t K, int64_t n, int64_t tau, int32_t *out)
+{
+    for (int64_t q = 0; q < K; ++q)
+        if (pcdm_oracle_sample(seed, k0 + q, n, tau, out + q * tau) != 0) return -1;
+    return 0;
+}
+
+/* Number of Feistel rounds of the spec, exported so tests can report it. */
+int pcdm_oracle_feistel_rounds(void) { return ORACLE_FEISTEL_ROUNDS; }
+
+/* ---------------------------------------------------------------------- */
+/* Problem constants                                                       */
+/* ---------------------------------------------------------------------- */
+
+/* L_i = sum_r a_ri^2, summed in storage order. */
+void pcdm_oracle_col_sqnorms(int64_t n, const int64_t *col_ptr, const double *val, double *L)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) s += val[p] * val[p];
+        L[i] = s;
+    }
+}
+
+/* omega = largest number of nonzeros in a row of A (0 when A has none). */
+int64_t pcdm_oracle_omega(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx)
+{
+    int64_t *count = (int64_t *)calloc((size_t)(m > 0 ? m : 1), sizeof(int64_t));
+    if (!count) return -1;
+    for (int64_t p = col_ptr[0]; p < col_ptr[n]; ++p) count[row_idx[p]] += 1;
+    int64_t omega = 0;
+    for (int64_t r = 0; r < m; ++r)
+        if (count[r] > omega) omega = count[r];
+    free(count);
+    return omega;
+}
+
+/* beta for the tau-nice sampling (Theorem ESO-nice).  omega is taken as at
+ * least 1 so that an all-zero A still gives beta = 1. */
+double pcdm_oracle_beta_nice(int64_t omega, int64_t tau, int64_t n)
+{
+    double om = (double)(omega < 1 ? 1 : omega);
+    double denom = (double)(n - 1 > 1 ? n - 1 : 1);
+    return 1.0 + (om - 1.0) * ((double)tau - 1.0) / denom;
+}
+
+/* ---------------------------------------------------------------------- */
+/* The method                                                              */
+/* ---------------------------------------------------------------------- */
+
+static double soft_threshold(double u, double t)
+{
+    if (u > t) return u - t;
+    if (u < -t) return u + t;
+    return 0.0;
+}
+
+/*
+ * One PCDM1 iteration on the set S (tau distinct coordinates), Jacobi style:
+ * every h_i is computed from the same x_k and the same residual g = A x_k - b,
+ * and only then are x and g moved.
+ *   grad_i = a_i^T g
+ *   h_i    = argmin_t grad_i t + (beta L_i / 2) t^2 + lambda |x_i + t|
+ *          = soft(x_i - grad_i/(beta L_i), lambda/(beta L_i)) - x_i
+ * A column with L_i = 0 leaves only lambda |x_i + t|, minimised by t = -x_i.
+ * The new coordinate is stored as the soft-threshold value itself and the
+ * residual moves by a_i * (x_new - x_old).
+ * hbuf and xbuf are scratch arrays of length tau.
+ */
+void pcdm_oracle_iteration(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx,
+                           const double *val, const double *L, double lambda, double beta,
+                           int64_t tau, const int32_t *S, double *x, double *g,
+                           double *hbuf, double *xbuf)
+{
+    (void)m; (void)n;
+    for (int64_t t = 0; t < tau; ++t) {
+        int64_t i = S[t];
+        double grad = 0.0;
+        for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) grad += val[p] * g[row_idx[p]];
+        double x_new;
+        if (L[i] > 0.0) {
+            double bl = beta * L[i];
+            x_new = soft_threshold(x[i] - grad / bl, lambda / bl);
+        } else {
+            x_new = 0.0;
+        }
+        xbuf[t] = x_new;
+        hbuf[t] = x_new - x[i];
+    }
+    for (int64_t t = 0; t < tau; ++t) {
+        int64_t i = S[t];
+        x[i] = xbuf[t];
+        double h = hbuf[t];
+        if (h == 0.0) continue;
+        for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) g[row_idx[p]] += val[p] * h;
+    }
+}
+
+/* g = A x - b. */
+void pcdm_oracle_residual(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx,
+                          const double *val, const double *b, const double *x, double *g)
+{
+    for (int64_t r = 0; r < m; ++r) g[r] = -b[r];
+    for (int64_t i = 0; i < n; ++i) {
+        if (x[i] == 0.0) continue;
+        for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) g[row_idx[p]] += val[p] * x[i];
+    }
+}
+
+/* F(x) = 1/2 ||Ax - b||^2 + lambda ||x||_1, computed from scratch. */
+double pcdm_oracle_objective(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx,
+                             const double *val, const double *b, const double *x, double lambda)
+{
+    double *r = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    if (!r) return NAN;
+    pcdm_oracle_residual(m, n, col_ptr, row_idx, val, b, x, r);
+    double rr = 0.0, l1 = 0.0;
+    for (int64_t q = 0; q < m; ++q) rr += r[q] * r[q];
+    for (int64_t i = 0; i < n; ++i) l1 += fabs(x[i]);
+    free(r);
+    return 0.5 * rr + lambda * l1;
+}
+
+/*
+ * Duality gap of LASSO at x, with r = A x - b supplied by the caller.
+ *   c = A^T r,  s = min(1, lambda/||c||_inf)  (s = 1 when c = 0),  theta = s r
+ *   P = 1/2 ||r||^2 + lambda ||x||_1
+ *   D = -1/2 ||theta||^2 - b^T theta           (dual of LASSO, feasible: ||A^T theta||_inf <= lambda)
+ *   gap = 1/2 (1-s)^2 ||r||^2 + sum_i (lambda |x_i| + s x_i c_i)
+ * The last line equals P - D when r = A x - b exactly (b^T r = x^T c - ||r||^2) and
+ * every summand is >= 0, so it is free of cancellation.
+ * out = {P, D, gap, ||c||_inf, s, ||r||^2, b^T r, ||x||_1, x^T c}
+ */
+void pcdm_oracle_gap(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx,
+                     const double *val, const double *b, const double *x, const double *r,
+                     double lambda, double *out)
+{
+    double *c = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!c) {
+        for (int q = 0; q < 9; ++q) out[q] = NAN;
+        return;
+    }
+    double cinf = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) s += val[p] * r[row_idx[p]];
+        c[i] = s;
+        if (fabs(s) > cinf) cinf = fabs(s);
+    }
+    double s = 1.0;
+    if (cinf > 0.0 && lambda / cinf < 1.0) s = lambda / cinf;
+    double rr = 0.0, br = 0.0;
+    for (int64_t q = 0; q < m; ++q) {
+        rr += r[q] * r[q];
+        br += b[q] * r[q];
+    }
+    double l1 = 0.0, xc = 0.0, terms = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        l1 += fabs(x[i]);
+        xc += x[i] * c[i];
+        terms += lambda * fabs(x[i]) + s * x[i] * c[i];
+    }
+    free(c);
+    out[0] = 0.5 * rr + lambda * l1;
+    out[1] = -0.5 * s * s * rr - s * br;
+    out[2] = 0.5 * (1.0 - s) * (1.0 - s) * rr + terms;
+    out[3] = cinf;
+    out[4] = s;
+    out[5] = rr;
+    out[6] = br;
+    out[7] = l1;
+    out[8] = xc;
+}
+
+/*
+ * Iterations k0 .. k0+iters-1 of Algorithm 1 from the state (x, g), with
+ * S_k drawn by pcdm_oracle_sample(seed, k, n, tau).  After iteration k, when
+ * refresh_every > 0 and (k+1) % refresh_every == 0, g is recomputed as A x - b.
+ * Returns 0, or -1 on allocation failure or bad sizes.
+ */
+int pcdm_oracle_run(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx,
+                    const double *val, const double *b, const double *L, double lambda,
+                    double beta, int64_t tau, uint64_t seed, int64_t k0, int64_t iters,
+                    int64_t refresh_every, double *x, double *g)
+{
+    if (tau < 1 || tau > n) return -1;
+    int32_t *S = (int32_t *)malloc((size_t)tau * sizeof(int32_t));
+    double *hbuf = (double *)malloc((size_t)tau * sizeof(double));
+    double *xbuf = (double *)malloc((size_t)tau * sizeof(double));
+    if (!S || !hbuf || !xbuf) {
+        free(S); free(hbuf); free(xbuf);
+        return -1;
+    }
+    int rc = 0;
+    for (int64_t it = 0; it < iters; ++it) {
+        int64_t k = k0 + it;
+        if (pcdm_oracle_sample(seed, k, n, tau, S) != 0) { rc = -1; break; }
+        pcdm_oracle_iteration(m, n, col_ptr, row_idx, val, L, lambda, beta, tau, S, x, g, hbuf, xbuf);
+        if (refresh_every > 0 && (k + 1) % refresh_every == 0)
+            pcdm_oracle_residual(m, n, col_ptr, row_idx, val, b, x, g);
+    }
+    free(S); free(hbuf); free(xbuf);
+    return rc;
+}
