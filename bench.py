@@ -1,0 +1,390 @@
+"""Benchmark: PCDM1 (tau-nice, LASSO) solved to a relative duality gap on one GB300 per rank.
+
+One step = one complete solve of the scale workload from x = 0:
+  reset (x = 0, g = -b), then Algorithm 1 iterations in chunks of one epoch
+  (ceil(n / tau) iterations, one persistent kernel launch each), each chunk
+  followed by an FP64 residual refresh and an FP64 duality-gap check, until
+  gap / primal <= tol.
+The default workload is the square scale instance: m = n = 4e6, every row with
+exactly omega = 16 nonzeros at uniform columns (nnz = 6.4e7), N(0,1) values,
+x* 1%-dense +-U[1,2], b = A x* + N(0, 1e-4), lambda = 0.05 ||A^T b||_inf,
+tau = 65536, FP64 values and iterates, tolerance 1e-6.
+
+value     coordinate updates per second over the timed steps (inputs resident in HBM)
+e2e       the same metric through the public API from pinned host buffers: create
+          (host-to-device copy of A and b, validation, L and omega), solve, read x back
+roofline  the fused iteration kernel: algorithmic bytes per launch / CUDA-event time
+cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same solve
+
+--impl reference times the oracle itself (one bounded sample of iterations per step).
+Under torchrun every rank solves its own replica (no collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coord updates/s & HBM GB/s vs peak; time to rel. duality gap 1e-6, plain vs batched"
+UNIT = "coord updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["pcdm", "reference"], default="pcdm")
+    p.add_argument("--n", type=int, default=4_000_000)
+    p.add_argument("--omega", type=int, default=16)
+    p.add_argument("--tau", type=int, default=65536)
+    p.add_argument("--dtype", choices=["f64", "f32", "bf16"], default="f64")
+    p.add_argument("--tol", type=float, default=1e-6)
+    p.add_argument("--check-every", type=int, default=0)
+    p.add_argument("--refresh-every", type=int, default=-1, help="-1: 0 for f64, 64 otherwise")
+    p.add_argument("--lanes", type=int, default=0)
+    p.add_argument("--unfused", action="store_true")
+    p.add_argument("--max-iters", type=int, default=200_000)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    p.add_argument("--quiet", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(local_units, local_seconds, world):
+    """Whole-job throughput: units of all ranks / the slowest rank's time."""
+    if world == 1:
+        return local_units / local_seconds, local_seconds, local_units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if (dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item()), float(u.item())
+
+
+# ----------------------------------------------------------------------------- helpers
+def workload_name(a):
+    return ("square scale LASSO: m=n=%d, omega=%d per row (nnz=%d), tau=%d, %s values, solve from x=0 "
+            "to rel. duality gap %g" % (a.n, a.omega, a.n * a.omega, a.tau, a.dtype, a.tol))
+
+
+def make_instance(a):
+    from paper_1212_0873_gb300 import instances
+    return instances.row_omega_instance(a.n, a.n, a.omega, density=0.01, noise=0.01, lam_frac=0.05,
+                                        val_dtype=a.dtype, seed=1002)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1212_0873_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_update(a):
+    """DRAM bytes per coordinate update of the fused kernel from the committed ncu
+    summary, when it was taken on the current kernel sources and this workload."""
+    path = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("src_hash") != kernel_source_hash():
+        return None
+    key = "%s/omega%d/tau%d" % (a.dtype, a.omega, a.tau)
+    ent = d.get("workloads", {}).get(key)
+    return None if ent is None else float(ent["dram_bytes_per_update"])
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (never changes any setting)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.file = None
+        self.gpu = gpu_index
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- the oracle arm
+def oracle_sample(inst, tau, seconds, max_iters):
+    """Time the FP64 oracle on the first iterations of the same solve (single thread)."""
+    import oracle
+    st = oracle.State(oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64), inst.b, inst.lam)
+    done, t_used = 0, 0.0
+    chunk = 1
+    while t_used < seconds and done < max_iters:
+        t0 = time.perf_counter()
+        st.run(tau, chunk, 0)
+        t_used += time.perf_counter() - t0
+        done += chunk
+        chunk = min(chunk * 2, max_iters - done) if done < max_iters else chunk
+        if chunk <= 0:
+            break
+    return done * tau / t_used, done, t_used
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    inst = make_instance(a)
+    st = oracle.State(oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64), inst.b, inst.lam)
+    iters_per_step = 2
+    for _ in range(a.warmup):
+        st.run(a.tau, iters_per_step, 0)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        st.run(a.tau, iters_per_step, 0)
+    dt = time.perf_counter() - t0
+    value = a.steps * iters_per_step * a.tau / dt
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "m": inst.m, "n": inst.n, "nnz": inst.nnz, "omega": a.omega,
+                   "tau": a.tau, "parallelism": "host, 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d iterations of %d updates per step, continuing one PCDM1 run from x=0"
+                                   % (iters_per_step, a.tau)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- the CUDA arm
+def run_pcdm(a, rank, local, world):
+    import torch
+    from paper_1212_0873_gb300 import Lasso
+
+    torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
+    inst = make_instance(a)
+    t_gen = time.perf_counter() - t_gen
+    refresh = a.refresh_every if a.refresh_every >= 0 else (0 if a.dtype == "f64" else 64)
+    kw = dict(fused=not a.unfused, refresh_every=refresh, check_every=a.check_every, lanes_per_col=a.lanes)
+    seed = rank
+    solver = Lasso.from_instance(inst, profile=True, **kw)
+    omega = solver.omega
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def one_solve():
+        solver.reset()
+        return solver.solve(a.tau, seed, a.tol, a.max_iters)
+
+    for _ in range(a.warmup):
+        ok, it, rel = one_solve()
+        if not ok:
+            raise RuntimeError("warm-up solve did not converge (%d iterations, rel gap %g)" % (it, rel))
+    solver.reset_stats()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    step_ms, iters = [], []
+    for _ in range(a.steps):
+        flush.zero_()                                   # L2 flush, outside the timed events
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ok, it, rel = one_solve()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(it)
+        if not ok:
+            raise RuntimeError("solve did not converge")
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    st = solver.stats()
+    local_seconds = sum(step_ms) / 1e3
+    local_updates = st["updates"]
+    value, max_seconds, _ = aggregate(local_updates, local_seconds, world)
+
+    # roofline of the fused iteration kernel
+    sv, sx = st["val_bytes"], st["xg_bytes"]
+    sidx, sL = 4, sx
+    alg_bytes = (st["gathered_nnz"] * (sv + sidx + sx) + st["updates"] * (2 * sx + sL + 8)
+                 + st["scattered_nnz"] * (sv + sidx + 2 * sx))
+    launches = max(st["iter_launches"], 1)
+    avg_launch_s = st["iter_kernel_ms"] / launches / 1e3
+    achieved = alg_bytes / launches / avg_launch_s / 1e9 if avg_launch_s > 0 else None
+    peak, peak_kind = measured_peaks()
+    tpu = traffic_per_update(a)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (tpu * st["updates"] / launches) if tpu is not None else None,
+                "kernel": "k_fused (persistent PCDM1 iterations)", "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes / launches, "avg_launch_ms": avg_launch_s * 1e3,
+                "launches": st["iter_launches"]}
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not a.no_e2e:
+        pin = {}
+        for name in ("col_ptr", "row_idx", "val", "b"):
+            arr = getattr(inst, name)
+            t = torch.empty(arr.shape, dtype=getattr(torch, {"float64": "float64", "float32": "float32",
+                                                              "int64": "int64", "int32": "int32",
+                                                              "uint16": "int16"}[str(arr.dtype)]),
+                            pin_memory=True)
+            t.numpy().view(arr.dtype)[...] = arr
+            pin[name] = t.numpy().view(arr.dtype)
+        h2d = sum(v.nbytes for v in pin.values())
+        e2e_s, e2e_updates, d2h = [], 0, 0
+        for q in range(a.warmup + a.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = Lasso(inst.m, inst.n, pin["col_ptr"], pin["row_idx"], pin["val"], pin["b"], inst.lam, **kw)
+            ok, it, rel = s2.solve(a.tau, seed, a.tol, a.max_iters)
+            x = s2.x()
+            gaps = s2.stats()["gaps"]
+            s2.close()
+            torch.cuda.synchronize()
+            if q >= a.warmup:
+                e2e_s.append(time.perf_counter() - t0)
+                e2e_updates += it * a.tau
+                d2h = x.nbytes + gaps * 9 * 8
+        e2e_value, _, _ = aggregate(e2e_updates, sum(e2e_s), world)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * sum(e2e_s) / len(e2e_s)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, done, used = oracle_sample(inst, a.tau, a.cpu_seconds, max(1, (a.n + a.tau - 1) // a.tau))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d iterations (tau=%d, %d updates) of the same solve from x=0, single-threaded "
+                         "FP64 oracle, %.1f s" % (done, a.tau, done * a.tau, used)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": max_seconds / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
+            "config": {"workload": workload_name(a), "m": inst.m, "n": inst.n, "nnz": inst.nnz, "omega": omega,
+                       "tau": a.tau, "tol": a.tol, "lambda": inst.lam, "fused": not a.unfused,
+                       "refresh_every": refresh, "check_every": a.check_every or math.ceil(a.n / a.tau),
+                       "iters_per_solve": iters[-1], "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "256 MB buffer written between timed steps (outside the events); A is %.2f GB"
+                             % ((inst.col_ptr.nbytes + inst.row_idx.nbytes + inst.val.nbytes) / 1e9)},
+            "time_to_gap_s": max_seconds / a.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": st["kernel_launches"],
+            "clocks": clk,
+            "batched": None,
+            "extras": {"nonzero_update_frac": st["nonzero_updates"] / max(st["updates"], 1),
+                       "mean_col_nnz_gathered": st["gathered_nnz"] / max(st["updates"], 1),
+                       "us_per_iteration_kernel": 1e3 * st["iter_kernel_ms"] / max(st["iterations"], 1),
+                       "gap_checks": st["gaps"], "instance_gen_s": t_gen,
+                       "step_ms": [round(v, 3) for v in step_ms]},
+        }
+        print(json.dumps(out), flush=True)
+    solver.close()
+    return 0
+
+
+def main():
+    a = parse()
+    rank, local, world = dist_setup()
+    if a.impl == "reference":
+        rc = run_reference(a, rank, world)
+    else:
+        rc = run_pcdm(a, rank, local, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * pcdm.h -- C ABI of libpcdm, a GB300 (sm_103a) implementation of the parallel
+ * coordinate descent method PCDM1 with tau-nice sampling (Richtarik & Takac,
+ * "Parallel Coordinate Descent Methods for Big Data Optimization",
+ * arXiv:1212.0873, Algorithm 1) specialised to LASSO:
+ *
+ *     minimise F(x) = 1/2 ||A x - b||^2 + lambda ||x||_1,   A sparse, stored by columns
+ *
+ * (eq. (P) with f = 1/2||Ax-b||^2 and Omega = lambda||.||_1; the LASSO instance of Sec. 8.1).
+ *
+ * One iteration k draws a tau-nice set S_k (Sec. 4.1, item 3), computes for every
+ * i in S_k the partial derivative grad_i = a_i^T g against the maintained residual
+ * g = A x - b, takes the step of eq. (h(x)) with w = L, L_i = ||a_i||^2 and
+ * beta = 1 + (omega-1)(tau-1)/max(1,n-1) (Theorem ESO-nice, Table ESO), and then
+ * moves x_i and g for all tau coordinates at once (Jacobi: every step reads x_k).
+ *
+ * Conventions for every entry point:
+ *  - Sizes are int64_t; row and column indices are int32_t (m, n < 2^31).
+ *  - "Device" pointers are CUDA global-memory pointers of the current device;
+ *    "host" pointers are ordinary (pageable or pinned) host memory.
+ *  - All work is enqueued on the stream given at pcdm_create.  Calls that return
+ *    host values (gap, solve, get_* to host, stats) synchronise that stream.
+ *  - Functions return a pcdm_status and never abort the process.  On failure
+ *    pcdm_last_error(handle) describes the cause.  After PCDM_ECUDA or
+ *    PCDM_ETIMEOUT the handle refuses further work (PCDM_ESTATE) until
+ *    pcdm_reset is called.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef PCDM_H
+#define PCDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pcdm_ctx *pcdm_handle;
+
+typedef enum {
+    PCDM_OK = 0,
+    PCDM_EINVAL = 1,    /* an argument or the matrix is invalid; nothing was changed */
+    PCDM_ENOMEM = 2,    /* device memory allocation failed */
+    PCDM_ECUDA = 3,     /* a CUDA call failed */
+    PCDM_ETIMEOUT = 4,  /* a bounded device-side wait (grid barrier) ran out */
+    PCDM_ENOTCONV = 5,  /* pcdm_solve hit max_iters before the tolerance */
+    PCDM_ESTATE = 6     /* the handle is in a failed state, or a call came out of order */
+} pcdm_status;
+
+typedef enum { PCDM_F64 = 0, PCDM_F32 = 1, PCDM_BF16 = 2 } pcdm_dtype;
+
+/*
+ * A in compressed sparse column form (the paper stores A = [a_1 .. a_n] by
+ * columns, Sec. 8.1).  col_ptr has n+1 entries with col_ptr[0] = 0,
+ * col_ptr[n] = nnz and col_ptr non-decreasing; the rows of column i are
+ * row_idx[col_ptr[i] .. col_ptr[i+1]-1], strictly increasing, each in [0, m);
+ * val holds the matching values in val_dtype, all finite.  Empty columns are
+ * allowed.  The library copies everything it needs: the caller keeps ownership.
+ */
+typedef struct {
+    int64_t m, n, nnz;
+    const int64_t *col_ptr;
+    const int32_t *row_idx;
+    const void *val;
+    int32_t val_dtype;    /* pcdm_dtype */
+    int32_t on_device;    /* 1: the three arrays are device pointers, 0: host pointers */
+} pcdm_csc;
+
+/*
+ * Options.  Fill with pcdm_default_opts and change what you need.
+ * Precision pairs (val_dtype, xg_dtype): (F64, F64), (F32, F32), (BF16, F32).
+ * The FP32 forms accumulate gradients in FP32; the residual refresh and the
+ * duality gap are always computed in FP64.
+ */
+typedef struct {
+    int32_t xg_dtype;            /* dtype of x, g and the gradient accumulator: PCDM_F64 or PCDM_F32 */
+    int32_t fused;               /* 1: one persistent cooperative kernel per run of iterations,
+                                    0: two kernels per iteration (gather/prox, scatter)          */
+    int64_t refresh_every;       /* after iteration k with (k+1) % refresh_every == 0, recompute
+                                    g = A x - b in FP64 (0: only when pcdm_gap runs)            */
+    int64_t check_every;         /* pcdm_solve: iterations between duality-gap checks
+                                    (0: one epoch, ceil(n / tau))                               */
+    int64_t lanes_per_col;       /* threads that share one column: 0 (auto), 4, 8, 16 or 32     */
+    uint64_t barrier_timeout_ns; /* bound on every grid-barrier wait of the fused kernel          */
+    int32_t profile;             /* 1: time every iteration-kernel launch with CUDA events        */
+    int32_t reserved;
+} pcdm_opts;
+
+/* Counters since pcdm_create or pcdm_reset_stats. */
+typedef struct {
+    int64_t iterations;        /* PCDM1 iterations run */
+    int64_t updates;           /* coordinate updates (tau per iteration) */
+    int64_t gathered_nnz;      /* nonzeros read by the gradient gathers */
+    int64_t scattered_nnz;     /* nonzeros scattered into g (columns with h_i != 0) */
+    int64_t nonzero_updates;   /* updates with h_i != 0 */
+    int64_t iter_launches;     /* launches of the iteration kernel(s) */
+    double iter_kernel_ms;     /* summed CUDA-event time of those launches (profile = 1), else 0 */
+    int64_t refreshes;         /* FP64 residual refreshes */
+    int64_t gaps;              /* duality-gap evaluations */
+    int64_t val_bytes;         /* bytes of one stored value */
+    int64_t xg_bytes;          /* bytes of one x or g entry */
+    int64_t kernel_launches;   /* every kernel this handle launched (all phases) */
+} pcdm_stats;
+
+/* Default options: xg_dtype F64, fused 1, refresh_every 0, check_every 0,
+ * lanes_per_col 0, barrier_timeout_ns 2e9, profile 0. */
+void pcdm_default_opts(pcdm_opts *opts);
+
+/*
+ * Create a solver for one LASSO instance (eq. (P), Sec. 8.1) and run the set-up:
+ * validation of A, L_i = ||a_i||^2 in FP64, omega = max_r #nonzeros of row r
+ * (Sec. 1, examples of partially separable functions), x = 0 and g = -b.
+ *   A          matrix (see pcdm_csc); copied
+ *   b          right-hand side, m entries of b_dtype (PCDM_F64 or PCDM_F32), host or
+ *              device as A->on_device says; copied and kept in FP64
+ *   lambda     regularisation weight, finite and >= 0
+ *   opts       NULL for defaults
+ *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream)
+ *   out        receives the handle
+ * Errors: EINVAL for a NULL pointer, sizes out of range, a bad dtype pair,
+ * lambda < 0 or not finite, col_ptr not monotone or not ending at nnz, a row
+ * index out of range or not strictly increasing in its column, a non-finite
+ * value in A or b.  ENOMEM, ECUDA.
+ */
+pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, double lambda,
+                        const pcdm_opts *opts, void *cuda_stream, pcdm_handle *out);
+
+/*
+ * Run `iters` iterations of Algorithm 1 (PCDM1) with the tau-nice sampling,
+ * continuing the handle's iteration counter k.  S_k depends only on
+ * (seed, k, n, tau), so step(a) followed by step(b) equals step(a+b).
+ * tau in [1, n]; iters >= 0.  EINVAL otherwise.
+ * The sampler: Philox4x32-10 (Salmon et al., SC'11) keyed by seed drives a
+ * 12-round Feistel permutation pi_k of [0, 2^w) (w the least even width with
+ * 2^w >= n, at least 2), walked back into [0, n); S_k = (pi_k(0) .. pi_k(tau-1)).
+ */
+pcdm_status pcdm_step(pcdm_handle h, int64_t tau, int64_t iters, uint64_t seed);
+
+/* Recompute g = A x - b in FP64 (stored in g's dtype). */
+pcdm_status pcdm_refresh(pcdm_handle h);
+
+/*
+ * Refresh g, then evaluate in FP64 the LASSO duality gap at the dual point
+ * theta = s g, s = min(1, lambda / ||A^T g||_inf):
+ *   primal = 1/2 ||g||^2 + lambda ||x||_1,  dual = -1/2 s^2 ||g||^2 - s b^T g,
+ *   gap = 1/2 (1-s)^2 ||g||^2 + lambda ||x||_1 + s x^T A^T g   (= primal - dual).
+ * Any output pointer may be NULL.  Synchronises the stream.
+ */
+pcdm_status pcdm_gap(pcdm_handle h, double *primal, double *dual, double *gap);
+
+/*
+ * Iterate until gap / primal <= rel_gap_tol: check the gap first, then run
+ * chunks of opts.check_every iterations (one epoch when 0), checking after each.
+ * iters_done and rel_gap (either may be NULL) receive the iterations run and
+ * the last relative gap.  Returns PCDM_ENOTCONV when max_iters ran out first.
+ */
+pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap_tol, int64_t max_iters,
+                       int64_t *iters_done, double *rel_gap);
+
+/* Copy x (n entries of xg_dtype) to host (on_device = 0) or device memory. */
+pcdm_status pcdm_get_x(pcdm_handle h, void *x_out, int32_t on_device);
+
+/* Replace x (n entries of xg_dtype, host or device) and recompute g = A x - b (warm start). */
+pcdm_status pcdm_set_x(pcdm_handle h, const void *x_in, int32_t on_device);
+
+/* Copy the maintained residual g (m entries of xg_dtype) to host or device memory. */
+pcdm_status pcdm_get_residual(pcdm_handle h, void *g_out, int32_t on_device);
+
+/* Copy L (n doubles, L_i = ||a_i||^2) to host or device memory. */
+pcdm_status pcdm_get_L(pcdm_handle h, double *L_out, int32_t on_device);
+
+/* Change lambda (finite, >= 0) for the following iterations; x and g are kept. */
+pcdm_status pcdm_set_lambda(pcdm_handle h, double lambda);
+
+/* omega, the degree of partial separability of f (largest row count of A). */
+pcdm_status pcdm_omega(pcdm_handle h, int64_t *omega);
+
+/* beta = 1 + (omega-1)(tau-1)/max(1, n-1) (Theorem ESO-nice); omega taken as >= 1. */
+pcdm_status pcdm_beta(pcdm_handle h, int64_t tau, double *beta);
+
+/* The iteration counter k (iterations run since create or reset), and its setter
+ * (checkpoint/resume: restore x with pcdm_set_x and k with pcdm_set_iteration). */
+pcdm_status pcdm_get_iteration(pcdm_handle h, int64_t *k);
+pcdm_status pcdm_set_iteration(pcdm_handle h, int64_t k);
+
+/* x = 0, g = -b, k = 0, and clear a failed state.  The counters of pcdm_get_stats
+ * are kept (pcdm_reset_stats clears them). */
+pcdm_status pcdm_reset(pcdm_handle h);
+
+/* Counters (see pcdm_stats); synchronises the stream. */
+pcdm_status pcdm_get_stats(pcdm_handle h, pcdm_stats *out);
+pcdm_status pcdm_reset_stats(pcdm_handle h);
+
+/*
+ * The tau-nice sample of iteration k on its own: S_device[j] = pi_k(j) for
+ * j < tau (see pcdm_step), written to device memory on cuda_stream.
+ * 1 <= n < 2^31, 0 <= tau <= n, k >= 0.  No handle needed.
+ */
+pcdm_status pcdm_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S_device, void *cuda_stream);
+
+/*
+ * Self-test of the bounded grid barrier used by the fused kernel: launches a
+ * small cooperative kernel whose barrier waits for one arrival more than there
+ * are blocks, so every wait must give up after timeout_ns.  Returns PCDM_ETIMEOUT
+ * when the bound worked (the expected outcome), PCDM_OK if the wait was
+ * satisfied (it cannot be), ECUDA on a CUDA error.  The device stays usable.
+ */
+pcdm_status pcdm_selftest_barrier_timeout(uint64_t timeout_ns, void *cuda_stream);
+
+/* Free everything the handle owns.  NULL is ignored. */
+void pcdm_destroy(pcdm_handle h);
+
+/* Last error message of the handle ("" if none); valid until the next call on it.
+ * With h == NULL: the last error of a failed pcdm_create or pcdm_sample on this thread. */
+const char *pcdm_last_error(pcdm_handle h);
+
+/* Static name of a status code. */
+const char *pcdm_status_string(pcdm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCDM_H */

@@ -1,0 +1,222 @@
+"""ctypes binding of libpcdm (include/pcdm.h): the same entry-point names,
+argument marshalling only.  Every call goes into the CUDA library; there is no
+CPU fallback.  If the library has not been built, the first call raises.
+
+Non-OK statuses raise PcdmError, except PCDM_ENOTCONV from pcdm_solve, which is
+reported through its return value.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libpcdm.so")
+
+PCDM_OK, PCDM_EINVAL, PCDM_ENOMEM, PCDM_ECUDA, PCDM_ETIMEOUT, PCDM_ENOTCONV, PCDM_ESTATE = range(7)
+PCDM_F64, PCDM_F32, PCDM_BF16 = 0, 1, 2
+DTYPE_CODES = {"f64": PCDM_F64, "f32": PCDM_F32, "bf16": PCDM_BF16}
+
+_i32, _i64, _u64, _dbl, _ptr = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+
+
+class pcdm_csc(ctypes.Structure):
+    _fields_ = [("m", _i64), ("n", _i64), ("nnz", _i64), ("col_ptr", _ptr), ("row_idx", _ptr), ("val", _ptr),
+                ("val_dtype", _i32), ("on_device", _i32)]
+
+
+class pcdm_opts(ctypes.Structure):
+    _fields_ = [("xg_dtype", _i32), ("fused", _i32), ("refresh_every", _i64), ("check_every", _i64),
+                ("lanes_per_col", _i64), ("barrier_timeout_ns", _u64), ("profile", _i32), ("reserved", _i32)]
+
+
+class pcdm_stats(ctypes.Structure):
+    _fields_ = [("iterations", _i64), ("updates", _i64), ("gathered_nnz", _i64), ("scattered_nnz", _i64),
+                ("nonzero_updates", _i64), ("iter_launches", _i64), ("iter_kernel_ms", _dbl),
+                ("refreshes", _i64), ("gaps", _i64), ("val_bytes", _i64), ("xg_bytes", _i64),
+                ("kernel_launches", _i64)]
+
+
+# Every function the header declares, with (restype, argtypes).
+SIGNATURES = {
+    "pcdm_default_opts": (None, [ctypes.POINTER(pcdm_opts)]),
+    "pcdm_create": (_i32, [ctypes.POINTER(pcdm_csc), _ptr, _i32, _dbl, ctypes.POINTER(pcdm_opts), _ptr,
+                           ctypes.POINTER(_ptr)]),
+    "pcdm_step": (_i32, [_ptr, _i64, _i64, _u64]),
+    "pcdm_refresh": (_i32, [_ptr]),
+    "pcdm_gap": (_i32, [_ptr, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
+    "pcdm_solve": (_i32, [_ptr, _i64, _u64, _dbl, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
+    "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
+    "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
+    "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
+    "pcdm_get_L": (_i32, [_ptr, _ptr, _i32]),
+    "pcdm_set_lambda": (_i32, [_ptr, _dbl]),
+    "pcdm_omega": (_i32, [_ptr, ctypes.POINTER(_i64)]),
+    "pcdm_beta": (_i32, [_ptr, _i64, ctypes.POINTER(_dbl)]),
+    "pcdm_get_iteration": (_i32, [_ptr, ctypes.POINTER(_i64)]),
+    "pcdm_set_iteration": (_i32, [_ptr, _i64]),
+    "pcdm_reset": (_i32, [_ptr]),
+    "pcdm_get_stats": (_i32, [_ptr, ctypes.POINTER(pcdm_stats)]),
+    "pcdm_reset_stats": (_i32, [_ptr]),
+    "pcdm_sample": (_i32, [_u64, _i64, _i64, _i64, _ptr, _ptr]),
+    "pcdm_selftest_barrier_timeout": (_i32, [_u64, _ptr]),
+    "pcdm_destroy": (None, [_ptr]),
+    "pcdm_last_error": (ctypes.c_char_p, [_ptr]),
+    "pcdm_status_string": (ctypes.c_char_p, [_i32]),
+}
+
+_lib = None
+
+
+class PcdmError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = int(status)
+        super().__init__("%s: %s" % (_STATUS_NAMES.get(int(status), str(status)), message))
+
+
+_STATUS_NAMES = {0: "PCDM_OK", 1: "PCDM_EINVAL", 2: "PCDM_ENOMEM", 3: "PCDM_ECUDA", 4: "PCDM_ETIMEOUT",
+                 5: "PCDM_ENOTCONV", 6: "PCDM_ESTATE"}
+
+
+def lib():
+    """The loaded libpcdm; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpcdm.so is not built (%s). Build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`; there is no CPU fallback."
+                               % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != PCDM_OK:
+        msg = lib().pcdm_last_error(handle)
+        raise PcdmError(status, (msg or b"").decode(errors="replace"))
+
+
+def _stream(stream):
+    return ctypes.c_void_p(int(stream) if stream else 0)
+
+
+# ---------------------------------------------------------------------------- entry points
+def pcdm_default_opts():
+    o = pcdm_opts()
+    lib().pcdm_default_opts(ctypes.byref(o))
+    return o
+
+
+def pcdm_create(A, b_ptr, b_dtype, lam, opts=None, stream=0):
+    h = _ptr()
+    st = lib().pcdm_create(ctypes.byref(A), _ptr(b_ptr), int(b_dtype), float(lam),
+                           ctypes.byref(opts) if opts is not None else None, _stream(stream), ctypes.byref(h))
+    _check(st, None)
+    return h
+
+
+def pcdm_step(h, tau, iters, seed):
+    _check(lib().pcdm_step(h, int(tau), int(iters), int(seed) & (2**64 - 1)), h)
+
+
+def pcdm_refresh(h):
+    _check(lib().pcdm_refresh(h), h)
+
+
+def pcdm_gap(h):
+    p, d, g = _dbl(), _dbl(), _dbl()
+    _check(lib().pcdm_gap(h, ctypes.byref(p), ctypes.byref(d), ctypes.byref(g)), h)
+    return p.value, d.value, g.value
+
+
+def pcdm_solve(h, tau, seed, rel_gap_tol, max_iters):
+    """Returns (converged, iters_done, rel_gap)."""
+    it, rel = _i64(), _dbl()
+    st = lib().pcdm_solve(h, int(tau), int(seed) & (2**64 - 1), float(rel_gap_tol), int(max_iters),
+                          ctypes.byref(it), ctypes.byref(rel))
+    if st == PCDM_ENOTCONV:
+        return False, it.value, rel.value
+    _check(st, h)
+    return True, it.value, rel.value
+
+
+def pcdm_get_x(h, ptr, on_device):
+    _check(lib().pcdm_get_x(h, _ptr(ptr), int(on_device)), h)
+
+
+def pcdm_set_x(h, ptr, on_device):
+    _check(lib().pcdm_set_x(h, _ptr(ptr), int(on_device)), h)
+
+
+def pcdm_get_residual(h, ptr, on_device):
+    _check(lib().pcdm_get_residual(h, _ptr(ptr), int(on_device)), h)
+
+
+def pcdm_get_L(h, ptr, on_device):
+    _check(lib().pcdm_get_L(h, _ptr(ptr), int(on_device)), h)
+
+
+def pcdm_set_lambda(h, lam):
+    _check(lib().pcdm_set_lambda(h, float(lam)), h)
+
+
+def pcdm_omega(h):
+    v = _i64()
+    _check(lib().pcdm_omega(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def pcdm_beta(h, tau):
+    v = _dbl()
+    _check(lib().pcdm_beta(h, int(tau), ctypes.byref(v)), h)
+    return v.value
+
+
+def pcdm_get_iteration(h):
+    v = _i64()
+    _check(lib().pcdm_get_iteration(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def pcdm_set_iteration(h, k):
+    _check(lib().pcdm_set_iteration(h, int(k)), h)
+
+
+def pcdm_reset(h):
+    _check(lib().pcdm_reset(h), h)
+
+
+def pcdm_get_stats(h):
+    s = pcdm_stats()
+    _check(lib().pcdm_get_stats(h, ctypes.byref(s)), h)
+    return {name: getattr(s, name) for name, _ in pcdm_stats._fields_}
+
+
+def pcdm_reset_stats(h):
+    _check(lib().pcdm_reset_stats(h), h)
+
+
+def pcdm_sample(seed, k, n, tau, S_device_ptr, stream=0):
+    _check(lib().pcdm_sample(int(seed) & (2**64 - 1), int(k), int(n), int(tau), _ptr(S_device_ptr),
+                             _stream(stream)), None)
+
+
+def pcdm_selftest_barrier_timeout(timeout_ns, stream=0):
+    """Returns the raw status (PCDM_ETIMEOUT is the expected outcome)."""
+    return int(lib().pcdm_selftest_barrier_timeout(int(timeout_ns), _stream(stream)))
+
+
+def pcdm_destroy(h):
+    lib().pcdm_destroy(h)
+
+
+def pcdm_last_error(h=None):
+    msg = lib().pcdm_last_error(h)
+    return (msg or b"").decode(errors="replace")
+
+
+def pcdm_status_string(status):
+    return lib().pcdm_status_string(int(status)).decode()

@@ -1,0 +1,249 @@
+// Type-independent kernels of libpcdm: the standalone tau-nice sampler, input
+// validation, conversions, the row part and the final reduction of the duality
+// gap, and the self-test of the bounded grid barrier.
+#include <cmath>
+
+#include "pcdm_internal.h"
+
+namespace pcdm {
+
+static inline unsigned grid_for(int64_t count, int per_block = 256, int64_t cap = 152 * 64)
+{
+    int64_t b = (count + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return unsigned(b);
+}
+
+__global__ void k_sample(SampleKey key, int64_t tau, int32_t *S)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < tau; j += stride)
+        S[j] = sample_index(uint32_t(j), key);
+}
+
+cudaError_t launch_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S, cudaStream_t st)
+{
+    if (tau <= 0) return cudaSuccess;
+    k_sample<<<grid_for(tau), 256, 0, st>>>(make_sample_key(seed, k, n), tau, S);
+    return cudaGetLastError();
+}
+
+__global__ void k_check_colptr(const int64_t *col_ptr, int64_t n, int64_t nnz, int *flags)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int f = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= n; i += stride) {
+        const int64_t c = col_ptr[i];
+        if (c < 0 || c > nnz) f = FLAG_COLPTR;
+        if (i == 0 && c != 0) f = FLAG_COLPTR;
+        if (i == n && c != nnz) f = FLAG_COLPTR;
+        if (i < n && col_ptr[i + 1] < c) f = FLAG_COLPTR;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+cudaError_t launch_check_colptr(const int64_t *col_ptr, int64_t n, int64_t nnz, int *flags, cudaStream_t st)
+{
+    k_check_colptr<<<grid_for(n + 1), 256, 0, st>>>(col_ptr, n, nnz, flags);
+    return cudaGetLastError();
+}
+
+__global__ void k_check_finite(const double *v, int64_t count, int *flags)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int f = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride)
+        if (!isfinite(v[i])) f = FLAG_B_NONFINITE;
+    if (f) atomicOr(flags, f);
+}
+
+cudaError_t launch_check_finite(const double *v, int64_t count, int *flags, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    k_check_finite<<<grid_for(count), 256, 0, st>>>(v, count, flags);
+    return cudaGetLastError();
+}
+
+__global__ void k_max_int(const int *a, int64_t count, int *out)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int best = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) best = max(best, a[i]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(0xFFFFFFFFu, best, off));
+    if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(out, best);
+}
+
+cudaError_t launch_max_int(const int *a, int64_t count, int *out, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    k_max_int<<<grid_for(count), 256, 0, st>>>(a, count, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_convert_b(const void *b_in, int b_is_f32, int64_t m, double *b_out)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += stride)
+        b_out[i] = b_is_f32 ? double(static_cast<const float *>(b_in)[i]) : static_cast<const double *>(b_in)[i];
+}
+
+cudaError_t launch_convert_b(const void *b_in, int b_is_f32, int64_t m, double *b_out, cudaStream_t st)
+{
+    if (m <= 0) return cudaSuccess;
+    k_convert_b<<<grid_for(m), 256, 0, st>>>(b_in, b_is_f32, m, b_out);
+    return cudaGetLastError();
+}
+
+template <typename XT>
+__global__ void k_neg_store(XT *g, const double *b, int64_t m)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += stride) g[i] = XT(-b[i]);
+}
+
+template <typename XT>
+cudaError_t launch_neg_store(XT *g, const double *b, int64_t m, cudaStream_t st)
+{
+    if (m <= 0) return cudaSuccess;
+    k_neg_store<XT><<<grid_for(m), 256, 0, st>>>(g, b, m);
+    return cudaGetLastError();
+}
+template cudaError_t launch_neg_store<double>(double *, const double *, int64_t, cudaStream_t);
+template cudaError_t launch_neg_store<float>(float *, const double *, int64_t, cudaStream_t);
+
+template <typename XT>
+__global__ void k_store_from_f64(XT *dst, const double *src, int64_t m)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += stride) dst[i] = XT(src[i]);
+}
+
+template <typename XT>
+cudaError_t launch_store_from_f64(XT *dst, const double *src, int64_t m, cudaStream_t st)
+{
+    if (m <= 0) return cudaSuccess;
+    k_store_from_f64<XT><<<grid_for(m), 256, 0, st>>>(dst, src, m);
+    return cudaGetLastError();
+}
+template cudaError_t launch_store_from_f64<double>(double *, const double *, int64_t, cudaStream_t);
+template cudaError_t launch_store_from_f64<float>(float *, const double *, int64_t, cudaStream_t);
+
+cudaError_t launch_f64_to_f32(float *dst, const double *src, int64_t count, cudaStream_t st)
+{
+    return launch_store_from_f64<float>(dst, src, count, st);
+}
+
+// Row part of the gap: block partials of ||r||^2 and b^T r.
+__global__ void __launch_bounds__(kBlock) k_gap_rows(const double *__restrict__ r, const double *__restrict__ b,
+                                                     int64_t m, double *__restrict__ part)
+{
+    const int64_t stride = int64_t(gridDim.x) * kBlock;
+    double rr = 0.0, br = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * kBlock + threadIdx.x; i < m; i += stride) {
+        const double ri = r[i];
+        rr += ri * ri;
+        br += b[i] * ri;
+    }
+    __shared__ double sm[2][kBlock / 32];
+    rr = warp_sum(rr);
+    br = warp_sum(br);
+    if ((threadIdx.x & 31) == 0) {
+        sm[0][threadIdx.x >> 5] = rr;
+        sm[1][threadIdx.x >> 5] = br;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int q = 0; q < kBlock / 32; ++q) {
+            a0 += sm[0][q];
+            a1 += sm[1][q];
+        }
+        part[2 * blockIdx.x + 0] = a0;
+        part[2 * blockIdx.x + 1] = a1;
+    }
+}
+
+cudaError_t launch_gap_rows(const double *r, const double *b, int64_t m, double *part, int blocks, cudaStream_t st)
+{
+    k_gap_rows<<<blocks, kBlock, 0, st>>>(r, b, m, part);
+    return cudaGetLastError();
+}
+
+// Final fixed-order reduction and the gap record (all in FP64):
+//   out = {P, D, gap, ||c||_inf, s, ||r||^2, b^T r, ||x||_1, x^T c}
+//   s = min(1, lambda/||c||_inf) (1 when c = 0), P = ||r||^2/2 + lambda ||x||_1,
+//   D = -s^2 ||r||^2/2 - s b^T r, gap = (1-s)^2 ||r||^2/2 + lambda ||x||_1 + s x^T c.
+__global__ void __launch_bounds__(kFinishBlock) k_gap_finish(const double *pc, int nbc, const double *pr, int nbr,
+                                                             double lambda, double *out)
+{
+    double cmax = 0.0, l1 = 0.0, xc = 0.0, rr = 0.0, br = 0.0;
+    for (int q = threadIdx.x; q < nbc; q += kFinishBlock) {
+        cmax = fmax(cmax, pc[3 * q + 0]);
+        l1 += pc[3 * q + 1];
+        xc += pc[3 * q + 2];
+    }
+    for (int q = threadIdx.x; q < nbr; q += kFinishBlock) {
+        rr += pr[2 * q + 0];
+        br += pr[2 * q + 1];
+    }
+    __shared__ double sm[5][kFinishBlock / 32];
+    cmax = warp_max(cmax);
+    l1 = warp_sum(l1);
+    xc = warp_sum(xc);
+    rr = warp_sum(rr);
+    br = warp_sum(br);
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        sm[0][w] = cmax;
+        sm[1][w] = l1;
+        sm[2][w] = xc;
+        sm[3][w] = rr;
+        sm[4][w] = br;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < kFinishBlock / 32; ++w) {
+            a[0] = fmax(a[0], sm[0][w]);
+            for (int q = 1; q < 5; ++q) a[q] += sm[q][w];
+        }
+        const double cinf = a[0], l1s = a[1], xcs = a[2], rrs = a[3], brs = a[4];
+        double s = 1.0;
+        if (cinf > 0.0 && lambda / cinf < 1.0) s = lambda / cinf;
+        out[0] = 0.5 * rrs + lambda * l1s;
+        out[1] = -0.5 * s * s * rrs - s * brs;
+        out[2] = 0.5 * (1.0 - s) * (1.0 - s) * rrs + (lambda * l1s + s * xcs);
+        out[3] = cinf;
+        out[4] = s;
+        out[5] = rrs;
+        out[6] = brs;
+        out[7] = l1s;
+        out[8] = xcs;
+    }
+}
+
+cudaError_t launch_gap_finish(const double *pc, int nbc, const double *pr, int nbr, double *out, double lambda,
+                              cudaStream_t st)
+{
+    k_gap_finish<<<1, kFinishBlock, 0, st>>>(pc, nbc, pr, nbr, lambda, out);
+    return cudaGetLastError();
+}
+
+// Barrier self-test: the wait target is one arrival more than the grid has, so
+// every block's wait must end by its time budget.
+__global__ void k_barrier_selftest(unsigned long long *bar, int *status, uint64_t timeout_ns)
+{
+    grid_sync(bar, (unsigned long long)gridDim.x + 1ull, status, timeout_ns);
+}
+
+cudaError_t launch_barrier_selftest(unsigned long long *bar, int *status, uint64_t timeout_ns, int blocks,
+                                    cudaStream_t st)
+{
+    void *params[] = {(void *)&bar, (void *)&status, (void *)&timeout_ns};
+    return cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(unsigned(blocks)), dim3(64), params, 0,
+                                       st);
+}
+
+}  // namespace pcdm

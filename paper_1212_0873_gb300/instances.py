@@ -153,17 +153,21 @@ def row_omega_instance(m, n, omega, density=0.01, noise=0.01, lam_frac=0.05, val
     about Poisson(m*omega/n).  Defaults follow the square scale workload:
     x* 1%-dense +-U[1,2], noise standard deviation 1e-2, lambda = 0.05 ||A^T b||_inf."""
     rng = np.random.default_rng(seed)
-    cols = _distinct_rows(rng, m, omega, n).astype(np.int32)      # (m, omega)
-    val_rowmajor = rng.standard_normal(m * omega)
-    flat_cols = cols.reshape(-1)
-    order = np.argsort(flat_cols, kind="stable")                   # row-major input: rows stay ascending
-    counts = np.bincount(flat_cols, minlength=n)
+    cols = _distinct_rows(rng, m, omega, n)                        # (m, omega) distinct columns per row
+    # CSC order = sort by (column, row): pack both into one int64 key and sort in place
+    key = cols.reshape(-1)
+    key <<= 32
+    key |= np.repeat(np.arange(m, dtype=np.int64), omega)
+    del cols
+    key.sort()
+    cols_sorted = key >> 32
+    row_idx = (key & 0xFFFFFFFF).astype(np.int32)
+    del key
+    counts = np.bincount(cols_sorted, minlength=n)
     col_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=col_ptr[1:])
-    row_idx = (order // omega).astype(np.int32)
-    val = val_rowmajor[order]
-    cols_sorted = flat_cols[order].astype(np.int64)
-    del order, val_rowmajor, cols
+    # values are i.i.d. and independent of the pattern: draw them in storage order
+    val = rng.standard_normal(m * omega)
     x_star = _planted(rng, n, int(round(density * n)))
     meta = dict(kind="row_omega", omega=omega, seed=seed, noise=noise, lam_frac=lam_frac)
     return _finish(rng, m, n, col_ptr, row_idx, cols_sorted, val, val_dtype, x_star, noise, lam_frac, meta)

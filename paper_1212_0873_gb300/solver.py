@@ -1,0 +1,178 @@
+"""A LASSO instance resident on the GPU and solved by PCDM1 through libpcdm.
+
+Marshalling only: arrays are numpy (host memory, copied by the library) or
+torch CUDA tensors (device memory, copied device to device); every step of the
+method runs in the library's kernels.
+"""
+import numpy as np
+
+from . import _binding as B
+
+_NP_VAL = {np.dtype(np.float64): "f64", np.dtype(np.float32): "f32", np.dtype(np.uint16): "bf16"}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_tensor(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr_and_device(a):
+    if _is_tensor(a):
+        if not a.is_cuda:
+            raise ValueError("torch tensors must be CUDA tensors (host data goes in as numpy arrays)")
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), 1
+    if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+        raise ValueError("arrays must be C-contiguous numpy arrays or CUDA tensors")
+    return a.ctypes.data, 0
+
+
+def _val_code(val):
+    if _is_tensor(val):
+        torch = _torch()
+        table = {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16"}
+        return table[val.dtype]
+    return _NP_VAL[val.dtype]
+
+
+def current_stream():
+    """The torch current CUDA stream handle (0 if torch has no CUDA)."""
+    try:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class Lasso:
+    """min 1/2 ||A x - b||^2 + lam ||x||_1 with A in CSC form, on one GPU."""
+
+    def __init__(self, m, n, col_ptr, row_idx, val, b, lam, *, xg_dtype=None, fused=True, refresh_every=0,
+                 check_every=0, lanes_per_col=0, profile=False, barrier_timeout_ns=None, stream=None):
+        val_dtype = _val_code(val)
+        if xg_dtype is None:
+            xg_dtype = "f64" if val_dtype == "f64" else "f32"
+        self.m, self.n = int(m), int(n)
+        self.val_dtype, self.xg_dtype = val_dtype, xg_dtype
+        p_cp, d_cp = _ptr_and_device(col_ptr)
+        p_ri, d_ri = _ptr_and_device(row_idx)
+        p_v, d_v = _ptr_and_device(val)
+        p_b, d_b = _ptr_and_device(b)
+        if len({d_cp, d_ri, d_v, d_b}) != 1:
+            raise ValueError("A and b must all be host arrays or all be device tensors")
+        nnz = int(col_ptr[-1]) if not _is_tensor(col_ptr) else int(col_ptr[-1].item())
+        A = B.pcdm_csc(self.m, self.n, nnz, p_cp, p_ri, p_v, B.DTYPE_CODES[val_dtype], d_cp)
+        opts = B.pcdm_default_opts()
+        opts.xg_dtype = B.DTYPE_CODES[xg_dtype]
+        opts.fused = 1 if fused else 0
+        opts.refresh_every = int(refresh_every)
+        opts.check_every = int(check_every)
+        opts.lanes_per_col = int(lanes_per_col)
+        opts.profile = 1 if profile else 0
+        if barrier_timeout_ns is not None:
+            opts.barrier_timeout_ns = int(barrier_timeout_ns)
+        b_dt = B.PCDM_F32 if (str(getattr(b, "dtype", "")) in ("float32", "torch.float32")) else B.PCDM_F64
+        self.stream = current_stream() if stream is None else stream
+        self._h = B.pcdm_create(A, p_b, b_dt, lam, opts, self.stream)
+        self.lam = float(lam)
+
+    @classmethod
+    def from_instance(cls, inst, **kw):
+        return cls(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val, inst.b, inst.lam, **kw)
+
+    # -------------------------------------------------------------- the method
+    def step(self, tau, iters, seed=0):
+        B.pcdm_step(self._h, tau, iters, seed)
+
+    def refresh(self):
+        B.pcdm_refresh(self._h)
+
+    def gap(self):
+        p, d, g = B.pcdm_gap(self._h)
+        return dict(primal=p, dual=d, gap=g, rel_gap=g / max(p, 1e-300))
+
+    def solve(self, tau, seed=0, tol=1e-6, max_iters=10**9):
+        """Returns (converged, iterations, relative gap)."""
+        return B.pcdm_solve(self._h, tau, seed, tol, max_iters)
+
+    # -------------------------------------------------------------- state
+    def _np_xg(self, count):
+        return np.empty(count, dtype=np.float64 if self.xg_dtype == "f64" else np.float32)
+
+    def x(self):
+        out = self._np_xg(self.n)
+        B.pcdm_get_x(self._h, out.ctypes.data, 0)
+        return out
+
+    def x_into(self, tensor):
+        """Copy x into a CUDA tensor of n entries of the iterate dtype."""
+        B.pcdm_get_x(self._h, tensor.data_ptr(), 1)
+        return tensor
+
+    def set_x(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64 if self.xg_dtype == "f64" else np.float32) \
+            if not _is_tensor(x) else x
+        p, d = _ptr_and_device(x)
+        B.pcdm_set_x(self._h, p, d)
+
+    def residual(self):
+        out = self._np_xg(self.m)
+        B.pcdm_get_residual(self._h, out.ctypes.data, 0)
+        return out
+
+    def L(self):
+        out = np.empty(self.n, dtype=np.float64)
+        B.pcdm_get_L(self._h, out.ctypes.data, 0)
+        return out
+
+    @property
+    def omega(self):
+        return B.pcdm_omega(self._h)
+
+    def beta(self, tau):
+        return B.pcdm_beta(self._h, tau)
+
+    @property
+    def iteration(self):
+        return B.pcdm_get_iteration(self._h)
+
+    @iteration.setter
+    def iteration(self, k):
+        B.pcdm_set_iteration(self._h, k)
+
+    def set_lambda(self, lam):
+        B.pcdm_set_lambda(self._h, lam)
+        self.lam = float(lam)
+
+    def reset(self):
+        B.pcdm_reset(self._h)
+
+    def stats(self):
+        return B.pcdm_get_stats(self._h)
+
+    def reset_stats(self):
+        B.pcdm_reset_stats(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.pcdm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

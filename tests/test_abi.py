@@ -1,0 +1,159 @@
+"""The C ABI on the CPU: the library loads, exports every function that
+include/pcdm.h declares, its structs have the layout the binding uses, and the
+argument checks that run before any CUDA call reject bad input.  No GPU needed:
+no call here reaches a kernel."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pcdm.h")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1212_0873_gb300 import build
+    build.build()
+    from paper_1212_0873_gb300 import _binding
+    _binding.lib()
+    return _binding
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcdm_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("pcdm_create", "pcdm_step", "pcdm_gap", "pcdm_solve", "pcdm_get_x", "pcdm_set_x",
+                     "pcdm_set_lambda", "pcdm_omega", "pcdm_destroy", "pcdm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(B):
+    lib = ctypes.CDLL(B.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(_declared_functions()) == set(B.SIGNATURES), "binding and header disagree"
+
+
+def test_struct_layout_matches_header(B):
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "pcdm.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(pcdm_csc), sizeof(pcdm_opts), sizeof(pcdm_stats));
+  printf("%zu %zu %zu\n", offsetof(pcdm_csc, val_dtype), offsetof(pcdm_opts, barrier_timeout_ns),
+         offsetof(pcdm_stats, iter_kernel_ms));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "layout.c")
+        exe = os.path.join(d, "layout")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(v) for v in out]
+    assert sizes[0] == ctypes.sizeof(B.pcdm_csc)
+    assert sizes[1] == ctypes.sizeof(B.pcdm_opts)
+    assert sizes[2] == ctypes.sizeof(B.pcdm_stats)
+    assert sizes[3] == B.pcdm_csc.val_dtype.offset
+    assert sizes[4] == B.pcdm_opts.barrier_timeout_ns.offset
+    assert sizes[5] == B.pcdm_stats.iter_kernel_ms.offset
+
+
+def test_default_opts_and_status_strings(B):
+    o = B.pcdm_default_opts()
+    assert (o.xg_dtype, o.fused, o.refresh_every, o.check_every, o.lanes_per_col, o.profile) == (0, 1, 0, 0, 0, 0)
+    assert o.barrier_timeout_ns == 2_000_000_000
+    for code, name in enumerate(["PCDM_OK", "PCDM_EINVAL", "PCDM_ENOMEM", "PCDM_ECUDA", "PCDM_ETIMEOUT",
+                                 "PCDM_ENOTCONV", "PCDM_ESTATE"]):
+        assert B.pcdm_status_string(code) == name
+
+
+def _csc(B, m=4, n=3, nnz=0, val_dtype=0):
+    import numpy as np
+    col_ptr = np.zeros(n + 1, dtype=np.int64)
+    keep = [col_ptr]
+    A = B.pcdm_csc(m, n, nnz, col_ptr.ctypes.data, None, None, val_dtype, 0)
+    return A, keep
+
+
+@pytest.mark.parametrize("case", ["null_A", "null_b", "m0", "n0", "neg_nnz", "huge_m", "lam_neg", "lam_nan",
+                                  "lam_inf", "pair_f64_f32", "pair_bf16_f64", "bad_bdtype", "bad_lanes",
+                                  "neg_refresh", "null_rows"])
+def test_create_rejects_bad_arguments_before_any_cuda_call(B, case):
+    import numpy as np
+    b = np.zeros(4)
+    A, keep = _csc(B)
+    opts = B.pcdm_default_opts()
+    lam = 0.1
+    bdt = B.PCDM_F64
+    a_arg, b_arg = A, b.ctypes.data
+    if case == "null_A":
+        a_arg = None
+    elif case == "null_b":
+        b_arg = None
+    elif case == "m0":
+        A.m = 0
+    elif case == "n0":
+        A.n = 0
+    elif case == "neg_nnz":
+        A.nnz = -1
+    elif case == "huge_m":
+        A.m = 2**31
+    elif case == "lam_neg":
+        lam = -1.0
+    elif case == "lam_nan":
+        lam = float("nan")
+    elif case == "lam_inf":
+        lam = float("inf")
+    elif case == "pair_f64_f32":
+        opts.xg_dtype = B.PCDM_F32
+    elif case == "pair_bf16_f64":
+        A.val_dtype = B.PCDM_BF16
+    elif case == "bad_bdtype":
+        bdt = B.PCDM_BF16
+    elif case == "bad_lanes":
+        opts.lanes_per_col = 12
+    elif case == "neg_refresh":
+        opts.refresh_every = -1
+    elif case == "null_rows":
+        A.nnz = 5
+    h = ctypes.c_void_p()
+    st = B.lib().pcdm_create(ctypes.byref(a_arg) if a_arg is not None else None, b_arg, bdt, lam,
+                             ctypes.byref(opts), None, ctypes.byref(h))
+    assert st == B.PCDM_EINVAL, (case, st, B.pcdm_last_error(None))
+    assert not h.value
+    assert B.pcdm_last_error(None)
+    del keep
+
+
+def test_calls_on_a_null_handle_are_rejected(B):
+    L = B.lib()
+    assert L.pcdm_step(None, 1, 1, 0) == B.PCDM_EINVAL
+    assert L.pcdm_gap(None, None, None, None) == B.PCDM_EINVAL
+    assert L.pcdm_solve(None, 1, 0, 1e-6, 10, None, None) == B.PCDM_EINVAL
+    assert L.pcdm_refresh(None) == B.PCDM_EINVAL
+    assert L.pcdm_reset(None) == B.PCDM_EINVAL
+    k = ctypes.c_int64()
+    assert L.pcdm_omega(None, ctypes.byref(k)) == B.PCDM_EINVAL
+    L.pcdm_destroy(None)
+
+
+@pytest.mark.parametrize("args", [(0, 0, 0, 1), (0, 0, 5, 6), (0, -1, 5, 1), (0, 0, 2**31, 1), (0, 0, 5, -1)])
+def test_sample_rejects_bad_sizes(B, args):
+    seed, k, n, tau = args
+    assert B.lib().pcdm_sample(seed, k, n, tau, None, None) == B.PCDM_EINVAL
+
+
+def test_selftest_rejects_bad_timeout(B):
+    assert B.lib().pcdm_selftest_barrier_timeout(0, None) == B.PCDM_EINVAL
