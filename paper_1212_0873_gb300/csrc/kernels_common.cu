@@ -15,8 +15,9 @@ static inline unsigned grid_for(int64_t count, int per_block = 256, int64_t cap 
     return unsigned(b);
 }
 
-__global__ void k_sample(SampleKey key, int64_t tau, int32_t *S)
+__global__ void k_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S)
 {
+    const SampleKey key = warp_sample_key(seed, k, n);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < tau; j += stride)
         S[j] = sample_index(uint32_t(j), key);
@@ -25,7 +26,7 @@ __global__ void k_sample(SampleKey key, int64_t tau, int32_t *S)
 cudaError_t launch_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S, cudaStream_t st)
 {
     if (tau <= 0) return cudaSuccess;
-    k_sample<<<grid_for(tau), 256, 0, st>>>(make_sample_key(seed, k, n), tau, S);
+    k_sample<<<grid_for(tau), 256, 0, st>>>(seed, k, n, tau, S);
     return cudaGetLastError();
 }
 
@@ -244,6 +245,113 @@ cudaError_t launch_barrier_selftest(unsigned long long *bar, int *status, uint64
     void *params[] = {(void *)&bar, (void *)&status, (void *)&timeout_ns};
     return cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(unsigned(blocks)), dim3(64), params, 0,
                                        st);
+}
+
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of padded column lengths (set-up of the padded layout).
+// Tiles of kScanTile columns: tile sums, a single-block scan of the tile sums,
+// then a block-local scan of each tile plus its offset.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+int64_t scan_tile_count(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+__device__ __forceinline__ int64_t padded_len(const int64_t *col_ptr, int64_t i, int64_t n, int granule)
+{
+    if (i >= n) return 0;
+    const int64_t c = col_ptr[i + 1] - col_ptr[i];
+    return (c + granule - 1) / granule * granule;
+}
+
+// Block-wide exclusive scan of one int64 per thread; returns the block total in *total.
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *total)
+{
+    __shared__ int64_t warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int64_t o = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+        int64_t ti = t;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t o = __shfl_up_sync(0xFFFFFFFFu, ti, off);
+            if (lane >= off) ti += o;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = ti - t;   // exclusive prefix of warp totals
+        if (lane == 31) *total = ti;
+    }
+    __syncthreads();
+    const int64_t out = warp_tot[w] + incl - v;
+    __syncthreads();
+    return out;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int64_t *col_ptr, int64_t n, int granule,
+                                                             int64_t *tile)
+{
+    const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanPer;
+    int64_t s = 0;
+    for (int q = 0; q < kScanPer; ++q) s += padded_len(col_ptr, base + q, n, granule);
+    __shared__ int64_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) tile[blockIdx.x] = tot;
+}
+
+// Single block: tile[0..ntiles) -> exclusive prefixes, tile[ntiles] = total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile_prefix(int64_t *tile, int64_t ntiles)
+{
+    const int64_t per = (ntiles + kScanThreads - 1) / kScanThreads;
+    const int64_t beg = int64_t(threadIdx.x) * per;
+    const int64_t end = beg + per < ntiles ? beg + per : ntiles;
+    int64_t s = 0;
+    for (int64_t q = beg; q < end; ++q) s += tile[q];
+    __shared__ int64_t tot;
+    int64_t run = block_exclusive_scan(s, &tot);
+    for (int64_t q = beg; q < end; ++q) {
+        const int64_t v = tile[q];
+        tile[q] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0) tile[ntiles] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int64_t *col_ptr, int64_t n, int granule,
+                                                             const int64_t *tile, int64_t ntiles, int64_t *pbeg)
+{
+    const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanPer;
+    int64_t len[kScanPer];
+    int64_t s = 0;
+    for (int q = 0; q < kScanPer; ++q) {
+        len[q] = padded_len(col_ptr, base + q, n, granule);
+        s += len[q];
+    }
+    __shared__ int64_t tot;
+    int64_t run = block_exclusive_scan(s, &tot) + tile[blockIdx.x];
+    for (int q = 0; q < kScanPer; ++q) {
+        if (base + q < n) pbeg[base + q] = run;
+        run += len[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) pbeg[n] = tile[ntiles];
+}
+
+cudaError_t launch_padded_scan(const int64_t *col_ptr, int64_t n, int granule, int64_t *pbeg, int64_t *tile,
+                               cudaStream_t st)
+{
+    const int64_t nt = scan_tile_count(n);
+    if (nt <= 0) return cudaSuccess;
+    k_scan_tiles<<<unsigned(nt), kScanThreads, 0, st>>>(col_ptr, n, granule, tile);
+    k_scan_tile_prefix<<<1, kScanThreads, 0, st>>>(tile, nt);
+    k_scan_apply<<<unsigned(nt), kScanThreads, 0, st>>>(col_ptr, n, granule, tile, nt, pbeg);
+    return cudaGetLastError();
 }
 
 }  // namespace pcdm

@@ -42,14 +42,14 @@ struct pcdm_ctx {
     double lambda = 0.0;
     pcdm_opts opts{};
     int W = 8;
-    int fused_blocks_max = 0;
+    int sms = 0;
 
-    int64_t *col_ptr = nullptr;
-    int32_t *row_idx = nullptr;
-    void *val = nullptr;
+    void *desc = nullptr;         // ColDesc<XT>[n]: padded start, count, 1/L_i
+    int32_t *prow = nullptr;      // padded row indices (P + kSlack)
+    void *pval = nullptr;         // padded values (P + kSlack)
+    int64_t P = 0;                // padded entries
     double *b = nullptr;          // FP64 copy of b
     double *L64 = nullptr;        // L_i in FP64
-    float *L32 = nullptr;         // L_i rounded to FP32 (FP32 iterate forms)
     void *x = nullptr;            // n entries of xg dtype
     void *g = nullptr;            // m entries of xg dtype
     double *g64 = nullptr;        // FP64 residual of the refresh (aliases g in the FP64 form)
@@ -124,7 +124,7 @@ cudaError_t dalloc_bytes(void **p, int64_t bytes)
 
 void free_all(pcdm_handle h)
 {
-    void *ptrs[] = {h->col_ptr, h->row_idx, h->val, h->b, h->L64, h->L32, h->x, h->g,
+    void *ptrs[] = {h->desc, h->prow, h->pval, h->b, h->L64, h->x, h->g,
                     h->S[0], h->S[1], h->h, h->counters, h->bar, h->status, h->gap_part, h->gap_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -137,13 +137,14 @@ void free_all(pcdm_handle h)
     for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
 }
 
+// Lanes per column: enough lanes of kLaneRun entries each to cover a column
+// of average length in one chunk.
 int auto_lanes(int64_t nnz, int64_t n)
 {
     const double mean = n > 0 ? double(nnz) / double(n) : 0.0;
-    if (mean < 6.0) return 4;
-    if (mean < 12.0) return 8;
-    if (mean < 24.0) return 16;
-    return 32;
+    int W = 1;
+    while (W < 32 && double(W * kLaneRun) < mean) W *= 2;
+    return W;
 }
 
 double beta_nice(int64_t omega, int64_t tau, int64_t n)
@@ -216,19 +217,15 @@ template <typename VT, typename XT>
 IterArgs<VT, XT> iter_args(pcdm_handle h, int64_t tau, uint64_t seed)
 {
     IterArgs<VT, XT> a;
-    a.col_ptr = h->col_ptr;
-    a.row_idx = h->row_idx;
-    a.val = static_cast<const VT *>(h->val);
-    if (sizeof(XT) == 8)
-        a.L = reinterpret_cast<const XT *>(h->L64);
-    else
-        a.L = reinterpret_cast<const XT *>(h->L32);
+    a.desc = static_cast<const ColDesc<XT> *>(h->desc);
+    a.prow = h->prow;
+    a.pval = static_cast<const VT *>(h->pval);
     a.x = static_cast<XT *>(h->x);
     a.g = static_cast<XT *>(h->g);
     a.h = static_cast<XT *>(h->h);
     a.S[0] = h->S[0];
     a.S[1] = h->S[1];
-    a.beta = XT(beta_nice(h->omega, tau, h->n));
+    a.inv_beta = XT(1.0 / beta_nice(h->omega, tau, h->n));
     a.lambda = XT(h->lambda);
     a.n = h->n;
     a.tau = tau;
@@ -238,6 +235,50 @@ IterArgs<VT, XT> iter_args(pcdm_handle h, int64_t tau, uint64_t seed)
     a.status = h->status;
     a.timeout_ns = h->opts.barrier_timeout_ns ? h->opts.barrier_timeout_ns : kDefaultTimeoutNs;
     return a;
+}
+
+// Launch shape of the fused kernel for tau: one group of W lanes per sampled
+// column when the grid can hold them (spread over all SMs, one block each),
+// otherwise full blocks at the co-residency limit.
+template <typename VT, typename XT>
+pcdm_status fused_shape(pcdm_handle h, int64_t tau, FusedShape *sh)
+{
+    sh->W = h->W;
+    const int64_t need = tau * h->W;
+    int64_t blocks = (need + 63) / 64;
+    if (blocks > h->sms) blocks = h->sms;
+    if (blocks < 1) blocks = 1;
+    int64_t threads = (need + blocks - 1) / blocks;
+    threads = (threads + 31) / 32 * 32;
+    if (threads > fused_max_block(h->W)) {
+        threads = fused_max_block(h->W);
+        blocks = (need + threads - 1) / threads;
+    }
+    const int cap = Kernels<VT, XT>::fused_max_blocks(h->W, int(threads));
+    if (cap <= 0) return set_err(h, PCDM_ECUDA, "cooperative occupancy query failed");
+    if (blocks > cap) blocks = cap;
+    sh->blocks = int(blocks);
+    sh->threads = int(threads);
+    return PCDM_OK;
+}
+
+// Shape of the pipelined kernel for tau, if it applies: one lane per column,
+// every position owned by one thread of a co-resident grid.
+template <typename VT, typename XT>
+bool pipe_shape(pcdm_handle h, int64_t tau, FusedShape *sh)
+{
+    if (h->W != 1) return false;
+    int64_t threads = (tau + h->sms - 1) / h->sms;
+    threads = (threads + 31) / 32 * 32;
+    if (threads < 32) threads = 32;
+    if (threads > kPipeMaxBlock) return false;
+    const int64_t blocks = (tau + threads - 1) / threads;
+    const int cap = Kernels<VT, XT>::pipe_max_blocks(int(threads));
+    if (cap <= 0 || blocks > cap) return false;
+    sh->W = 1;
+    sh->blocks = int(blocks);
+    sh->threads = int(threads);
+    return true;
 }
 
 // Run `iters` iterations starting at h->k with S_k already drawn.
@@ -252,14 +293,15 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         CK(h, cudaEventRecord(e0, h->stream));
     }
     if (h->opts.fused) {
-        if (h->fused_blocks_max <= 0) {
-            h->fused_blocks_max = Kernels<VT, XT>::fused_max_blocks(h->W);
-            if (h->fused_blocks_max <= 0) return set_err(h, PCDM_ECUDA, "cooperative occupancy query failed");
-        }
-        const int64_t want = (tau * h->W + kBlock - 1) / kBlock;
-        const int blocks = int(want < h->fused_blocks_max ? want : h->fused_blocks_max);
+        FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
-        CK(h, Kernels<VT, XT>::fused(a, h->W, h->k, iters, blocks, h->stream));
+        if (pipe_shape<VT, XT>(h, tau, &sh)) {
+            CK(h, Kernels<VT, XT>::fused_pipe(a, sh, h->k, iters, h->stream));
+        } else {
+            pcdm_status s = fused_shape<VT, XT>(h, tau, &sh);
+            if (s != PCDM_OK) return s;
+            CK(h, Kernels<VT, XT>::fused(a, sh, h->k, iters, h->stream));
+        }
         h->st_launches += 1;
         h->st_kernels += 1;
     } else {
@@ -290,8 +332,9 @@ pcdm_status refresh_t(pcdm_handle h)
 {
     double *target = h->g64;
     CK(h, launch_neg_store<double>(target, h->b, h->m, h->stream));
-    CK(h, Kernels<VT, XT>::refresh_cols(h->col_ptr, h->row_idx, static_cast<const VT *>(h->val),
-                                        static_cast<const XT *>(h->x), h->n, target, h->W, h->stream));
+    CK(h, Kernels<VT, XT>::refresh_cols(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
+                                        static_cast<const VT *>(h->pval), static_cast<const XT *>(h->x), h->n,
+                                        target, h->W, h->stream));
     if (sizeof(XT) == 4) CK(h, launch_store_from_f64<float>(static_cast<float *>(h->g), target, h->m, h->stream));
     h->st_refreshes += 1;
     h->st_kernels += sizeof(XT) == 4 ? 3 : 2;
@@ -305,8 +348,9 @@ pcdm_status gap_t(pcdm_handle h)
     if (s != PCDM_OK) return s;
     double *part_c = h->gap_part;
     double *part_r = h->gap_part + 3 * h->gap_blocks;
-    CK(h, Kernels<VT, XT>::gap_cols(h->col_ptr, h->row_idx, static_cast<const VT *>(h->val), h->g64,
-                                    static_cast<const XT *>(h->x), h->n, part_c, h->gap_blocks, h->W, h->stream));
+    CK(h, Kernels<VT, XT>::gap_cols(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
+                                    static_cast<const VT *>(h->pval), h->g64, static_cast<const XT *>(h->x), h->n,
+                                    part_c, h->gap_blocks, h->W, h->stream));
     CK(h, launch_gap_rows(h->g64, h->b, h->m, part_r, h->gap_row_blocks, h->stream));
     CK(h, launch_gap_finish(part_c, h->gap_blocks, part_r, h->gap_row_blocks, h->gap_out, h->lambda, h->stream));
     CK(h, cudaMemcpyAsync(h->host_buf, h->gap_out, 9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -451,21 +495,16 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
 
     CKC(cudaGetDevice(&h->device));
     const int64_t vb = dtype_bytes(h->val_dtype), xb = dtype_bytes(h->xg_dtype);
-    int sms = 0;
-    CKC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    CKC(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
     {
         int64_t gb = (h->n * h->W + kBlock - 1) / kBlock;
-        const int64_t cap = int64_t(sms) * 8;
+        const int64_t cap = int64_t(h->sms) * 8;
         h->gap_blocks = int(gb < 1 ? 1 : (gb > cap ? cap : gb));
         int64_t rb = (h->m + kBlock - 1) / kBlock;
         h->gap_row_blocks = int(rb < 1 ? 1 : (rb > cap ? cap : rb));
     }
-    CKC(dalloc(&h->col_ptr, h->n + 1));
-    CKC(dalloc(&h->row_idx, h->nnz));
-    CKC(dalloc_bytes(&h->val, h->nnz * vb));
     CKC(dalloc(&h->b, h->m));
     CKC(dalloc(&h->L64, h->n));
-    if (h->xg_dtype == PCDM_F32) CKC(dalloc(&h->L32, h->n));
     CKC(dalloc_bytes(&h->x, h->n * xb));
     CKC(dalloc_bytes(&h->g, h->m * xb));
     if (h->xg_dtype == PCDM_F64)
@@ -479,20 +518,35 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     CKC(dalloc(&h->gap_out, 9));
     CKC(cudaMallocHost(reinterpret_cast<void **>(&h->host_buf), 16 * sizeof(double)));
 
-    const cudaMemcpyKind kin = copy_kind(A->on_device, 1);
+    // Stage the caller's CSC on the device (freed once the padded layout exists).
+    struct Staging {
+        int64_t *col_ptr = nullptr, *pbeg = nullptr, *tile = nullptr;
+        int32_t *row_idx = nullptr;
+        void *val = nullptr;
+        int *rowcnt = nullptr;
+        ~Staging()
+        {
+            void *p[] = {col_ptr, pbeg, tile, row_idx, val, rowcnt};
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } stg;
     cudaStream_t st = h->stream;
-    CKC(cudaMemcpyAsync(h->col_ptr, A->col_ptr, size_t(h->n + 1) * sizeof(int64_t), kin, st));
+    const cudaMemcpyKind kin = copy_kind(A->on_device, 1);
+    CKC(dalloc(&stg.col_ptr, h->n + 1));
+    CKC(dalloc(&stg.row_idx, h->nnz));
+    CKC(dalloc_bytes(&stg.val, h->nnz * vb));
+    CKC(cudaMemcpyAsync(stg.col_ptr, A->col_ptr, size_t(h->n + 1) * sizeof(int64_t), kin, st));
     if (h->nnz > 0) {
-        CKC(cudaMemcpyAsync(h->row_idx, A->row_idx, size_t(h->nnz) * sizeof(int32_t), kin, st));
-        CKC(cudaMemcpyAsync(h->val, A->val, size_t(h->nnz * vb), kin, st));
+        CKC(cudaMemcpyAsync(stg.row_idx, A->row_idx, size_t(h->nnz) * sizeof(int32_t), kin, st));
+        CKC(cudaMemcpyAsync(stg.val, A->val, size_t(h->nnz * vb), kin, st));
     }
     if (b_dtype == PCDM_F64) {
         CKC(cudaMemcpyAsync(h->b, b, size_t(h->m) * sizeof(double), kin, st));
     } else {
-        // Stage the FP32 b in the g buffer's space (g64 or g is at least m floats).
-        void *stage = h->g;
-        CKC(cudaMemcpyAsync(stage, b, size_t(h->m) * sizeof(float), kin, st));
-        CKC(launch_convert_b(stage, 1, h->m, h->b, st));
+        // Stage the FP32 b in the g buffer (at least m floats) and widen it.
+        CKC(cudaMemcpyAsync(h->g, b, size_t(h->m) * sizeof(float), kin, st));
+        CKC(launch_convert_b(h->g, 1, h->m, h->b, st));
     }
 
     // Validation, first of col_ptr alone so that the column kernels index safely.
@@ -500,50 +554,82 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     int *omega_dev = h->status + 2;
     int *hflags = reinterpret_cast<int *>(h->host_buf + 10);
     CKC(cudaMemsetAsync(h->status, 0, 4 * sizeof(int), st));
-    CKC(launch_check_colptr(h->col_ptr, h->n, h->nnz, flags, st));
+    CKC(launch_check_colptr(stg.col_ptr, h->n, h->nnz, flags, st));
     CKC(cudaMemcpyAsync(hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
     if (*hflags & FLAG_COLPTR) {
         h->err = "col_ptr must start at 0, be non-decreasing and end at nnz";
         return fail(PCDM_EINVAL);
     }
-    int *rowcnt = nullptr;
-    CKC(dalloc(&rowcnt, h->m));
-    cudaError_t e = cudaMemsetAsync(rowcnt, 0, size_t(h->m) * sizeof(int), st);
-    if (e == cudaSuccess) {
-        switch (h->val_dtype) {
-        case PCDM_F64:
-            e = Kernels<double, double>::setup_cols(h->col_ptr, h->row_idx, static_cast<const double *>(h->val), h->m,
-                                                    h->n, h->L64, rowcnt, flags, st);
-            break;
-        case PCDM_F32:
-            e = Kernels<float, float>::setup_cols(h->col_ptr, h->row_idx, static_cast<const float *>(h->val), h->m,
-                                                  h->n, h->L64, rowcnt, flags, st);
-            break;
-        default:
-            e = Kernels<bf16_t, float>::setup_cols(h->col_ptr, h->row_idx, static_cast<const bf16_t *>(h->val), h->m,
-                                                   h->n, h->L64, rowcnt, flags, st);
-            break;
+    CKC(dalloc(&stg.rowcnt, h->m));
+    CKC(cudaMemsetAsync(stg.rowcnt, 0, size_t(h->m) * sizeof(int), st));
+    switch (h->val_dtype) {
+    case PCDM_F64:
+        CKC(Kernels<double, double>::setup_cols(stg.col_ptr, stg.row_idx, static_cast<const double *>(stg.val),
+                                                h->m, h->n, h->L64, stg.rowcnt, flags, st));
+        break;
+    case PCDM_F32:
+        CKC(Kernels<float, float>::setup_cols(stg.col_ptr, stg.row_idx, static_cast<const float *>(stg.val), h->m,
+                                              h->n, h->L64, stg.rowcnt, flags, st));
+        break;
+    default:
+        CKC(Kernels<bf16_t, float>::setup_cols(stg.col_ptr, stg.row_idx, static_cast<const bf16_t *>(stg.val),
+                                               h->m, h->n, h->L64, stg.rowcnt, flags, st));
+        break;
+    }
+    CKC(launch_check_finite(h->b, h->m, flags, st));
+    CKC(launch_max_int(stg.rowcnt, h->m, omega_dev, st));
+    CKC(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    {
+        const int f = hflags[0];
+        if (f) {
+            std::string msg = "invalid input:";
+            if (f & FLAG_ROW_RANGE) msg += " row index outside [0, m);";
+            if (f & FLAG_ROW_ORDER) msg += " rows of a column not strictly increasing;";
+            if (f & FLAG_NONFINITE) msg += " non-finite value in A;";
+            if (f & FLAG_B_NONFINITE) msg += " non-finite value in b;";
+            h->err = msg;
+            return fail(PCDM_EINVAL);
         }
     }
-    if (e == cudaSuccess) e = launch_check_finite(h->b, h->m, flags, st);
-    if (e == cudaSuccess) e = launch_max_int(rowcnt, h->m, omega_dev, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(rowcnt);
-    if (e != cudaSuccess) return fail(cuda_fail(h, e, "set-up kernels"));
-    const int f = hflags[0];
-    if (f) {
-        std::string msg = "invalid input:";
-        if (f & FLAG_ROW_RANGE) msg += " row index outside [0, m);";
-        if (f & FLAG_ROW_ORDER) msg += " rows of a column not strictly increasing;";
-        if (f & FLAG_NONFINITE) msg += " non-finite value in A;";
-        if (f & FLAG_B_NONFINITE) msg += " non-finite value in b;";
-        h->err = msg;
+    h->omega = hflags[1];
+
+    // Padded layout: exclusive scan of the padded lengths, then copy and descriptors.
+    const int granule = h->val_dtype == PCDM_BF16 ? 8 : 4;
+    CKC(dalloc(&stg.pbeg, h->n + 1));
+    CKC(dalloc(&stg.tile, scan_tile_count(h->n) + 1));
+    CKC(launch_padded_scan(stg.col_ptr, h->n, granule, stg.pbeg, stg.tile, st));
+    int64_t *hP = reinterpret_cast<int64_t *>(h->host_buf + 11);
+    CKC(cudaMemcpyAsync(hP, stg.pbeg + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    h->P = *hP;
+    if (h->P / 4 > int64_t(0xFFFFFFFFu)) {
+        h->err = "matrix too large for the padded layout (more than 2^34 padded entries)";
         return fail(PCDM_EINVAL);
     }
-    h->omega = hflags[1];
-    if (h->xg_dtype == PCDM_F32) CKC(launch_f64_to_f32(h->L32, h->L64, h->n, st));
+    CKC(dalloc(&h->prow, h->P + kSlack));
+    CKC(dalloc_bytes(&h->pval, (h->P + kSlack) * vb));
+    CKC(dalloc_bytes(&h->desc, h->n * 16));
+    CKC(cudaMemsetAsync(h->prow, 0, size_t(h->P + kSlack) * sizeof(int32_t), st));
+    CKC(cudaMemsetAsync(h->pval, 0, size_t((h->P + kSlack) * vb), st));
+    switch (h->val_dtype) {
+    case PCDM_F64:
+        CKC(Kernels<double, double>::build_layout(stg.col_ptr, stg.row_idx, static_cast<const double *>(stg.val),
+                                                  stg.pbeg, h->L64, h->n, static_cast<ColDesc<double> *>(h->desc),
+                                                  h->prow, static_cast<double *>(h->pval), st));
+        break;
+    case PCDM_F32:
+        CKC(Kernels<float, float>::build_layout(stg.col_ptr, stg.row_idx, static_cast<const float *>(stg.val),
+                                                stg.pbeg, h->L64, h->n, static_cast<ColDesc<float> *>(h->desc),
+                                                h->prow, static_cast<float *>(h->pval), st));
+        break;
+    default:
+        CKC(Kernels<bf16_t, float>::build_layout(stg.col_ptr, stg.row_idx, static_cast<const bf16_t *>(stg.val),
+                                                 stg.pbeg, h->L64, h->n, static_cast<ColDesc<float> *>(h->desc),
+                                                 h->prow, static_cast<bf16_t *>(h->pval), st));
+        break;
+    }
     CKC(cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st));
     {
         pcdm_status s = reset_state(h);

@@ -1,9 +1,9 @@
 // Device building blocks of libpcdm (sm_103a).
 //
-// - philox_w0 / feistel_pi / sample_index: the tau-nice sampler of pcdm_step
+// - philox4x32_10 / feistel_pi / sample_index: the tau-nice sampler of pcdm_step
 //   (Sec. 4.1 item 3: every tau-subset equally likely), a 12-round Feistel
-//   permutation of [0, 2^w) whose round function is Philox4x32-10 (Salmon et al.,
-//   SC'11), walked back into [0, n).
+//   permutation of [0, 2^w) keyed by Philox4x32-10 (Salmon et al., SC'11) round
+//   keys, walked back into [0, n).
 // - ldv: value loads for FP64 / FP32 / BF16 storage.
 // - red_add: fire-and-forget global atomic adds (red.global.add.{f32,f64}).
 // - group_sum / group_max: reductions inside a group of W lanes of one warp.
@@ -27,9 +27,10 @@ struct bf16_t {
 };
 
 // ---------------------------------------------------------------------------
-// Philox4x32-10, word 0 of the output block.
-__device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                              uint32_t k0, uint32_t k1)
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies,
+// a word permutation and xor with a Weyl-sequence key schedule.
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t out[4])
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -46,13 +47,19 @@ __device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    return c0;
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
 }
 
-// Key of the permutation of iteration k.
+constexpr int kFeistelRounds = 12;
+
+// Permutation key of iteration k: 12 round keys (three Philox blocks with
+// counters (c, 0, lo32(k), hi32(k)), c = 0, 1, 2, keyed by the seed) and the
+// Feistel domain of [0, n).
 struct SampleKey {
-    uint32_t key0, key1;   // lo32(seed), hi32(seed)
-    uint32_t klo, khi;     // lo32(k), hi32(k)
+    uint32_t K[kFeistelRounds];
     uint32_t hb;           // half width of the Feistel domain
     uint32_t mask;         // 2^hb - 1
     uint32_t n;            // ground set size
@@ -65,27 +72,59 @@ __host__ __device__ inline uint32_t feistel_half_bits(int64_t n)
     return w / 2;
 }
 
-__host__ __device__ inline SampleKey make_sample_key(uint64_t seed, int64_t k, int64_t n)
+__device__ __forceinline__ void sample_key_domain(SampleKey &s, int64_t n)
 {
-    SampleKey s;
-    s.key0 = uint32_t(seed);
-    s.key1 = uint32_t(seed >> 32);
-    s.klo = uint32_t(uint64_t(k));
-    s.khi = uint32_t(uint64_t(k) >> 32);
     s.hb = feistel_half_bits(n);
     s.mask = (s.hb >= 32) ? 0xFFFFFFFFu : ((1u << s.hb) - 1u);
     s.n = uint32_t(n);
+}
+
+// Every thread computes the three blocks itself.
+__device__ __forceinline__ SampleKey make_sample_key(uint64_t seed, int64_t k, int64_t n)
+{
+    SampleKey s;
+#pragma unroll
+    for (uint32_t c = 0; c < 3; ++c)
+        philox4x32_10(c, 0u, uint32_t(uint64_t(k)), uint32_t(uint64_t(k) >> 32), uint32_t(seed), uint32_t(seed >> 32),
+                      s.K + 4 * c);
+    sample_key_domain(s, n);
     return s;
 }
 
-constexpr int kFeistelRounds = 12;
+// The same key, computed once per warp (lanes 0..2 one block each) and
+// broadcast; every lane of the warp must call it.
+__device__ __forceinline__ SampleKey warp_sample_key(uint64_t seed, int64_t k, int64_t n)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if (lane < 3)
+        philox4x32_10(lane, 0u, uint32_t(uint64_t(k)), uint32_t(uint64_t(k) >> 32), uint32_t(seed),
+                      uint32_t(seed >> 32), w);
+    SampleKey s;
+#pragma unroll
+    for (int r = 0; r < kFeistelRounds; ++r) s.K[r] = __shfl_sync(0xFFFFFFFFu, w[r & 3], r >> 2);
+    sample_key_domain(s, n);
+    return s;
+}
+
+// MurmurHash3's 32-bit finalizer (Appleby): the Feistel round function mixes
+// R with the round key.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
 
 __device__ __forceinline__ uint32_t feistel_pi(uint32_t v, const SampleKey &s)
 {
     uint32_t left = v >> s.hb, right = v & s.mask;
-#pragma unroll 1
-    for (uint32_t r = 0; r < kFeistelRounds; ++r) {
-        const uint32_t f = philox_w0(right, r, s.klo, s.khi, s.key0, s.key1) & s.mask;
+#pragma unroll
+    for (int r = 0; r < kFeistelRounds; ++r) {
+        const uint32_t f = fmix32(right ^ s.K[r]) & s.mask;
         const uint32_t nr = left ^ f;
         left = right;
         right = nr;
@@ -100,6 +139,17 @@ __device__ __forceinline__ int32_t sample_index(uint32_t j, const SampleKey &s)
     while (v >= s.n) v = feistel_pi(v, s);
     return int32_t(v);
 }
+
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies of 16 bytes (L2 only), per-thread groups.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const uint32_t sa = uint32_t(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------------------
 // Value loads (read-only data: non-coherent path is safe).
@@ -134,8 +184,10 @@ __device__ __forceinline__ T soft_threshold(T u, T t)
 template <int W>
 __device__ __forceinline__ unsigned group_mask(unsigned lane_w)
 {
-    if (W == 32) return 0xFFFFFFFFu;
-    return ((1u << W) - 1u) << (lane_w & ~unsigned(W - 1));
+    if constexpr (W == 32)
+        return 0xFFFFFFFFu;
+    else
+        return ((1u << W) - 1u) << (lane_w & ~unsigned(W - 1));
 }
 
 template <int W, typename T>
@@ -188,33 +240,75 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsig
 
 __device__ __forceinline__ int ld_volatile_int(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
 
+__device__ __forceinline__ bool wait_counter(unsigned long long *counter, unsigned long long target, int *status,
+                                             uint64_t timeout_ns)
+{
+    int ok = 1;
+    const uint64_t t0 = global_ns();
+    uint32_t spins = 0;
+    while (ld_acquire_u64(counter) < target) {
+        if (ld_volatile_int(status) != DEV_OK) {
+            ok = 0;
+            break;
+        }
+        if ((++spins & 31u) == 0u && global_ns() - t0 > timeout_ns) {
+            atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+            ok = 0;
+            break;
+        }
+    }
+    __threadfence();
+    return ok != 0;
+}
+
 __device__ __forceinline__ bool grid_sync(unsigned long long *counter, unsigned long long target, int *status,
                                           uint64_t timeout_ns)
 {
+    if (gridDim.x == 1) {
+        __threadfence();
+        __syncthreads();
+        return true;
+    }
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
         __threadfence();
         red_release_add_u64(counter, 1ull);
-        const uint64_t t0 = global_ns();
-        uint32_t spins = 0;
-        while (ld_acquire_u64(counter) < target) {
-            if (ld_volatile_int(status) != DEV_OK) {
-                ok = 0;
-                break;
-            }
-            if ((++spins & 31u) == 0u && global_ns() - t0 > timeout_ns) {
-                atomicCAS(status, DEV_OK, DEV_TIMEOUT);
-                ok = 0;
-                break;
-            }
-        }
-        __threadfence();
-        s_ok = ok;
+        s_ok = wait_counter(counter, target, status, timeout_ns) ? 1 : 0;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Split form of grid_sync: arrive, do independent work, then wait.
+__device__ __forceinline__ void grid_arrive(unsigned long long *counter)
+{
+    if (gridDim.x == 1) {
+        __threadfence();
+        __syncthreads();
+        return;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_add_u64(counter, 1ull);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned long long *counter, unsigned long long target, int *status,
+                                          uint64_t timeout_ns)
+{
+    if (gridDim.x == 1) return true;
+    __shared__ int s_ok2;
+    if (threadIdx.x == 0) s_ok2 = wait_counter(counter, target, status, timeout_ns) ? 1 : 0;
+    __syncthreads();
+    return s_ok2 != 0;
+}
+
+// Asynchronous prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 }  // namespace pcdm

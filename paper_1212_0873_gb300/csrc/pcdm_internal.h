@@ -1,5 +1,17 @@
 // Host-side declarations shared by the C-ABI implementation (pcdm_api.cu) and
 // the kernel translation units (kernels_*.cu).  Not part of the public ABI.
+//
+// Device layout of A (built once by pcdm_create from the caller's CSC):
+//   desc[i]   16-byte column descriptor {start of the padded segment / 4, nnz of
+//             column i, 1/L_i (0 for an empty column)}: one vector load gives all a
+//             kernel needs to walk column i and take its step.
+//   prow[]    row indices, each column's segment starting at a multiple of G
+//             entries (G = 4 for FP64/FP32 values, 8 for BF16) and padded to a
+//             multiple of G with row 0 / value 0, so every segment is 16-byte
+//             aligned and a whole number of 16-byte words (vector loads, bulk copies).
+//   pval[]    values in the same layout.
+// Both arrays carry kSlack trailing entries so that a lane may read a full run
+// of E entries starting anywhere inside a segment.
 #pragma once
 
 #include <cstdint>
@@ -9,22 +21,50 @@
 
 namespace pcdm {
 
-constexpr int kBlock = 256;          // threads per block of every column kernel
+constexpr int kBlock = 256;          // threads per block of the grid-stride column kernels
 constexpr int kFinishBlock = 256;    // threads of the single-block gap reduction
+// Largest block of the persistent iteration kernel: 448 threads (up to 144
+// registers each; 152 such blocks hold 65536 one-lane groups) for one lane per
+// column, 256 (up to 255 registers) for wider groups, whose chunk loops need more.
+__host__ __device__ constexpr int fused_max_block(int W) { return W == 1 ? 448 : 256; }
+constexpr int kPipeMaxBlock = 448;   // block limit of the pipelined kernel (its chunk buffers fill shared memory)
+constexpr int64_t kSlack = 1024;     // trailing entries of prow / pval
+constexpr int kLaneRun = 16;         // entries a lane reads per chunk (16-byte vector loads)
+
+template <typename XT>
+struct ColDesc;
+template <>
+struct alignas(16) ColDesc<double> {
+    uint32_t pb4;      // segment start / 4
+    int32_t cnt;       // nonzeros of the column
+    double invL;       // 1 / ||a_i||^2, 0 for an empty column
+};
+template <>
+struct alignas(16) ColDesc<float> {
+    uint32_t pb4;
+    int32_t cnt;
+    float invL;
+    float unused;
+};
+
+template <typename VT>
+__host__ __device__ constexpr int pad_granule()
+{
+    return sizeof(VT) == 2 ? 8 : 4;
+}
 
 // Everything one PCDM1 iteration reads and writes.  XT is the dtype of x, g, h,
-// L and of the gradient accumulator; VT the dtype of the stored values.
+// 1/L and of the gradient accumulator; VT the dtype of the stored values.
 template <typename VT, typename XT>
 struct IterArgs {
-    const int64_t *col_ptr;
-    const int32_t *row_idx;
-    const VT *val;
-    const XT *L;
+    const ColDesc<XT> *desc;
+    const int32_t *prow;
+    const VT *pval;
     XT *x;
     XT *g;
     XT *h;                      // h[j] = step of coordinate S_k[j]
     int32_t *S[2];              // S_k lives in S[k & 1]
-    XT beta, lambda;
+    XT inv_beta, lambda;
     int64_t n, tau;
     uint64_t seed;
     unsigned long long *counters;   // [0] gathered nnz, [1] scattered nnz, [2] nonzero updates
@@ -33,26 +73,41 @@ struct IterArgs {
     uint64_t timeout_ns;
 };
 
+// Launch shape of the fused kernel.
+struct FusedShape {
+    int W = 1;          // lanes per column
+    int blocks = 1;
+    int threads = 32;
+};
+
 // Column kernels, instantiated for (double,double), (float,float), (bf16_t,float).
 template <typename VT, typename XT>
 struct Kernels {
-    // S_{k} must already be in S[k & 1].  Gather + prox + x update for j < tau.
+    // Two-kernel form.  S_k must already be in S[k & 1].
     static cudaError_t gather(const IterArgs<VT, XT> &a, int W, int64_t k, cudaStream_t st);
-    // Scatter of the columns with h != 0; with sample_next, also S_{k+1} -> S[(k+1) & 1].
     static cudaError_t scatter(const IterArgs<VT, XT> &a, int W, int64_t k, bool sample_next, cudaStream_t st);
     // Persistent cooperative kernel: iterations k0 .. k0+iters-1, S_{k0} already drawn;
-    // leaves S_{k0+iters} drawn.  `blocks` must not exceed fused_max_blocks(W).
-    static cudaError_t fused(const IterArgs<VT, XT> &a, int W, int64_t k0, int64_t iters, int blocks,
+    // leaves S_{k0+iters} drawn.
+    static cudaError_t fused(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
                              cudaStream_t st);
-    static int fused_max_blocks(int W);
-    // L_i = sum a_ri^2 (FP64), row counts and validation of rows/values.
+    // Largest co-resident grid of the fused kernel for W lanes per column and a block of `threads`.
+    static int fused_max_blocks(int W, int threads);
+    // Pipelined persistent kernel (one lane per column, tau <= blocks * threads).
+    static cudaError_t fused_pipe(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
+                                  cudaStream_t st);
+    static int pipe_max_blocks(int threads);
+    // L_i = sum a_ri^2 (FP64), row counts and validation, on the caller's CSC layout.
     static cudaError_t setup_cols(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, int64_t m,
                                   int64_t n, double *L, int *rowcnt, int *flags, cudaStream_t st);
+    // Padded layout: copy the columns into prow/pval at pbeg (entries) and write desc.
+    static cudaError_t build_layout(const int64_t *col_ptr, const int32_t *row_idx, const VT *val,
+                                    const int64_t *pbeg, const double *L, int64_t n, ColDesc<XT> *desc,
+                                    int32_t *prow, VT *pval, cudaStream_t st);
     // g64 += A x over the columns with x_i != 0.
-    static cudaError_t refresh_cols(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, const XT *x,
+    static cudaError_t refresh_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const XT *x,
                                     int64_t n, double *g64, int W, cudaStream_t st);
     // Per-block partials (max |c_i|, sum |x_i|, sum x_i c_i), c = A^T r.
-    static cudaError_t gap_cols(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, const double *r,
+    static cudaError_t gap_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *r,
                                 const XT *x, int64_t n, double *part, int blocks, int W, cudaStream_t st);
 };
 
@@ -72,6 +127,11 @@ cudaError_t launch_gap_finish(const double *pc, int nbc, const double *pr, int n
                               cudaStream_t st);
 cudaError_t launch_barrier_selftest(unsigned long long *bar, int *status, uint64_t timeout_ns, int blocks,
                                     cudaStream_t st);
+// Exclusive scan of the padded column lengths: pbeg[i] = sum_{q<i} roundup(cnt_q, granule),
+// pbeg[n] = total.  `tile` is scratch of scan_tile_count(n) + 1 int64.
+int64_t scan_tile_count(int64_t n);
+cudaError_t launch_padded_scan(const int64_t *col_ptr, int64_t n, int granule, int64_t *pbeg, int64_t *tile,
+                               cudaStream_t st);
 
 // Validation flag bits (setup kernels).
 enum : int {

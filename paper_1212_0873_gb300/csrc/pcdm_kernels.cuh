@@ -1,20 +1,27 @@
 // Column kernels of libpcdm, templated on the stored value type VT and the
-// iterate type XT (x, g, h, L and the gradient accumulator).  Included by one
+// iterate type XT (x, g, h, 1/L and the gradient accumulator).  Included by one
 // translation unit per (VT, XT) pair, which instantiates Kernels<VT, XT>.
 //
-// Work mapping: a group of W lanes of one warp (W in {4, 8, 16, 32}) owns one
-// sampled column at a time; lane l reads entries beg+l, beg+l+W, ... so the
-// group's loads of row_idx and val are contiguous, and the partial sums meet in
-// a shuffle tree inside the group.
+// Work mapping.  A group of W lanes of one warp (W in {1, 2, 4, 8, 16, 32}) owns
+// one column at a time; lane l owns the contiguous run of kE entries starting at
+// l*kE inside each chunk of W*kE entries, read with 16-byte vector loads from the
+// padded layout (see pcdm_internal.h).  Short columns (the common case) use
+// W = 1: no cross-lane reduction, and the proximal step runs on all 32 lanes of
+// a warp at once, which matters on GB300 where FP64 issues at about 2 DFMA per
+// clock per SM.
 //
 // One PCDM1 iteration (Algorithm 1, step 4, with h(x) of eq. (h(x)), w = L):
 //   phase 1 (gather):  grad_i = a_i^T g for i = S_k[j], all from the same g;
 //                      x_new = soft(x_i - grad_i/(beta L_i), lambda/(beta L_i));
-//                      h[j] = x_new - x_i; x_i = x_new
-//   phase 2 (scatter): g_r += a_ri h[j] for the columns with h[j] != 0 (red.global.add),
-//                      and S_{k+1} is drawn into the other sample buffer.
-// The two phases are separated by a kernel boundary (two-kernel form) or by a
-// bounded grid barrier (fused persistent form), which keeps the update Jacobi.
+//                      h_j = x_new - x_i; x_i = x_new
+//   phase 2 (scatter): g_r += a_ri h_j for the columns with h_j != 0 (red.global.add),
+//                      and S_{k+1} is drawn.
+// The phases are separated by a kernel boundary (two-kernel form) or by a
+// bounded grid barrier (fused persistent form).  The fused form keeps each
+// group's next column in registers across the barrier: during phase 2 of
+// iteration k it already draws its sample of iteration k+1 and loads that
+// column's descriptor and first chunk, so that after the barrier only the
+// gathers of g and x remain on the critical path.
 #pragma once
 
 #include <cmath>
@@ -22,6 +29,8 @@
 #include "pcdm_internal.h"
 
 namespace pcdm {
+
+constexpr int kE = kLaneRun;   // entries per lane and chunk
 
 template <typename VT, typename XT>
 __device__ __forceinline__ int32_t *sample_buf(const IterArgs<VT, XT> &a, int64_t k)
@@ -45,46 +54,186 @@ __device__ __forceinline__ void flush_counters(const Counters &c, unsigned long 
     }
 }
 
-// Phase 1 for sampled position j (all W lanes of the group call it together).
+// ---------------------------------------------------------------------------
+// Column descriptor and chunk loads.
+template <typename XT>
+struct Col {
+    int64_t pbeg;
+    int cnt;
+    XT invL;
+};
+
+template <typename XT>
+__device__ __forceinline__ Col<XT> load_col(const ColDesc<XT> *d, int32_t i)
+{
+    const int4 v = __ldg(reinterpret_cast<const int4 *>(d + i));
+    Col<XT> c;
+    c.pbeg = int64_t(uint32_t(v.x)) * 4;
+    c.cnt = v.y;
+    if constexpr (sizeof(XT) == 8)
+        c.invL = __hiloint2double(v.w, v.z);
+    else
+        c.invL = __int_as_float(v.z);
+    return c;
+}
+
+template <int E, typename XT>
+struct Chunk {
+    int32_t row[E];
+    XT val[E];
+};
+
+template <int E>
+__device__ __forceinline__ void ld_rows(int32_t (&r)[E], const int32_t *p)
+{
+#pragma unroll
+    for (int q = 0; q < E / 4; ++q) {
+        const int4 v = __ldg(reinterpret_cast<const int4 *>(p) + q);
+        r[4 * q + 0] = v.x;
+        r[4 * q + 1] = v.y;
+        r[4 * q + 2] = v.z;
+        r[4 * q + 3] = v.w;
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void ld_vals(double (&v)[E], const double *p)
+{
+#pragma unroll
+    for (int q = 0; q < E / 2; ++q) {
+        const double2 d = __ldg(reinterpret_cast<const double2 *>(p) + q);
+        v[2 * q + 0] = d.x;
+        v[2 * q + 1] = d.y;
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void ld_vals(float (&v)[E], const float *p)
+{
+#pragma unroll
+    for (int q = 0; q < E / 4; ++q) {
+        const float4 d = __ldg(reinterpret_cast<const float4 *>(p) + q);
+        v[4 * q + 0] = d.x;
+        v[4 * q + 1] = d.y;
+        v[4 * q + 2] = d.z;
+        v[4 * q + 3] = d.w;
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void ld_vals(float (&v)[E], const bf16_t *p)
+{
+#pragma unroll
+    for (int q = 0; q < E / 8; ++q) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p) + q);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            v[8 * q + 2 * t + 0] = __uint_as_float(w[t] << 16);
+            v[8 * q + 2 * t + 1] = __uint_as_float(w[t] & 0xFFFF0000u);
+        }
+    }
+}
+
+template <int E, typename VT, typename XT>
+__device__ __forceinline__ void ld_chunk(Chunk<E, XT> &c, const int32_t *prow, const VT *pval, int64_t p)
+{
+    ld_rows<E>(c.row, prow + p);
+    ld_vals<E>(c.val, pval + p);
+}
+
+// sum_e val[e] * v[row[e]] over the first `valid` entries of the lane's run.
+template <int E, typename XT, typename GT, typename AT>
+__device__ __forceinline__ AT chunk_dot(const Chunk<E, XT> &c, const GT *v, int valid)
+{
+    GT gv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) gv[e] = (e < valid) ? ldcg(v + c.row[e]) : GT(0);
+    AT acc = AT(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (e < valid) acc = fma(AT(c.val[e]), AT(gv[e]), acc);
+    return acc;
+}
+
+template <int E, typename XT>
+__device__ __forceinline__ void chunk_scatter(const Chunk<E, XT> &c, XT *g, XT h, int valid)
+{
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (e < valid) red_add(g + c.row[e], c.val[e] * h);
+}
+
+// a_i^T g over a whole column, chunk by chunk (all W lanes of the group together).
 template <int W, typename VT, typename XT>
-__device__ __forceinline__ void gather_prox_one(const IterArgs<VT, XT> &a, const int32_t *S, int64_t j, int lane,
-                                                unsigned gmask, Counters &cnt)
+__device__ __forceinline__ XT column_dot(const IterArgs<VT, XT> &a, const Col<XT> &c, int lane, unsigned gmask)
+{
+    constexpr int CH = W * kE;
+    XT acc = XT(0);
+    for (int cs = 0; cs < c.cnt; cs += CH) {
+        Chunk<kE, XT> t;
+        const int st = cs + lane * kE;
+        if (st < c.cnt) ld_chunk<kE>(t, a.prow, a.pval, c.pbeg + st);
+        acc += chunk_dot<kE, XT, XT, XT>(t, a.g, c.cnt - st);
+    }
+    return group_sum<W>(acc, gmask);
+}
+
+template <int W, typename VT, typename XT>
+__device__ __forceinline__ void column_scatter(const IterArgs<VT, XT> &a, const Col<XT> &c, int lane, XT h,
+                                               int from)
+{
+    constexpr int CH = W * kE;
+    for (int cs = from; cs < c.cnt; cs += CH) {
+        Chunk<kE, XT> t;
+        const int st = cs + lane * kE;
+        if (st < c.cnt) {
+            ld_chunk<kE>(t, a.prow, a.pval, c.pbeg + st);
+            chunk_scatter<kE>(t, a.g, h, c.cnt - st);
+        }
+    }
+}
+
+// The step of eq. (h(x)) for one coordinate: soft(x - grad/(beta L), lambda/(beta L)),
+// with 1/(beta L) = (1/L)(1/beta); an empty column (1/L stored as 0) goes to 0.
+template <typename XT>
+__device__ __forceinline__ XT prox_step(XT xi, XT grad, XT invL, XT inv_beta, XT lambda)
+{
+    if (invL == XT(0)) return XT(0);
+    const XT ibl = invL * inv_beta;
+    return soft_threshold<XT>(fma(-grad, ibl, xi), lambda * ibl);
+}
+
+// Phase 1 for sampled position j, columns read from memory (no prefetch).
+template <int W, typename VT, typename XT>
+__device__ __forceinline__ void gather_generic(const IterArgs<VT, XT> &a, const int32_t *S, int64_t j, int lane,
+                                               unsigned gmask, Counters &cnt)
 {
     const int32_t i = ldcg(S + j);
-    const int64_t beg = __ldg(a.col_ptr + i);
-    const int64_t end = __ldg(a.col_ptr + i + 1);
-    XT acc = XT(0);
-    for (int64_t p = beg + lane; p < end; p += W) acc += XT(ldv(a.val + p)) * ldcg(a.g + __ldg(a.row_idx + p));
-    acc = group_sum<W>(acc, gmask);
+    const Col<XT> c = load_col(a.desc, i);
+    const XT xi = ldcg(a.x + i);
+    const XT grad = column_dot<W>(a, c, lane, gmask);
+    const XT xn = prox_step<XT>(xi, grad, c.invL, a.inv_beta, a.lambda);
+    const XT h = xn - xi;
     if (lane == 0) {
-        const XT xi = ldcg(a.x + i);
-        const XT Li = __ldg(a.L + i);
-        XT xn = XT(0);
-        if (Li > XT(0)) {
-            const XT bl = a.beta * Li;
-            xn = soft_threshold<XT>(xi - acc / bl, a.lambda / bl);
-        }
-        const XT h = xn - xi;
         a.x[i] = xn;
         a.h[j] = h;
-        cnt.gathered += (unsigned long long)(end - beg);
+        cnt.gathered += (unsigned long long)c.cnt;
         if (h != XT(0)) {
             cnt.nonzero += 1;
-            cnt.scattered += (unsigned long long)(end - beg);
+            cnt.scattered += (unsigned long long)c.cnt;
         }
     }
 }
 
 // Phase 2 for sampled position j.
 template <int W, typename VT, typename XT>
-__device__ __forceinline__ void scatter_one(const IterArgs<VT, XT> &a, const int32_t *S, int64_t j, int lane)
+__device__ __forceinline__ void scatter_generic(const IterArgs<VT, XT> &a, const int32_t *S, int64_t j, int lane)
 {
     const XT h = ldcg(a.h + j);
     if (h == XT(0)) return;
     const int32_t i = ldcg(S + j);
-    const int64_t beg = __ldg(a.col_ptr + i);
-    const int64_t end = __ldg(a.col_ptr + i + 1);
-    for (int64_t p = beg + lane; p < end; p += W) red_add(a.g + __ldg(a.row_idx + p), XT(ldv(a.val + p)) * h);
+    column_scatter<W>(a, load_col(a.desc, i), lane, h, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -96,7 +245,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(const IterArgs<VT, XT> a, int
     const unsigned gmask = group_mask<W>(threadIdx.x & 31);
     const int64_t grp = (int64_t(blockIdx.x) * kBlock + threadIdx.x) / W;
     Counters cnt;
-    if (grp < a.tau) gather_prox_one<W>(a, sample_buf(a, k), grp, lane, gmask, cnt);
+    if (grp < a.tau) gather_generic<W>(a, sample_buf(a, k), grp, lane, gmask, cnt);
     flush_counters(cnt, a.counters);
 }
 
@@ -106,46 +255,395 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const IterArgs<VT, XT> a, in
     const int lane = threadIdx.x & (W - 1);
     const int64_t gid = int64_t(blockIdx.x) * kBlock + threadIdx.x;
     const int64_t grp = gid / W;
-    if (grp < a.tau) scatter_one<W>(a, sample_buf(a, k), grp, lane);
-    if (sample_next && gid < a.tau) {
-        const SampleKey key = make_sample_key(a.seed, k + 1, a.n);
-        sample_buf(a, k + 1)[gid] = sample_index(uint32_t(gid), key);
+    if (grp < a.tau) scatter_generic<W>(a, sample_buf(a, k), grp, lane);
+    if (sample_next) {
+        const SampleKey key = warp_sample_key(a.seed, k + 1, a.n);
+        if (gid < a.tau) sample_buf(a, k + 1)[gid] = sample_index(uint32_t(gid), key);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Fused persistent form: one cooperative launch runs `iters` iterations.
+// Position j0 = (global thread index) / W is this group's register-resident
+// column; positions j0 + ngrp, j0 + 2 ngrp, ... (only when tau exceeds the
+// number of groups) go through the generic path.
 template <int W, typename VT, typename XT>
-__global__ void __launch_bounds__(kBlock) k_fused(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
+__global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
 {
+    constexpr int CH = W * kE;
+    constexpr int G = pad_granule<VT>();
     const int lane = threadIdx.x & (W - 1);
     const unsigned gmask = group_mask<W>(threadIdx.x & 31);
-    const int64_t nthreads = int64_t(gridDim.x) * kBlock;
-    const int64_t gid = int64_t(blockIdx.x) * kBlock + threadIdx.x;
-    const int64_t grp = gid / W;
+    const int64_t nthreads = int64_t(gridDim.x) * blockDim.x;
+    const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t j0 = gid / W;
     const int64_t ngrp = nthreads / W;
+    const bool own = j0 < a.tau;
     unsigned long long target = 0;
     Counters cnt;
+
+    // Prologue: the column of iteration k0 into registers.
+    int32_t i0 = 0;
+    Col<XT> c0;
+    c0.pbeg = 0;
+    c0.cnt = 0;
+    c0.invL = XT(0);
+    Chunk<kE, XT> ch;
+    if (own) {
+        i0 = ldcg(sample_buf(a, k0) + j0);
+        c0 = load_col(a.desc, i0);
+        if (lane * kE < c0.cnt) ld_chunk<kE>(ch, a.prow, a.pval, c0.pbeg + lane * kE);
+    }
+
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t k = k0 + it;
         const int32_t *S = sample_buf(a, k);
-        for (int64_t j = grp; j < a.tau; j += ngrp) gather_prox_one<W>(a, S, j, lane, gmask, cnt);
+        XT h0 = XT(0);
+        // ---------------- phase 1: gradient, step, x update
+        // Issue the loads of x_i and of g at the chunk's rows first, draw this
+        // group's sample of iteration k+1 (integer work) while they are in
+        // flight, then consume them on the FP pipe.
+        const SampleKey key = warp_sample_key(a.seed, k + 1, a.n);
+        int32_t i_next = 0;
+        Col<XT> c_next = c0;
+        if (own) {
+            const XT xi = ldcg(a.x + i0);
+            XT gv[kE];
+            const int valid0 = c0.cnt - lane * kE;
+#pragma unroll
+            for (int e = 0; e < kE; ++e) gv[e] = (e < valid0) ? ldcg(a.g + ch.row[e]) : XT(0);
+            i_next = sample_index(uint32_t(j0), key);
+            c_next = load_col(a.desc, i_next);
+            XT acc = XT(0);
+#pragma unroll
+            for (int e = 0; e < kE; ++e)
+                if (e < valid0) acc = fma(ch.val[e], gv[e], acc);
+            for (int cs = CH; cs < c0.cnt; cs += CH) {
+                Chunk<kE, XT> t;
+                const int st = cs + lane * kE;
+                if (st < c0.cnt) ld_chunk<kE>(t, a.prow, a.pval, c0.pbeg + st);
+                acc += chunk_dot<kE, XT, XT, XT>(t, a.g, c0.cnt - st);
+            }
+            acc = group_sum<W>(acc, gmask);
+            const XT xn = prox_step<XT>(xi, acc, c0.invL, a.inv_beta, a.lambda);
+            h0 = xn - xi;
+            if (lane == 0) {
+                a.x[i0] = xn;
+                cnt.gathered += (unsigned long long)c0.cnt;
+                if (h0 != XT(0)) {
+                    cnt.nonzero += 1;
+                    cnt.scattered += (unsigned long long)c0.cnt;
+                }
+            }
+        }
+        for (int64_t j = j0 + ngrp; j < a.tau; j += ngrp) gather_generic<W>(a, S, j, lane, gmask, cnt);
         target += gridDim.x;
         if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) return;
-        for (int64_t j = grp; j < a.tau; j += ngrp) scatter_one<W>(a, S, j, lane);
-        {
-            const SampleKey key = make_sample_key(a.seed, k + 1, a.n);
-            int32_t *Snext = sample_buf(a, k + 1);
-            for (int64_t j = gid; j < a.tau; j += nthreads) Snext[j] = sample_index(uint32_t(j), key);
+
+        // ---------------- phase 2: residual update, next sample
+        // the chunk registers are free by now (reloaded from L2 for the few columns with h != 0)
+        if (own && h0 != XT(0)) column_scatter<W>(a, c0, lane, h0, 0);
+        for (int64_t j = j0 + ngrp; j < a.tau; j += ngrp) scatter_generic<W>(a, S, j, lane);
+        int32_t *Sn = sample_buf(a, k + 1);
+        for (int64_t j = ngrp + gid; j < a.tau; j += nthreads) Sn[j] = sample_index(uint32_t(j), key);
+        if (own) {
+            i0 = i_next;
+            c0 = c_next;
+            if (lane == 0) Sn[j0] = i0;
         }
         target += gridDim.x;
-        if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) return;
+        grid_arrive(a.bar);
+        if (own) {
+            if (lane * kE < c0.cnt) ld_chunk<kE>(ch, a.prow, a.pval, c0.pbeg + lane * kE);
+            if (lane == 0 && c0.cnt > CH) {
+                const int64_t tail = ((int64_t(c0.cnt) + G - 1) / G) * G - CH;
+                prefetch_l2_bulk(a.prow + c0.pbeg + CH, uint32_t(tail * 4));
+                prefetch_l2_bulk(a.pval + c0.pbeg + CH, uint32_t(tail * int64_t(sizeof(VT))));
+            }
+        }
+        if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) return;
     }
     flush_counters(cnt, a.counters);
 }
 
 // ---------------------------------------------------------------------------
-// Set-up: one thread per column (runs once per matrix).
+// Pipelined persistent form: one lane per column, every sampled position owned
+// by one thread (tau <= threads of the grid).  Thread j keeps i_k and i_{k+1}
+// with their descriptors in registers; the first kE entries of column i_k sit in
+// shared-memory buffer (it & 1).  Per iteration k:
+//   phase 1  the gathers of g at the chunk's rows (and the start of the column's
+//            tail) are issued; the sample i_{k+2} is drawn (integer work) while
+//            they are in flight and its descriptor load is issued; then
+//            gradient, step, x;
+//   barrier
+//   phase 2  the warp copies the first chunks of its 32 columns i_{k+1} into the
+//            other buffer with cp.async, consecutive lanes taking consecutive
+//            16-byte pieces of the same column (coalesced), and prefetches their
+//            tails into L2; then the scatter of column i_k (h != 0) from the
+//            current buffer;
+//   barrier
+// On GB300 the scattered gathers of phase 1 saturate each SM's load/store
+// pipe, so everything else that uses it (bulk copies, shuffles, shared-memory
+// traffic) is kept out of phase 1.
+template <typename VT, typename XT>
+__device__ __forceinline__ void smem_vals(XT (&v)[kE], const uint4 *p, int stride)
+{
+    if constexpr (sizeof(VT) == 8) {
+#pragma unroll
+        for (int w = 0; w < kE / 2; ++w) {
+            const uint4 u = p[w * stride];
+            v[2 * w + 0] = XT(__hiloint2double(int(u.y), int(u.x)));
+            v[2 * w + 1] = XT(__hiloint2double(int(u.w), int(u.z)));
+        }
+    } else if constexpr (sizeof(VT) == 4) {
+#pragma unroll
+        for (int w = 0; w < kE / 4; ++w) {
+            const uint4 u = p[w * stride];
+            v[4 * w + 0] = XT(__uint_as_float(u.x));
+            v[4 * w + 1] = XT(__uint_as_float(u.y));
+            v[4 * w + 2] = XT(__uint_as_float(u.z));
+            v[4 * w + 3] = XT(__uint_as_float(u.w));
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < kE / 8; ++w) {
+            const uint4 u = p[w * stride];
+            const uint32_t q[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                v[8 * w + 2 * t + 0] = XT(__uint_as_float(q[t] << 16));
+                v[8 * w + 2 * t + 1] = XT(__uint_as_float(q[t] & 0xFFFF0000u));
+            }
+        }
+    }
+}
+
+// Values of one 16-byte word of a shared chunk (16 / sizeof(VT) entries).
+template <typename VT, typename XT>
+__device__ __forceinline__ void decode_word(const uint4 u, XT (&v)[16 / sizeof(VT)])
+{
+    if constexpr (sizeof(VT) == 8) {
+        v[0] = XT(__hiloint2double(int(u.y), int(u.x)));
+        v[1] = XT(__hiloint2double(int(u.w), int(u.z)));
+    } else if constexpr (sizeof(VT) == 4) {
+        v[0] = XT(__uint_as_float(u.x));
+        v[1] = XT(__uint_as_float(u.y));
+        v[2] = XT(__uint_as_float(u.z));
+        v[3] = XT(__uint_as_float(u.w));
+    } else {
+        const uint32_t q[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            v[2 * t + 0] = XT(__uint_as_float(q[t] << 16));
+            v[2 * t + 1] = XT(__uint_as_float(q[t] & 0xFFFF0000u));
+        }
+    }
+}
+
+template <typename VT>
+__host__ __device__ constexpr int pipe_value_words()
+{
+    return kLaneRun * int(sizeof(VT)) / 16;
+}
+
+template <typename VT>
+__host__ __device__ constexpr size_t pipe_smem_bytes(int threads)
+{
+    return size_t(2) * size_t(threads) * 16 * size_t(4 + pipe_value_words<VT>());
+}
+
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int VW = pipe_value_words<VT>();
+    constexpr int PIECES = 4 + VW;                        // 16-byte pieces of one chunk
+    const int nt = blockDim.x, t = threadIdx.x;
+    const int lane = t & 31, wbase = t & ~31;
+    const size_t buf_bytes = size_t(nt) * 16 * size_t(PIECES);
+    const int64_t j0 = int64_t(blockIdx.x) * nt + t;
+    const bool own = j0 < a.tau;
+    unsigned long long target = 0;
+    Counters cnt;
+
+    // piece q of thread tt's chunk in buffer b (rows first, then values)
+    auto piece_at = [&](int b, int q, int tt) {
+        return reinterpret_cast<uint4 *>(smem + size_t(b) * buf_bytes) + size_t(q) * nt + tt;
+    };
+    // The warp copies the chunks of its 32 columns (descriptor of the calling
+    // lane = its own next column; cnt 0 means nothing to copy).
+    auto copy_warp_chunks = [&](int b, const Col<XT> &d) {
+        const uint32_t pb_lo = uint32_t(d.pbeg), pb_hi = uint32_t(uint64_t(d.pbeg) >> 32);
+        for (int p = lane; p < 32 * PIECES; p += 32) {
+            const int c = p / PIECES, q = p - c * PIECES;
+            const int64_t pb = int64_t((uint64_t(__shfl_sync(0xFFFFFFFFu, pb_hi, c)) << 32) |
+                                       __shfl_sync(0xFFFFFFFFu, pb_lo, c));
+            const int cc = __shfl_sync(0xFFFFFFFFu, d.cnt, c);
+            if (cc <= 0) continue;
+            const uint4 *src = q < 4 ? reinterpret_cast<const uint4 *>(a.prow + pb) + q
+                                     : reinterpret_cast<const uint4 *>(a.pval + pb) + (q - 4);
+            cp_async16(piece_at(b, q, wbase + c), src);
+        }
+        cp_async_commit();
+    };
+    auto own_col = [&](const Col<XT> &d) {
+        Col<XT> z = d;
+        if (!own) z.cnt = 0;
+        return z;
+    };
+
+    // Prologue: i_{k0} (drawn by the caller) and its chunk; i_{k0+1} and its descriptor.
+    int32_t i_cur = 0, i_nxt = 0;
+    Col<XT> d_cur, d_nxt;
+    d_cur.pbeg = d_nxt.pbeg = 0;
+    d_cur.cnt = d_nxt.cnt = 0;
+    d_cur.invL = d_nxt.invL = XT(0);
+    {
+        const SampleKey key1 = warp_sample_key(a.seed, k0 + 1, a.n);
+        if (own) {
+            i_cur = ldcg(sample_buf(a, k0) + j0);
+            d_cur = load_col(a.desc, i_cur);
+            i_nxt = sample_index(uint32_t(j0), key1);
+            d_nxt = load_col(a.desc, i_nxt);
+        }
+    }
+    copy_warp_chunks(0, own_col(d_cur));
+    cp_async_wait<0>();
+    __syncwarp();
+
+    constexpr int kT = kE / 2;   // tail entries [kE, kE + kT) fetched early into registers
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t k = k0 + it;
+        const int b = int(it & 1);
+        // the chunks of this iteration's columns, copied during the previous phase 2
+        cp_async_wait<0>();
+        __syncwarp();
+
+        // ---------------- phase 1: gradient, step, x update
+        // The loads go first (x_i, the gathers of g at the chunk's rows, the start
+        // of the column's tail); the sample of k+2 (integer work only: no
+        // shuffles or shared-memory traffic, which would queue behind the loads)
+        // is drawn while they are in flight.
+        XT h = XT(0), xi = XT(0);
+        int32_t i_nn = 0;
+        Col<XT> d_nn = d_nxt;
+        const int valid = own ? d_cur.cnt : 0;
+        if (own) {
+            xi = ldcg(a.x + i_cur);
+            int32_t row[kE];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 r4 = *piece_at(b, q, t);
+                row[4 * q + 0] = int32_t(r4.x);
+                row[4 * q + 1] = int32_t(r4.y);
+                row[4 * q + 2] = int32_t(r4.z);
+                row[4 * q + 3] = int32_t(r4.w);
+            }
+            XT gv[kE];
+#pragma unroll
+            for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg(a.g + row[e]) : XT(0);
+            Chunk<kT, XT> tl;
+            if (valid > kE) ld_chunk<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE);
+            i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
+            d_nn = load_col(a.desc, i_nn);
+            XT gt[kT];
+#pragma unroll
+            for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg(a.g + tl.row[e]) : XT(0);
+            constexpr int EPW = 16 / int(sizeof(VT));
+            XT acc = XT(0);
+#pragma unroll
+            for (int w = 0; w < VW; ++w) {
+                XT vw[EPW];
+                decode_word<VT, XT>(*piece_at(b, 4 + w, t), vw);
+#pragma unroll
+                for (int q = 0; q < EPW; ++q)
+                    if (w * EPW + q < valid) acc = fma(vw[q], gv[w * EPW + q], acc);
+            }
+#pragma unroll
+            for (int e = 0; e < kT; ++e)
+                if (kE + e < valid) acc = fma(tl.val[e], gt[e], acc);
+            for (int cs = kE + kT; cs < valid; cs += kE) {
+                Chunk<kE, XT> tc;
+                ld_chunk<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs);
+                acc += chunk_dot<kE, XT, XT, XT>(tc, a.g, valid - cs);
+            }
+            const XT xn = prox_step<XT>(xi, acc, d_cur.invL, a.inv_beta, a.lambda);
+            h = xn - xi;
+            a.x[i_cur] = xn;
+            cnt.gathered += (unsigned long long)valid;
+            if (h != XT(0)) {
+                cnt.nonzero += 1;
+                cnt.scattered += (unsigned long long)valid;
+            }
+        }
+        target += gridDim.x;
+        if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) {
+            cp_async_wait<0>();
+            return;
+        }
+
+        // ---------------- phase 2: next columns' chunks stream in; residual update
+        // The memory pipe is otherwise idle here: the copies of the chunks of
+        // i_{k+1} into the other buffer (coalesced across the warp) and the L2
+        // prefetch of their tails run through phase 2 and the barrier.
+        copy_warp_chunks(b ^ 1, own_col(d_nxt));
+        if (own && d_nxt.cnt > kE) {
+            constexpr int G = pad_granule<VT>();
+            const int64_t tail = ((int64_t(d_nxt.cnt) + G - 1) / G) * G - kE;
+            prefetch_l2_bulk(a.prow + d_nxt.pbeg + kE, uint32_t(tail * 4));
+            prefetch_l2_bulk(a.pval + d_nxt.pbeg + kE, uint32_t(tail * int64_t(sizeof(VT))));
+        }
+        if (own && h != XT(0)) {
+            int32_t row[kE];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 r4 = *piece_at(b, q, t);
+                row[4 * q + 0] = int32_t(r4.x);
+                row[4 * q + 1] = int32_t(r4.y);
+                row[4 * q + 2] = int32_t(r4.z);
+                row[4 * q + 3] = int32_t(r4.w);
+            }
+            constexpr int EPW = 16 / int(sizeof(VT));
+#pragma unroll
+            for (int w = 0; w < VW; ++w) {
+                XT vw[EPW];
+                decode_word<VT, XT>(*piece_at(b, 4 + w, t), vw);
+#pragma unroll
+                for (int q = 0; q < EPW; ++q)
+                    if (w * EPW + q < valid) red_add(a.g + row[w * EPW + q], vw[q] * h);
+            }
+            column_scatter<1>(a, d_cur, 0, h, kE);
+        }
+        target += gridDim.x;
+        if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) {
+            cp_async_wait<0>();
+            return;
+        }
+        i_cur = i_nxt;
+        d_cur = d_nxt;
+        i_nxt = i_nn;
+        d_nxt = d_nn;
+    }
+    cp_async_wait<0>();
+    // S_{k0+iters} for the caller (the sample of the next launch).
+    if (own) sample_buf(a, k0 + iters)[j0] = i_cur;
+    flush_counters(cnt, a.counters);
+}
+
+// ---------------------------------------------------------------------------
+// Set-up on the caller's layout: one thread per column (runs once per matrix).
+template <typename VT>
+__device__ __forceinline__ double ld_orig(const VT *p);
+template <>
+__device__ __forceinline__ double ld_orig<double>(const double *p) { return *p; }
+template <>
+__device__ __forceinline__ double ld_orig<float>(const float *p) { return double(*p); }
+template <>
+__device__ __forceinline__ double ld_orig<bf16_t>(const bf16_t *p)
+{
+    return double(__uint_as_float(uint32_t(p->bits) << 16));
+}
+
 template <typename VT>
 __global__ void k_setup_cols(const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
                              const VT *__restrict__ val, int64_t m, int64_t n, double *__restrict__ L,
@@ -164,7 +662,7 @@ __global__ void k_setup_cols(const int64_t *__restrict__ col_ptr, const int32_t 
             }
             if (r <= prev) f |= FLAG_ROW_ORDER;
             prev = r;
-            const double v = double(ldv(val + p));
+            const double v = ld_orig<VT>(val + p);
             if (!isfinite(v)) f |= FLAG_NONFINITE;
             s = __dadd_rn(s, __dmul_rn(v, v));   // no contraction: the same bits as a plain sum of squares
             atomicAdd(rowcnt + r, 1);
@@ -174,44 +672,83 @@ __global__ void k_setup_cols(const int64_t *__restrict__ col_ptr, const int32_t 
     if (f) atomicOr(flags, f);
 }
 
+// Padded layout and descriptors (prow / pval zero-filled beforehand).
+template <typename VT, typename XT>
+__global__ void k_build_layout(const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
+                               const VT *__restrict__ val, const int64_t *__restrict__ pbeg,
+                               const double *__restrict__ L, int64_t n, ColDesc<XT> *__restrict__ desc,
+                               int32_t *__restrict__ prow, VT *__restrict__ pval)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t s = col_ptr[i], c = col_ptr[i + 1] - s, pb = pbeg[i];
+        for (int64_t p = 0; p < c; ++p) {
+            prow[pb + p] = row_idx[s + p];
+            pval[pb + p] = val[s + p];
+        }
+        ColDesc<XT> d;
+        d.pb4 = uint32_t(pb / 4);
+        d.cnt = int32_t(c);
+        d.invL = L[i] > 0.0 ? XT(1.0 / L[i]) : XT(0);
+        if constexpr (sizeof(XT) == 4) d.unused = 0.f;
+        desc[i] = d;
+    }
+}
+
 // Refresh: g64 += a_i x_i over the columns with x_i != 0, in FP64.
 template <int W, typename VT, typename XT>
-__global__ void __launch_bounds__(kBlock) k_refresh_cols(const int64_t *__restrict__ col_ptr,
-                                                         const int32_t *__restrict__ row_idx,
-                                                         const VT *__restrict__ val, const XT *__restrict__ x,
+__global__ void __launch_bounds__(kBlock) k_refresh_cols(const ColDesc<XT> *__restrict__ desc,
+                                                         const int32_t *__restrict__ prow,
+                                                         const VT *__restrict__ pval, const XT *__restrict__ x,
                                                          int64_t n, double *__restrict__ g64)
 {
+    constexpr int CH = W * kE;
     const int lane = threadIdx.x & (W - 1);
     const int64_t ngrp = int64_t(gridDim.x) * kBlock / W;
     for (int64_t i = (int64_t(blockIdx.x) * kBlock + threadIdx.x) / W; i < n; i += ngrp) {
         const double xi = double(__ldg(x + i));
         if (xi == 0.0) continue;
-        const int64_t beg = __ldg(col_ptr + i), end = __ldg(col_ptr + i + 1);
-        for (int64_t p = beg + lane; p < end; p += W) red_add(g64 + __ldg(row_idx + p), double(ldv(val + p)) * xi);
+        const Col<XT> c = load_col(desc, int32_t(i));
+        for (int cs = 0; cs < c.cnt; cs += CH) {
+            Chunk<kE, XT> t;
+            const int st = cs + lane * kE;
+            if (st >= c.cnt) continue;
+            ld_chunk<kE>(t, prow, pval, c.pbeg + st);
+            const int valid = c.cnt - st;
+#pragma unroll
+            for (int e = 0; e < kE; ++e)
+                if (e < valid) red_add(g64 + t.row[e], double(t.val[e]) * xi);
+        }
     }
 }
 
 // Gap, column part: c_i = a_i^T r in FP64; block partials of max|c_i|, sum|x_i|, sum x_i c_i.
 template <int W, typename VT, typename XT>
-__global__ void __launch_bounds__(kBlock) k_gap_cols(const int64_t *__restrict__ col_ptr,
-                                                     const int32_t *__restrict__ row_idx,
-                                                     const VT *__restrict__ val, const double *__restrict__ r,
+__global__ void __launch_bounds__(kBlock) k_gap_cols(const ColDesc<XT> *__restrict__ desc,
+                                                     const int32_t *__restrict__ prow,
+                                                     const VT *__restrict__ pval, const double *__restrict__ r,
                                                      const XT *__restrict__ x, int64_t n, double *__restrict__ part)
 {
+    constexpr int CH = W * kE;
     const int lane = threadIdx.x & (W - 1);
     const unsigned gmask = group_mask<W>(threadIdx.x & 31);
     const int64_t ngrp = int64_t(gridDim.x) * kBlock / W;
     double cmax = 0.0, l1 = 0.0, xc = 0.0;
     for (int64_t i = (int64_t(blockIdx.x) * kBlock + threadIdx.x) / W; i < n; i += ngrp) {
-        const int64_t beg = __ldg(col_ptr + i), end = __ldg(col_ptr + i + 1);
-        double c = 0.0;
-        for (int64_t p = beg + lane; p < end; p += W) c += double(ldv(val + p)) * __ldg(r + __ldg(row_idx + p));
-        c = group_sum<W>(c, gmask);
+        const Col<XT> c = load_col(desc, int32_t(i));
+        double acc = 0.0;
+        for (int cs = 0; cs < c.cnt; cs += CH) {
+            Chunk<kE, XT> t;
+            const int st = cs + lane * kE;
+            if (st < c.cnt) ld_chunk<kE>(t, prow, pval, c.pbeg + st);
+            acc += chunk_dot<kE, XT, double, double>(t, r, c.cnt - st);
+        }
+        acc = group_sum<W>(acc, gmask);
         if (lane == 0) {
             const double xi = double(__ldg(x + i));
-            cmax = fmax(cmax, fabs(c));
+            cmax = fmax(cmax, fabs(acc));
             l1 += fabs(xi);
-            xc += xi * c;
+            xc += xi * acc;
         }
     }
     __shared__ double sm[3][kBlock / 32];
@@ -240,14 +777,10 @@ __global__ void __launch_bounds__(kBlock) k_gap_cols(const int64_t *__restrict__
 
 // ---------------------------------------------------------------------------
 // Launchers.
-template <int W>
-static inline int64_t blocks_for_groups(int64_t groups)
-{
-    return (groups * W + kBlock - 1) / kBlock;
-}
-
 #define PCDM_DISPATCH_W(W, ...)                                    \
     switch (W) {                                                   \
+    case 1: { constexpr int W_ = 1; __VA_ARGS__; } break;          \
+    case 2: { constexpr int W_ = 2; __VA_ARGS__; } break;          \
     case 4: { constexpr int W_ = 4; __VA_ARGS__; } break;          \
     case 8: { constexpr int W_ = 8; __VA_ARGS__; } break;          \
     case 16: { constexpr int W_ = 16; __VA_ARGS__; } break;        \
@@ -255,14 +788,19 @@ static inline int64_t blocks_for_groups(int64_t groups)
     default: return cudaErrorInvalidValue;                         \
     }
 
+static inline unsigned blocks_for_threads(int64_t threads, int64_t cap)
+{
+    int64_t b = (threads + kBlock - 1) / kBlock;
+    if (b < 1) b = 1;
+    if (cap > 0 && b > cap) b = cap;
+    return unsigned(b);
+}
+
 template <typename VT, typename XT>
 cudaError_t Kernels<VT, XT>::gather(const IterArgs<VT, XT> &a, int W, int64_t k, cudaStream_t st)
 {
     if (a.tau <= 0) return cudaSuccess;
-    PCDM_DISPATCH_W(W, {
-        const int64_t blocks = blocks_for_groups<W_>(a.tau);
-        k_gather<W_, VT, XT><<<dim3(unsigned(blocks)), kBlock, 0, st>>>(a, k);
-    });
+    PCDM_DISPATCH_W(W, { k_gather<W_, VT, XT><<<blocks_for_threads(a.tau * W_, 0), kBlock, 0, st>>>(a, k); });
     return cudaGetLastError();
 }
 
@@ -271,24 +809,25 @@ cudaError_t Kernels<VT, XT>::scatter(const IterArgs<VT, XT> &a, int W, int64_t k
 {
     if (a.tau <= 0) return cudaSuccess;
     PCDM_DISPATCH_W(W, {
-        const int64_t blocks = blocks_for_groups<W_>(a.tau);
-        k_scatter<W_, VT, XT><<<dim3(unsigned(blocks)), kBlock, 0, st>>>(a, k, sample_next ? 1 : 0);
+        k_scatter<W_, VT, XT><<<blocks_for_threads(a.tau * W_, 0), kBlock, 0, st>>>(a, k, sample_next ? 1 : 0);
     });
     return cudaGetLastError();
 }
 
 template <typename VT, typename XT>
-int Kernels<VT, XT>::fused_max_blocks(int W)
+int Kernels<VT, XT>::fused_max_blocks(int W, int threads)
 {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (W) {
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<4, VT, XT>, kBlock, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<8, VT, XT>, kBlock, 0); break;
-    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<16, VT, XT>, kBlock, 0); break;
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<32, VT, XT>, kBlock, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<1, VT, XT>, threads, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<2, VT, XT>, threads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<4, VT, XT>, threads, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<8, VT, XT>, threads, 0); break;
+    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<16, VT, XT>, threads, 0); break;
+    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<32, VT, XT>, threads, 0); break;
     default: return 0;
     }
     if (e != cudaSuccess) return 0;
@@ -296,17 +835,43 @@ int Kernels<VT, XT>::fused_max_blocks(int W)
 }
 
 template <typename VT, typename XT>
-cudaError_t Kernels<VT, XT>::fused(const IterArgs<VT, XT> &a, int W, int64_t k0, int64_t iters, int blocks,
+cudaError_t Kernels<VT, XT>::fused(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
                                    cudaStream_t st)
 {
     if (iters <= 0 || a.tau <= 0) return cudaSuccess;
     IterArgs<VT, XT> args = a;
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
-    PCDM_DISPATCH_W(W, {
-        return cudaLaunchCooperativeKernel((const void *)k_fused<W_, VT, XT>, dim3(unsigned(blocks)), dim3(kBlock),
-                                           params, 0, st);
+    PCDM_DISPATCH_W(sh.W, {
+        return cudaLaunchCooperativeKernel((const void *)k_fused<W_, VT, XT>, dim3(unsigned(sh.blocks)),
+                                           dim3(unsigned(sh.threads)), params, 0, st);
     });
     return cudaErrorInvalidValue;
+}
+
+template <typename VT, typename XT>
+int Kernels<VT, XT>::pipe_max_blocks(int threads)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const size_t bytes = pipe_smem_bytes<VT>(threads);
+    if (cudaFuncSetAttribute(k_fused_pipe<VT, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) !=
+        cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_pipe<VT, XT>, threads, bytes) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+template <typename VT, typename XT>
+cudaError_t Kernels<VT, XT>::fused_pipe(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
+                                        cudaStream_t st)
+{
+    if (iters <= 0 || a.tau <= 0) return cudaSuccess;
+    IterArgs<VT, XT> args = a;
+    void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
+    return cudaLaunchCooperativeKernel((const void *)k_fused_pipe<VT, XT>, dim3(unsigned(sh.blocks)),
+                                       dim3(unsigned(sh.threads)), params, pipe_smem_bytes<VT>(sh.threads), st);
 }
 
 template <typename VT, typename XT>
@@ -314,31 +879,40 @@ cudaError_t Kernels<VT, XT>::setup_cols(const int64_t *col_ptr, const int32_t *r
                                         int64_t n, double *L, int *rowcnt, int *flags, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 65535 * 8) blocks = 65535 * 8;
-    k_setup_cols<VT><<<dim3(unsigned(blocks)), 256, 0, st>>>(col_ptr, row_idx, val, m, n, L, rowcnt, flags);
+    k_setup_cols<VT><<<blocks_for_threads(n, 152 * 64), kBlock, 0, st>>>(col_ptr, row_idx, val, m, n, L, rowcnt,
+                                                                          flags);
     return cudaGetLastError();
 }
 
 template <typename VT, typename XT>
-cudaError_t Kernels<VT, XT>::refresh_cols(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, const XT *x,
+cudaError_t Kernels<VT, XT>::build_layout(const int64_t *col_ptr, const int32_t *row_idx, const VT *val,
+                                          const int64_t *pbeg, const double *L, int64_t n, ColDesc<XT> *desc,
+                                          int32_t *prow, VT *pval, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_build_layout<VT, XT><<<blocks_for_threads(n, 152 * 64), kBlock, 0, st>>>(col_ptr, row_idx, val, pbeg, L, n,
+                                                                                desc, prow, pval);
+    return cudaGetLastError();
+}
+
+template <typename VT, typename XT>
+cudaError_t Kernels<VT, XT>::refresh_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const XT *x,
                                           int64_t n, double *g64, int W, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     PCDM_DISPATCH_W(W, {
-        int64_t blocks = blocks_for_groups<W_>(n);
-        if (blocks > 152 * 64) blocks = 152 * 64;
-        k_refresh_cols<W_, VT, XT><<<dim3(unsigned(blocks)), kBlock, 0, st>>>(col_ptr, row_idx, val, x, n, g64);
+        k_refresh_cols<W_, VT, XT><<<blocks_for_threads(n * W_, 152 * 16), kBlock, 0, st>>>(desc, prow, pval, x,
+                                                                                              n, g64);
     });
     return cudaGetLastError();
 }
 
 template <typename VT, typename XT>
-cudaError_t Kernels<VT, XT>::gap_cols(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, const double *r,
+cudaError_t Kernels<VT, XT>::gap_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *r,
                                       const XT *x, int64_t n, double *part, int blocks, int W, cudaStream_t st)
 {
     PCDM_DISPATCH_W(W, {
-        k_gap_cols<W_, VT, XT><<<dim3(unsigned(blocks)), kBlock, 0, st>>>(col_ptr, row_idx, val, r, x, n, part);
+        k_gap_cols<W_, VT, XT><<<dim3(unsigned(blocks)), kBlock, 0, st>>>(desc, prow, pval, r, x, n, part);
     });
     return cudaGetLastError();
 }
