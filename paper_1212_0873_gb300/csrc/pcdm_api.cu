@@ -52,6 +52,8 @@ struct pcdm_ctx {
     double *L64 = nullptr;        // L_i in FP64
     void *x = nullptr;            // n entries of xg dtype
     void *g = nullptr;            // m entries of xg dtype
+    void *g2 = nullptr;           // second residual buffer of the pipelined kernel
+    bool g2_valid = false;        // g2 holds the same residual as g
     double *g64 = nullptr;        // FP64 residual of the refresh (aliases g in the FP64 form)
     int32_t *S[2] = {nullptr, nullptr};
     void *h = nullptr;
@@ -124,7 +126,7 @@ cudaError_t dalloc_bytes(void **p, int64_t bytes)
 
 void free_all(pcdm_handle h)
 {
-    void *ptrs[] = {h->desc, h->prow, h->pval, h->b, h->L64, h->x, h->g,
+    void *ptrs[] = {h->desc, h->prow, h->pval, h->b, h->L64, h->x, h->g, h->g2,
                     h->S[0], h->S[1], h->h, h->counters, h->bar, h->status, h->gap_part, h->gap_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -222,6 +224,7 @@ IterArgs<VT, XT> iter_args(pcdm_handle h, int64_t tau, uint64_t seed)
     a.pval = static_cast<const VT *>(h->pval);
     a.x = static_cast<XT *>(h->x);
     a.g = static_cast<XT *>(h->g);
+    a.g2 = static_cast<XT *>(h->g2);
     a.h = static_cast<XT *>(h->h);
     a.S[0] = h->S[0];
     a.S[1] = h->S[1];
@@ -296,11 +299,21 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
         if (pipe_shape<VT, XT>(h, tau, &sh)) {
+            const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
+            if (!h->g2) {
+                CK(h, cudaStreamSynchronize(h->stream));
+                CK(h, dalloc_bytes(&h->g2, int64_t(gbytes)));
+                a.g2 = static_cast<XT *>(h->g2);
+                h->g2_valid = false;
+            }
+            if (!h->g2_valid) CK(h, cudaMemcpyAsync(h->g2, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
             CK(h, Kernels<VT, XT>::fused_pipe(a, sh, h->k, iters, h->stream));
+            h->g2_valid = true;
         } else {
             pcdm_status s = fused_shape<VT, XT>(h, tau, &sh);
             if (s != PCDM_OK) return s;
             CK(h, Kernels<VT, XT>::fused(a, sh, h->k, iters, h->stream));
+            h->g2_valid = false;
         }
         h->st_launches += 1;
         h->st_kernels += 1;
@@ -310,6 +323,7 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
             CK(h, Kernels<VT, XT>::gather(a, h->W, kk, h->stream));
             CK(h, Kernels<VT, XT>::scatter(a, h->W, kk, true, h->stream));
         }
+        h->g2_valid = false;
         h->st_launches += iters;
         h->st_kernels += 2 * iters;
     }
@@ -336,6 +350,7 @@ pcdm_status refresh_t(pcdm_handle h)
                                         static_cast<const VT *>(h->pval), static_cast<const XT *>(h->x), h->n,
                                         target, h->W, h->stream));
     if (sizeof(XT) == 4) CK(h, launch_store_from_f64<float>(static_cast<float *>(h->g), target, h->m, h->stream));
+    h->g2_valid = false;
     h->st_refreshes += 1;
     h->st_kernels += sizeof(XT) == 4 ? 3 : 2;
     return PCDM_OK;
@@ -405,6 +420,7 @@ pcdm_status reset_state(pcdm_handle h)
     else
         CK(h, launch_neg_store<float>(static_cast<float *>(h->g), h->b, h->m, h->stream));
     CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    h->g2_valid = false;
     h->st_kernels += 1;   // the g = -b kernel
     h->k = 0;
     h->sample_valid = false;

@@ -152,6 +152,65 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------------------
+// TMA bulk copies global -> shared with mbarrier completion (sm_90+).  Source
+// and destination 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+
+// Makes mbarrier initialisations visible to the async proxy (TMA completions).
+__device__ __forceinline__ void fence_mbarrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the given phase of an mbarrier, bounded by timeout_ns; on expiry the
+// status word records a timeout and false is returned.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, int *status, uint64_t timeout_ns);
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Value loads (read-only data: non-coherent path is safe).
 __device__ __forceinline__ double ldv(const double *p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const float *p) { return __ldg(p); }
@@ -243,6 +302,8 @@ __device__ __forceinline__ int ld_volatile_int(const int *p) { return *reinterpr
 __device__ __forceinline__ bool wait_counter(unsigned long long *counter, unsigned long long target, int *status,
                                              uint64_t timeout_ns)
 {
+    // The acquire load that sees the target orders every later access of this
+    // thread (and, through the block barrier that follows, of its block).
     int ok = 1;
     const uint64_t t0 = global_ns();
     uint32_t spins = 0;
@@ -257,7 +318,6 @@ __device__ __forceinline__ bool wait_counter(unsigned long long *counter, unsign
             break;
         }
     }
-    __threadfence();
     return ok != 0;
 }
 
@@ -269,10 +329,11 @@ __device__ __forceinline__ bool grid_sync(unsigned long long *counter, unsigned 
         __syncthreads();
         return true;
     }
+    // The block barrier orders the block's accesses before thread 0's release
+    // add, which publishes them at GPU scope.
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         red_release_add_u64(counter, 1ull);
         s_ok = wait_counter(counter, target, status, timeout_ns) ? 1 : 0;
     }
@@ -289,10 +350,7 @@ __device__ __forceinline__ void grid_arrive(unsigned long long *counter)
         return;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        red_release_add_u64(counter, 1ull);
-    }
+    if (threadIdx.x == 0) red_release_add_u64(counter, 1ull);
 }
 
 __device__ __forceinline__ bool grid_wait(unsigned long long *counter, unsigned long long target, int *status,
@@ -303,6 +361,23 @@ __device__ __forceinline__ bool grid_wait(unsigned long long *counter, unsigned 
     if (threadIdx.x == 0) s_ok2 = wait_counter(counter, target, status, timeout_ns) ? 1 : 0;
     __syncthreads();
     return s_ok2 != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, int *status, uint64_t timeout_ns)
+{
+    if (mbar_try_wait(mbar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    uint32_t spins = 0;
+    while (!mbar_try_wait(mbar, parity)) {
+        if ((++spins & 15u) == 0u) {
+            if (ld_volatile_int(status) != DEV_OK) return false;
+            if (global_ns() - t0 > timeout_ns) {
+                atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
 }
 
 // Asynchronous prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16).

@@ -62,6 +62,7 @@ struct IterArgs {
     const VT *pval;
     XT *x;
     XT *g;
+    XT *g2;                     // second residual buffer of the pipelined kernel (equal to g at launch)
     XT *h;                      // h[j] = step of coordinate S_k[j]
     int32_t *S[2];              // S_k lives in S[k & 1]
     XT inv_beta, lambda;

@@ -368,56 +368,26 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
 
 // ---------------------------------------------------------------------------
 // Pipelined persistent form: one lane per column, every sampled position owned
-// by one thread (tau <= threads of the grid).  Thread j keeps i_k and i_{k+1}
-// with their descriptors in registers; the first kE entries of column i_k sit in
-// shared-memory buffer (it & 1).  Per iteration k:
-//   phase 1  the gathers of g at the chunk's rows (and the start of the column's
-//            tail) are issued; the sample i_{k+2} is drawn (integer work) while
-//            they are in flight and its descriptor load is issued; then
-//            gradient, step, x;
-//   barrier
-//   phase 2  the warp copies the first chunks of its 32 columns i_{k+1} into the
-//            other buffer with cp.async, consecutive lanes taking consecutive
-//            16-byte pieces of the same column (coalesced), and prefetches their
-//            tails into L2; then the scatter of column i_k (h != 0) from the
-//            current buffer;
-//   barrier
-// On GB300 the scattered gathers of phase 1 saturate each SM's load/store
-// pipe, so everything else that uses it (bulk copies, shuffles, shared-memory
-// traffic) is kept out of phase 1.
-template <typename VT, typename XT>
-__device__ __forceinline__ void smem_vals(XT (&v)[kE], const uint4 *p, int stride)
-{
-    if constexpr (sizeof(VT) == 8) {
-#pragma unroll
-        for (int w = 0; w < kE / 2; ++w) {
-            const uint4 u = p[w * stride];
-            v[2 * w + 0] = XT(__hiloint2double(int(u.y), int(u.x)));
-            v[2 * w + 1] = XT(__hiloint2double(int(u.w), int(u.z)));
-        }
-    } else if constexpr (sizeof(VT) == 4) {
-#pragma unroll
-        for (int w = 0; w < kE / 4; ++w) {
-            const uint4 u = p[w * stride];
-            v[4 * w + 0] = XT(__uint_as_float(u.x));
-            v[4 * w + 1] = XT(__uint_as_float(u.y));
-            v[4 * w + 2] = XT(__uint_as_float(u.z));
-            v[4 * w + 3] = XT(__uint_as_float(u.w));
-        }
-    } else {
-#pragma unroll
-        for (int w = 0; w < kE / 8; ++w) {
-            const uint4 u = p[w * stride];
-            const uint32_t q[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                v[8 * w + 2 * t + 0] = XT(__uint_as_float(q[t] << 16));
-                v[8 * w + 2 * t + 1] = XT(__uint_as_float(q[t] & 0xFFFF0000u));
-            }
-        }
-    }
-}
-
+// by one thread (tau <= threads of the grid), one grid barrier per iteration.
+// The residual lives in two buffers: at iteration k, buffer k&1 holds g_k and is
+// only read (gathers), the other holds g_{k-1} and only receives atomic adds:
+// the steps of iteration k-1 (it missed them) and of iteration k.  So the
+// scatter of iteration k never touches what the gathers of iteration k read,
+// the update stays Jacobi, and only the barrier that publishes g_{k+1} remains.
+// Both buffers hold the same residual at every launch boundary.
+// Thread j keeps i_k and i_{k+1} with their descriptors in registers; the first
+// kE entries of column i_k sit in the thread's slot of shared-memory buffer
+// (it & 1), brought in by TMA bulk copies during the previous iteration
+// (completion on an mbarrier).  Per iteration k:
+//   gather   the gathers of g_k at the chunk's rows (and the start of the
+//            column's tail) are issued; the sample i_{k+2} is drawn (integer
+//            work) while they are in flight and its descriptor load is issued;
+//            then gradient, step, x;
+//   scatter  steps of k-1 and k into the other buffer;
+//   barrier  release-arrive; then TMA copies of the first chunk of column i_{k+1}
+//            into the other slot and L2 prefetch of its tail; then wait
+// On GB300 the scattered gathers saturate each SM's load/store pipe, so the
+// bulk copies run on the TMA engine and the sampling is integer work only.
 // Values of one 16-byte word of a shared chunk (16 / sizeof(VT) entries).
 template <typename VT, typename XT>
 __device__ __forceinline__ void decode_word(const uint4 u, XT (&v)[16 / sizeof(VT)])
@@ -446,10 +416,50 @@ __host__ __device__ constexpr int pipe_value_words()
     return kLaneRun * int(sizeof(VT)) / 16;
 }
 
+// Shared-memory slot of one thread: kE row indices, kE values, 16 bytes of
+// padding (with it, the 128-bit loads of 8 consecutive threads hit distinct banks).
+template <typename VT>
+__host__ __device__ constexpr int pipe_slot_bytes()
+{
+    return 16 * (4 + pipe_value_words<VT>()) + 16;
+}
+
 template <typename VT>
 __host__ __device__ constexpr size_t pipe_smem_bytes(int threads)
 {
-    return size_t(2) * size_t(threads) * 16 * size_t(4 + pipe_value_words<VT>());
+    return size_t(2) * size_t(threads) * size_t(pipe_slot_bytes<VT>()) + 16;
+}
+
+// Scatter of one column's first chunk (from a shared slot) and of its tail
+// (from memory) into g: g_r += a_ri * h.
+template <typename VT, typename XT>
+__device__ __forceinline__ void slot_scatter(const IterArgs<VT, XT> &a, const unsigned char *slot, const Col<XT> &d,
+                                             XT h, XT *g)
+{
+    constexpr int VW = pipe_value_words<VT>();
+    constexpr int EPW = 16 / int(sizeof(VT));
+    int32_t row[kE];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 r4 = reinterpret_cast<const uint4 *>(slot)[q];
+        row[4 * q + 0] = int32_t(r4.x);
+        row[4 * q + 1] = int32_t(r4.y);
+        row[4 * q + 2] = int32_t(r4.z);
+        row[4 * q + 3] = int32_t(r4.w);
+    }
+#pragma unroll
+    for (int w = 0; w < VW; ++w) {
+        XT vw[EPW];
+        decode_word<VT, XT>(reinterpret_cast<const uint4 *>(slot + 64)[w], vw);
+#pragma unroll
+        for (int q = 0; q < EPW; ++q)
+            if (w * EPW + q < d.cnt) red_add(g + row[w * EPW + q], vw[q] * h);
+    }
+    for (int cs = kE; cs < d.cnt; cs += kE) {
+        Chunk<kE, XT> t;
+        ld_chunk<kE>(t, a.prow, a.pval, d.pbeg + cs);
+        chunk_scatter<kE>(t, g, h, d.cnt - cs);
+    }
 }
 
 template <typename VT, typename XT>
@@ -457,69 +467,72 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int VW = pipe_value_words<VT>();
-    constexpr int PIECES = 4 + VW;                        // 16-byte pieces of one chunk
+    constexpr int SB = pipe_slot_bytes<VT>();
+    constexpr int G = pad_granule<VT>();
     const int nt = blockDim.x, t = threadIdx.x;
-    const int lane = t & 31, wbase = t & ~31;
-    const size_t buf_bytes = size_t(nt) * 16 * size_t(PIECES);
     const int64_t j0 = int64_t(blockIdx.x) * nt + t;
     const bool own = j0 < a.tau;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + size_t(2) * nt * SB);
     unsigned long long target = 0;
+    uint32_t phase = 0;   // bit b: parity of the next completion of mbar[b]
     Counters cnt;
 
-    // piece q of thread tt's chunk in buffer b (rows first, then values)
-    auto piece_at = [&](int b, int q, int tt) {
-        return reinterpret_cast<uint4 *>(smem + size_t(b) * buf_bytes) + size_t(q) * nt + tt;
-    };
-    // The warp copies the chunks of its 32 columns (descriptor of the calling
-    // lane = its own next column; cnt 0 means nothing to copy).
-    auto copy_warp_chunks = [&](int b, const Col<XT> &d) {
-        const uint32_t pb_lo = uint32_t(d.pbeg), pb_hi = uint32_t(uint64_t(d.pbeg) >> 32);
-        for (int p = lane; p < 32 * PIECES; p += 32) {
-            const int c = p / PIECES, q = p - c * PIECES;
-            const int64_t pb = int64_t((uint64_t(__shfl_sync(0xFFFFFFFFu, pb_hi, c)) << 32) |
-                                       __shfl_sync(0xFFFFFFFFu, pb_lo, c));
-            const int cc = __shfl_sync(0xFFFFFFFFu, d.cnt, c);
-            if (cc <= 0) continue;
-            const uint4 *src = q < 4 ? reinterpret_cast<const uint4 *>(a.prow + pb) + q
-                                     : reinterpret_cast<const uint4 *>(a.pval + pb) + (q - 4);
-            cp_async16(piece_at(b, q, wbase + c), src);
+    auto slot = [&](int b) { return smem + (size_t(b) * nt + t) * SB; };
+    // the residual buffer that holds g_k at iteration k
+    auto gbuf = [&](int64_t kk) { return (kk & 1) ? a.g2 : a.g; };
+    // This thread's share of filling buffer b: arrive on mbar[b] and, for a
+    // non-empty column, bulk-copy its first chunk (rows, then values).
+    auto fill = [&](int b, const Col<XT> &d, bool mine) {
+        if (mine && d.cnt > 0) {
+            const int64_t pc = (int64_t(d.cnt) + G - 1) / G * G;
+            const uint32_t e = uint32_t(pc < kE ? pc : kE);
+            const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
+            mbar_arrive_expect_tx(&mbar[b], br + bv);
+            bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b]);
+            bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b]);
+        } else {
+            mbar_arrive(&mbar[b]);
         }
-        cp_async_commit();
     };
-    auto own_col = [&](const Col<XT> &d) {
-        Col<XT> z = d;
-        if (!own) z.cnt = 0;
-        return z;
+    auto wait_buf = [&](int b) {
+        const bool ok = mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, a.status, a.timeout_ns);
+        phase ^= 1u << b;
+        return ok;
     };
+
+    if (t == 0) {
+        mbar_init(&mbar[0], uint32_t(nt));
+        mbar_init(&mbar[1], uint32_t(nt));
+        fence_mbarrier_init();
+    }
+    __syncthreads();
 
     // Prologue: i_{k0} (drawn by the caller) and its chunk; i_{k0+1} and its descriptor.
     int32_t i_cur = 0, i_nxt = 0;
-    Col<XT> d_cur, d_nxt;
-    d_cur.pbeg = d_nxt.pbeg = 0;
-    d_cur.cnt = d_nxt.cnt = 0;
-    d_cur.invL = d_nxt.invL = XT(0);
-    {
-        const SampleKey key1 = warp_sample_key(a.seed, k0 + 1, a.n);
-        if (own) {
-            i_cur = ldcg(sample_buf(a, k0) + j0);
-            d_cur = load_col(a.desc, i_cur);
-            i_nxt = sample_index(uint32_t(j0), key1);
-            d_nxt = load_col(a.desc, i_nxt);
-        }
+    Col<XT> d_cur, d_nxt, d_prev;
+    d_cur.pbeg = d_nxt.pbeg = d_prev.pbeg = 0;
+    d_cur.cnt = d_nxt.cnt = d_prev.cnt = 0;
+    d_cur.invL = d_nxt.invL = d_prev.invL = XT(0);
+    XT h_prev = XT(0);   // the step of the previous iteration's column (still owed to one buffer)
+    if (own) {
+        i_cur = ldcg(sample_buf(a, k0) + j0);
+        d_cur = load_col(a.desc, i_cur);
+        i_nxt = sample_index(uint32_t(j0), make_sample_key(a.seed, k0 + 1, a.n));
+        d_nxt = load_col(a.desc, i_nxt);
     }
-    copy_warp_chunks(0, own_col(d_cur));
-    cp_async_wait<0>();
-    __syncwarp();
+    fill(0, d_cur, own);
 
     constexpr int kT = kE / 2;   // tail entries [kE, kE + kT) fetched early into registers
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t k = k0 + it;
         const int b = int(it & 1);
-        // the chunks of this iteration's columns, copied during the previous phase 2
-        cp_async_wait<0>();
-        __syncwarp();
+        // the chunks of this iteration's columns (filled during the previous iteration)
+        if (!wait_buf(b)) return;
+        const unsigned char *my = slot(b);
+        const XT *gk = gbuf(k);
+        XT *gn = gbuf(k + 1);
 
-        // ---------------- phase 1: gradient, step, x update
+        // ---------------- gather, step, x update (reads g_k)
         // The loads go first (x_i, the gathers of g at the chunk's rows, the start
         // of the column's tail); the sample of k+2 (integer work only: no
         // shuffles or shared-memory traffic, which would queue behind the loads)
@@ -533,7 +546,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
             int32_t row[kE];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint4 r4 = *piece_at(b, q, t);
+                const uint4 r4 = reinterpret_cast<const uint4 *>(my)[q];
                 row[4 * q + 0] = int32_t(r4.x);
                 row[4 * q + 1] = int32_t(r4.y);
                 row[4 * q + 2] = int32_t(r4.z);
@@ -541,20 +554,20 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
             }
             XT gv[kE];
 #pragma unroll
-            for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg(a.g + row[e]) : XT(0);
+            for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg(gk + row[e]) : XT(0);
             Chunk<kT, XT> tl;
             if (valid > kE) ld_chunk<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE);
             i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
             d_nn = load_col(a.desc, i_nn);
             XT gt[kT];
 #pragma unroll
-            for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg(a.g + tl.row[e]) : XT(0);
+            for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg(gk + tl.row[e]) : XT(0);
             constexpr int EPW = 16 / int(sizeof(VT));
             XT acc = XT(0);
 #pragma unroll
             for (int w = 0; w < VW; ++w) {
                 XT vw[EPW];
-                decode_word<VT, XT>(*piece_at(b, 4 + w, t), vw);
+                decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
 #pragma unroll
                 for (int q = 0; q < EPW; ++q)
                     if (w * EPW + q < valid) acc = fma(vw[q], gv[w * EPW + q], acc);
@@ -565,7 +578,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
             for (int cs = kE + kT; cs < valid; cs += kE) {
                 Chunk<kE, XT> tc;
                 ld_chunk<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs);
-                acc += chunk_dot<kE, XT, XT, XT>(tc, a.g, valid - cs);
+                acc += chunk_dot<kE, XT, XT, XT>(tc, gk, valid - cs);
             }
             const XT xn = prox_step<XT>(xi, acc, d_cur.invL, a.inv_beta, a.lambda);
             h = xn - xi;
@@ -576,47 +589,32 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                 cnt.scattered += (unsigned long long)valid;
             }
         }
-        target += gridDim.x;
-        if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) {
-            cp_async_wait<0>();
-            return;
-        }
 
-        // ---------------- phase 2: next columns' chunks stream in; residual update
-        // The memory pipe is otherwise idle here: the copies of the chunks of
-        // i_{k+1} into the other buffer (coalesced across the warp) and the L2
-        // prefetch of their tails run through phase 2 and the barrier.
-        copy_warp_chunks(b ^ 1, own_col(d_nxt));
+        // ---------------- scatter into the other buffer (g_{k-1} -> g_{k+1})
+        // No barrier is needed before it: every gather of iteration k reads g_k,
+        // which nobody writes during iteration k.  The other buffer holds g_{k-1}
+        // and receives the steps of iterations k-1 and k.  The previous column's
+        // chunk sits in slot b^1, so it is re-scattered before that slot is refilled.
+        if (own && h_prev != XT(0)) slot_scatter<VT, XT>(a, slot(b ^ 1), d_prev, h_prev, gn);
+        if (own && h != XT(0)) slot_scatter<VT, XT>(a, my, d_cur, h, gn);
+        h_prev = h;
+        d_prev = d_cur;
+
+        // ---------------- the only grid barrier of the iteration: g_{k+1} complete
+        // Split: the release-arrive publishes x and the scatter; the bulk copies of
+        // the next columns (reads of A only, nothing to publish) are issued after
+        // it, so the release does not wait for them, and they overlap the wait.
+        target += gridDim.x;
+        grid_arrive(a.bar);
+        fence_proxy_async_shared();
+        fill(b ^ 1, d_nxt, own);
         if (own && d_nxt.cnt > kE) {
-            constexpr int G = pad_granule<VT>();
             const int64_t tail = ((int64_t(d_nxt.cnt) + G - 1) / G) * G - kE;
             prefetch_l2_bulk(a.prow + d_nxt.pbeg + kE, uint32_t(tail * 4));
             prefetch_l2_bulk(a.pval + d_nxt.pbeg + kE, uint32_t(tail * int64_t(sizeof(VT))));
         }
-        if (own && h != XT(0)) {
-            int32_t row[kE];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 r4 = *piece_at(b, q, t);
-                row[4 * q + 0] = int32_t(r4.x);
-                row[4 * q + 1] = int32_t(r4.y);
-                row[4 * q + 2] = int32_t(r4.z);
-                row[4 * q + 3] = int32_t(r4.w);
-            }
-            constexpr int EPW = 16 / int(sizeof(VT));
-#pragma unroll
-            for (int w = 0; w < VW; ++w) {
-                XT vw[EPW];
-                decode_word<VT, XT>(*piece_at(b, 4 + w, t), vw);
-#pragma unroll
-                for (int q = 0; q < EPW; ++q)
-                    if (w * EPW + q < valid) red_add(a.g + row[w * EPW + q], vw[q] * h);
-            }
-            column_scatter<1>(a, d_cur, 0, h, kE);
-        }
-        target += gridDim.x;
-        if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) {
-            cp_async_wait<0>();
+        if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) {
+            wait_buf(b ^ 1);   // the copies just issued land before the block leaves
             return;
         }
         i_cur = i_nxt;
@@ -624,7 +622,12 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         i_nxt = i_nn;
         d_nxt = d_nn;
     }
-    cp_async_wait<0>();
+    // Both buffers equal again: the last iteration's steps (still in slot
+    // (iters-1)&1) go into the buffer that holds g_{k0+iters-1}.
+    if (iters > 0 && own && h_prev != XT(0))
+        slot_scatter<VT, XT>(a, slot(int((iters - 1) & 1)), d_prev, h_prev, gbuf(k0 + iters - 1));
+    // the last fill (the chunks of i_{k0+iters}) lands before the block leaves
+    wait_buf(int(iters & 1));
     // S_{k0+iters} for the caller (the sample of the next launch).
     if (own) sample_buf(a, k0 + iters)[j0] = i_cur;
     flush_counters(cnt, a.counters);
