@@ -290,10 +290,13 @@ def run_pcdm(a, rank, local, world):
     value, max_seconds, _ = aggregate(local_updates, local_seconds, world)
 
     # roofline of the fused iteration kernel
-    sv, sx = st["val_bytes"], st["xg_bytes"]
-    sidx, sL = 4, sx
-    alg_bytes = (st["gathered_nnz"] * (sv + sidx + sx) + st["updates"] * (2 * sx + sL + 8)
-                 + st["scattered_nnz"] * (sv + sidx + 2 * sx))
+    # algorithmic bytes: per gathered nonzero value + row index + g_r; per update
+    # x_i read and write (FP64), 1/L_i and the column's start and length; per
+    # scattered nonzero value + row index + read and write of g_r
+    sv, sg, sx = st["val_bytes"], st["xg_bytes"], 8
+    sidx, sL = 4, sg
+    alg_bytes = (st["gathered_nnz"] * (sv + sidx + sg) + st["updates"] * (2 * sx + sL + 8)
+                 + st["scattered_nnz"] * (sv + sidx + 2 * sg))
     launches = max(st["iter_launches"], 1)
     avg_launch_s = st["iter_kernel_ms"] / launches / 1e3
     achieved = alg_bytes / launches / avg_launch_s / 1e9 if avg_launch_s > 0 else None

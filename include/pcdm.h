@@ -69,17 +69,19 @@ typedef struct {
 /*
  * Options.  Fill with pcdm_default_opts and change what you need.
  * Precision pairs (val_dtype, xg_dtype): (F64, F64), (F32, F32), (BF16, F32).
- * The FP32 forms accumulate gradients in FP32; the residual refresh and the
- * duality gap are always computed in FP64.
+ * The FP32 forms keep g in FP32 and accumulate gradients in FP32; x and the
+ * proximal step are FP64 in every pair (an FP32 x alone bounds the reachable
+ * relative duality gap near 1e-6); the residual refresh and the duality gap are
+ * always computed in FP64.
  */
 typedef struct {
-    int32_t xg_dtype;            /* dtype of x, g and the gradient accumulator: PCDM_F64 or PCDM_F32 */
+    int32_t xg_dtype;            /* dtype of g and the gradient accumulator: PCDM_F64 or PCDM_F32 */
     int32_t fused;               /* 1: one persistent cooperative kernel per run of iterations,
                                     0: two kernels per iteration (gather/prox, scatter)          */
     int64_t refresh_every;       /* after iteration k with (k+1) % refresh_every == 0, recompute
                                     g = A x - b in FP64 (0: only when pcdm_gap runs)            */
     int64_t check_every;         /* pcdm_solve: iterations between duality-gap checks
-                                    (0: one epoch, ceil(n / tau))                               */
+                                    (0: adaptive, see pcdm_next_check_interval)                 */
     int64_t lanes_per_col;       /* threads that share one column: 0 (auto), 4, 8, 16 or 32     */
     uint64_t barrier_timeout_ns; /* bound on every grid-barrier wait of the fused kernel          */
     int32_t profile;             /* 1: time every iteration-kernel launch with CUDA events        */
@@ -98,7 +100,7 @@ typedef struct {
     int64_t refreshes;         /* FP64 residual refreshes */
     int64_t gaps;              /* duality-gap evaluations */
     int64_t val_bytes;         /* bytes of one stored value */
-    int64_t xg_bytes;          /* bytes of one x or g entry */
+    int64_t xg_bytes;          /* bytes of one g entry (x entries are 8-byte doubles) */
     int64_t kernel_launches;   /* every kernel this handle launched (all phases) */
 } pcdm_stats;
 
@@ -150,17 +152,34 @@ pcdm_status pcdm_gap(pcdm_handle h, double *primal, double *dual, double *gap);
 
 /*
  * Iterate until gap / primal <= rel_gap_tol: check the gap first, then run
- * chunks of opts.check_every iterations (one epoch when 0), checking after each.
- * iters_done and rel_gap (either may be NULL) receive the iterations run and
- * the last relative gap.  Returns PCDM_ENOTCONV when max_iters ran out first.
+ * chunks of iterations, checking after each: opts.check_every iterations when
+ * it is positive, else the adaptive schedule of pcdm_next_check_interval (the
+ * first chunk one epoch, ceil(n / tau) iterations).  The gap check is not part
+ * of Algorithm 1; it is the stopping test.  iters_done and rel_gap (either may
+ * be NULL) receive the iterations run and the last relative gap.  Returns
+ * PCDM_ENOTCONV when max_iters ran out first.
  */
 pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap_tol, int64_t max_iters,
                        int64_t *iters_done, double *rel_gap);
 
-/* Copy x (n entries of xg_dtype) to host (on_device = 0) or device memory. */
+/*
+ * The adaptive gap-check schedule of pcdm_solve (host arithmetic only; needs no
+ * handle and no device).  After checks at iterations k_prev and k_cur with
+ * relative gaps rel_prev > rel_cur > rel_gap_tol, the rate of the last interval,
+ * log(rel_prev / rel_cur) / (k_cur - k_prev), is extrapolated to the tolerance
+ * with a 5% margin; the result is clamped to [ceil(epoch / 4), 8 epoch] and to
+ * twice the last interval.  Without a decrease (or with a non-positive input) it
+ * returns epoch.  A gap evaluation is a full FP64 pass over A, costing about as
+ * much as 20 iterations at tau = 65536, so fewer checks near the end of a solve
+ * save time; overshooting the tolerance costs at most the margin.
+ */
+int64_t pcdm_next_check_interval(int64_t epoch, int64_t k_prev, double rel_prev, int64_t k_cur, double rel_cur,
+                                 double rel_gap_tol);
+
+/* Copy x (n doubles) to host (on_device = 0) or device memory. */
 pcdm_status pcdm_get_x(pcdm_handle h, void *x_out, int32_t on_device);
 
-/* Replace x (n entries of xg_dtype, host or device) and recompute g = A x - b (warm start). */
+/* Replace x (n doubles, host or device) and recompute g = A x - b (warm start). */
 pcdm_status pcdm_set_x(pcdm_handle h, const void *x_in, int32_t on_device);
 
 /* Copy the maintained residual g (m entries of xg_dtype) to host or device memory. */

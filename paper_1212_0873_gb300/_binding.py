@@ -44,6 +44,7 @@ SIGNATURES = {
     "pcdm_refresh": (_i32, [_ptr]),
     "pcdm_gap": (_i32, [_ptr, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
     "pcdm_solve": (_i32, [_ptr, _i64, _u64, _dbl, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
+    "pcdm_next_check_interval": (_i64, [_i64, _i64, ctypes.c_double, _i64, ctypes.c_double, ctypes.c_double]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -220,3 +221,8 @@ def pcdm_last_error(h=None):
 
 def pcdm_status_string(status):
     return lib().pcdm_status_string(int(status)).decode()
+
+
+def pcdm_next_check_interval(epoch, k_prev, rel_prev, k_cur, rel_cur, rel_gap_tol):
+    return int(lib().pcdm_next_check_interval(int(epoch), int(k_prev), float(rel_prev), int(k_cur), float(rel_cur),
+                                              float(rel_gap_tol)))

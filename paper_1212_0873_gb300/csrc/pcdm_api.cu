@@ -50,7 +50,7 @@ struct pcdm_ctx {
     int64_t P = 0;                // padded entries
     double *b = nullptr;          // FP64 copy of b
     double *L64 = nullptr;        // L_i in FP64
-    void *x = nullptr;            // n entries of xg dtype
+    double *x = nullptr;          // n FP64 entries
     void *g = nullptr;            // m entries of xg dtype
     void *g2 = nullptr;           // second residual buffer of the pipelined kernel
     bool g2_valid = false;        // g2 holds the same residual as g
@@ -222,14 +222,14 @@ IterArgs<VT, XT> iter_args(pcdm_handle h, int64_t tau, uint64_t seed)
     a.desc = static_cast<const ColDesc<XT> *>(h->desc);
     a.prow = h->prow;
     a.pval = static_cast<const VT *>(h->pval);
-    a.x = static_cast<XT *>(h->x);
+    a.x = static_cast<double *>(h->x);
     a.g = static_cast<XT *>(h->g);
     a.g2 = static_cast<XT *>(h->g2);
     a.h = static_cast<XT *>(h->h);
     a.S[0] = h->S[0];
     a.S[1] = h->S[1];
-    a.inv_beta = XT(1.0 / beta_nice(h->omega, tau, h->n));
-    a.lambda = XT(h->lambda);
+    a.inv_beta = 1.0 / beta_nice(h->omega, tau, h->n);
+    a.lambda = h->lambda;
     a.n = h->n;
     a.tau = tau;
     a.seed = seed;
@@ -347,7 +347,7 @@ pcdm_status refresh_t(pcdm_handle h)
     double *target = h->g64;
     CK(h, launch_neg_store<double>(target, h->b, h->m, h->stream));
     CK(h, Kernels<VT, XT>::refresh_cols(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
-                                        static_cast<const VT *>(h->pval), static_cast<const XT *>(h->x), h->n,
+                                        static_cast<const VT *>(h->pval), static_cast<const double *>(h->x), h->n,
                                         target, h->W, h->stream));
     if (sizeof(XT) == 4) CK(h, launch_store_from_f64<float>(static_cast<float *>(h->g), target, h->m, h->stream));
     h->g2_valid = false;
@@ -364,7 +364,7 @@ pcdm_status gap_t(pcdm_handle h)
     double *part_c = h->gap_part;
     double *part_r = h->gap_part + 3 * h->gap_blocks;
     CK(h, Kernels<VT, XT>::gap_cols(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
-                                    static_cast<const VT *>(h->pval), h->g64, static_cast<const XT *>(h->x), h->n,
+                                    static_cast<const VT *>(h->pval), h->g64, static_cast<const double *>(h->x), h->n,
                                     part_c, h->gap_blocks, h->W, h->stream));
     CK(h, launch_gap_rows(h->g64, h->b, h->m, part_r, h->gap_row_blocks, h->stream));
     CK(h, launch_gap_finish(part_c, h->gap_blocks, part_r, h->gap_row_blocks, h->gap_out, h->lambda, h->stream));
@@ -414,7 +414,7 @@ pcdm_status usable(pcdm_handle h)
 
 pcdm_status reset_state(pcdm_handle h)
 {
-    CK(h, cudaMemsetAsync(h->x, 0, size_t(h->n) * size_t(dtype_bytes(h->xg_dtype)), h->stream));
+    CK(h, cudaMemsetAsync(h->x, 0, size_t(h->n) * sizeof(double), h->stream));
     if (h->xg_dtype == PCDM_F64)
         CK(h, launch_neg_store<double>(static_cast<double *>(h->g), h->b, h->m, h->stream));
     else
@@ -521,7 +521,7 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     }
     CKC(dalloc(&h->b, h->m));
     CKC(dalloc(&h->L64, h->n));
-    CKC(dalloc_bytes(&h->x, h->n * xb));
+    CKC(dalloc(&h->x, h->n));
     CKC(dalloc_bytes(&h->g, h->m * xb));
     if (h->xg_dtype == PCDM_F64)
         h->g64 = static_cast<double *>(h->g);
@@ -721,6 +721,24 @@ pcdm_status pcdm_gap(pcdm_handle h, double *primal, double *dual, double *gap)
     return PCDM_OK;
 }
 
+int64_t pcdm_next_check_interval(int64_t epoch, int64_t k_prev, double rel_prev, int64_t k_cur, double rel_cur,
+                                 double rel_gap_tol)
+{
+    if (epoch < 1) epoch = 1;
+    const int64_t lo = (epoch + 3) / 4, hi = 8 * epoch;
+    const int64_t last = k_cur - k_prev;
+    if (last < 1 || !(rel_prev > rel_cur) || !(rel_cur > 0.0) || !(rel_gap_tol > 0.0) || !(rel_cur > rel_gap_tol))
+        return epoch;
+    // linear rate of the last interval, extrapolated with a 5% margin
+    const double rate = std::log(rel_prev / rel_cur) / double(last);
+    const double pred = 1.05 * std::log(rel_cur / rel_gap_tol) / rate;
+    int64_t next = pred < double(hi) ? int64_t(std::ceil(pred)) : hi;
+    if (next > 2 * last) next = 2 * last;   // no long jumps from a short observation
+    if (next < lo) next = lo;
+    if (next > hi) next = hi;
+    return next;
+}
+
 pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap_tol, int64_t max_iters,
                        int64_t *iters_done, double *rel_gap)
 {
@@ -728,7 +746,9 @@ pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap
     if (s != PCDM_OK) return s;
     if (tau < 1 || tau > h->n) return set_err(h, PCDM_EINVAL, "tau must be in [1, n]");
     if (max_iters < 0 || !(rel_gap_tol >= 0.0)) return set_err(h, PCDM_EINVAL, "max_iters < 0 or bad tolerance");
-    const int64_t every = h->opts.check_every > 0 ? h->opts.check_every : (h->n + tau - 1) / tau;
+    const int64_t epoch = (h->n + tau - 1) / tau;
+    const bool fixed = h->opts.check_every > 0;
+    int64_t every = fixed ? h->opts.check_every : epoch;
     double rec[9];
     int64_t done = 0;
     s = do_gap(h, rec);
@@ -738,10 +758,12 @@ pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap
         const int64_t chunk = every < max_iters - done ? every : max_iters - done;
         s = pcdm_step(h, tau, chunk, seed);
         if (s != PCDM_OK) return s;
+        const double rel_prev = rel;
         done += chunk;
         s = do_gap(h, rec);
         if (s != PCDM_OK) return s;
         rel = rec[2] / (rec[0] > 1e-300 ? rec[0] : 1e-300);
+        if (!fixed) every = pcdm_next_check_interval(epoch, done - chunk, rel_prev, done, rel, rel_gap_tol);
     }
     if (iters_done) *iters_done = done;
     if (rel_gap) *rel_gap = rel;
@@ -754,7 +776,7 @@ pcdm_status pcdm_get_x(pcdm_handle h, void *x_out, int32_t on_device)
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
     if (!x_out) return set_err(h, PCDM_EINVAL, "x_out is NULL");
-    CK(h, cudaMemcpyAsync(x_out, h->x, size_t(h->n * dtype_bytes(h->xg_dtype)), copy_kind(1, on_device), h->stream));
+    CK(h, cudaMemcpyAsync(x_out, h->x, size_t(h->n) * sizeof(double), copy_kind(1, on_device), h->stream));
     return sync_check(h);
 }
 
@@ -763,7 +785,7 @@ pcdm_status pcdm_set_x(pcdm_handle h, const void *x_in, int32_t on_device)
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
     if (!x_in) return set_err(h, PCDM_EINVAL, "x_in is NULL");
-    CK(h, cudaMemcpyAsync(h->x, x_in, size_t(h->n * dtype_bytes(h->xg_dtype)), copy_kind(on_device, 1), h->stream));
+    CK(h, cudaMemcpyAsync(h->x, x_in, size_t(h->n) * sizeof(double), copy_kind(on_device, 1), h->stream));
     h->sample_valid = false;
     s = do_refresh(h);
     if (s != PCDM_OK) return s;

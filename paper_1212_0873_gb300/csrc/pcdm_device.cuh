@@ -202,12 +202,62 @@ __device__ __forceinline__ void fence_proxy_async_shared()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar, uint64_t pol)
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
-                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mbar)), "l"(pol)
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// L2 eviction priorities.  Every iteration reads the residual at random rows
+// (the whole vector is hot) while the columns of A, their descriptors and x are
+// touched once: the residual is marked evict-last and the streamed data
+// evict-first, so that streaming A through L2 does not push the residual out.
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Coherent (L2) loads and stores with an L2 policy.
+__device__ __forceinline__ double ldcg_hint(const double *p, uint64_t pol)
+{
+    double v;
+    asm volatile("ld.global.cg.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ldcg_hint(const float *p, uint64_t pol)
+{
+    float v;
+    asm volatile("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(double *p, double v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(float *p, float v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+// Read-only 16-byte load with an L2 policy.
+__device__ __forceinline__ int4 ldnc_v4_hint(const void *p, uint64_t pol)
+{
+    int4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -231,6 +281,14 @@ __device__ __forceinline__ void red_add(double *p, double v)
 __device__ __forceinline__ void red_add(float *p, float v)
 {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double *p, double v, uint64_t pol)
+{
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add(float *p, float v, uint64_t pol)
+{
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
 }
 
 template <typename T>
@@ -308,14 +366,17 @@ __device__ __forceinline__ bool wait_counter(unsigned long long *counter, unsign
     const uint64_t t0 = global_ns();
     uint32_t spins = 0;
     while (ld_acquire_u64(counter) < target) {
-        if (ld_volatile_int(status) != DEV_OK) {
-            ok = 0;
-            break;
-        }
-        if ((++spins & 31u) == 0u && global_ns() - t0 > timeout_ns) {
-            atomicCAS(status, DEV_OK, DEV_TIMEOUT);
-            ok = 0;
-            break;
+        // every 16th spin: another block's failure, then the time limit
+        if ((++spins & 15u) == 0u) {
+            if (ld_volatile_int(status) != DEV_OK) {
+                ok = 0;
+                break;
+            }
+            if (global_ns() - t0 > timeout_ns) {
+                atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+                ok = 0;
+                break;
+            }
         }
     }
     return ok != 0;

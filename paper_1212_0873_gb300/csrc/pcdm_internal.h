@@ -53,19 +53,21 @@ __host__ __device__ constexpr int pad_granule()
     return sizeof(VT) == 2 ? 8 : 4;
 }
 
-// Everything one PCDM1 iteration reads and writes.  XT is the dtype of x, g, h,
-// 1/L and of the gradient accumulator; VT the dtype of the stored values.
+// Everything one PCDM1 iteration reads and writes.  XT is the dtype of g, h,
+// 1/L and of the gradient accumulator; VT the dtype of the stored values.  x and
+// the proximal step are FP64 in every precision pair (an FP32 x bounds the
+// reachable relative duality gap at about 1e-6).
 template <typename VT, typename XT>
 struct IterArgs {
     const ColDesc<XT> *desc;
     const int32_t *prow;
     const VT *pval;
-    XT *x;
+    double *x;
     XT *g;
     XT *g2;                     // second residual buffer of the pipelined kernel (equal to g at launch)
     XT *h;                      // h[j] = step of coordinate S_k[j]
     int32_t *S[2];              // S_k lives in S[k & 1]
-    XT inv_beta, lambda;
+    double inv_beta, lambda;
     int64_t n, tau;
     uint64_t seed;
     unsigned long long *counters;   // [0] gathered nnz, [1] scattered nnz, [2] nonzero updates
@@ -105,11 +107,11 @@ struct Kernels {
                                     const int64_t *pbeg, const double *L, int64_t n, ColDesc<XT> *desc,
                                     int32_t *prow, VT *pval, cudaStream_t st);
     // g64 += A x over the columns with x_i != 0.
-    static cudaError_t refresh_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const XT *x,
+    static cudaError_t refresh_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *x,
                                     int64_t n, double *g64, int W, cudaStream_t st);
     // Per-block partials (max |c_i|, sum |x_i|, sum x_i c_i), c = A^T r.
     static cudaError_t gap_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *r,
-                                const XT *x, int64_t n, double *part, int blocks, int W, cudaStream_t st);
+                                const double *x, int64_t n, double *part, int blocks, int W, cudaStream_t st);
 };
 
 // Type-independent kernels (kernels_common.cu).

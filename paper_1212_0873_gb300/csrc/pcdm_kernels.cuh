@@ -64,6 +64,25 @@ struct Col {
 };
 
 template <typename XT>
+__device__ __forceinline__ Col<XT> col_from_word(const int4 v)
+{
+    Col<XT> c;
+    c.pbeg = int64_t(uint32_t(v.x)) * 4;
+    c.cnt = v.y;
+    if constexpr (sizeof(XT) == 8)
+        c.invL = __hiloint2double(v.w, v.z);
+    else
+        c.invL = __int_as_float(v.z);
+    return c;
+}
+
+template <typename XT>
+__device__ __forceinline__ Col<XT> load_col(const ColDesc<XT> *d, int32_t i, uint64_t pol)
+{
+    return col_from_word<XT>(ldnc_v4_hint(d + i, pol));
+}
+
+template <typename XT>
 __device__ __forceinline__ Col<XT> load_col(const ColDesc<XT> *d, int32_t i)
 {
     const int4 v = __ldg(reinterpret_cast<const int4 *>(d + i));
@@ -135,6 +154,69 @@ __device__ __forceinline__ void ld_vals(float (&v)[E], const bf16_t *p)
     }
 }
 
+// Chunk load with an L2 policy (the pipelined kernel marks A evict-first).
+template <int E, typename XT>
+__device__ __forceinline__ void ld_chunk_hint(Chunk<E, XT> &c, const int32_t *prow, const double *pval, int64_t p,
+                                              uint64_t pol)
+{
+    static_assert(sizeof(XT) == 8, "FP64 values go with FP64 iterates");
+#pragma unroll
+    for (int q = 0; q < E / 4; ++q) {
+        const int4 v = ldnc_v4_hint(prow + p + 4 * q, pol);
+        c.row[4 * q + 0] = v.x;
+        c.row[4 * q + 1] = v.y;
+        c.row[4 * q + 2] = v.z;
+        c.row[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int q = 0; q < E / 2; ++q) {
+        const int4 v = ldnc_v4_hint(pval + p + 2 * q, pol);
+        c.val[2 * q + 0] = __hiloint2double(v.y, v.x);
+        c.val[2 * q + 1] = __hiloint2double(v.w, v.z);
+    }
+}
+template <int E, typename XT>
+__device__ __forceinline__ void ld_chunk_hint(Chunk<E, XT> &c, const int32_t *prow, const float *pval, int64_t p,
+                                              uint64_t pol)
+{
+#pragma unroll
+    for (int q = 0; q < E / 4; ++q) {
+        const int4 v = ldnc_v4_hint(prow + p + 4 * q, pol);
+        c.row[4 * q + 0] = v.x;
+        c.row[4 * q + 1] = v.y;
+        c.row[4 * q + 2] = v.z;
+        c.row[4 * q + 3] = v.w;
+        const int4 u = ldnc_v4_hint(pval + p + 4 * q, pol);
+        c.val[4 * q + 0] = __int_as_float(u.x);
+        c.val[4 * q + 1] = __int_as_float(u.y);
+        c.val[4 * q + 2] = __int_as_float(u.z);
+        c.val[4 * q + 3] = __int_as_float(u.w);
+    }
+}
+template <int E, typename XT>
+__device__ __forceinline__ void ld_chunk_hint(Chunk<E, XT> &c, const int32_t *prow, const bf16_t *pval, int64_t p,
+                                              uint64_t pol)
+{
+#pragma unroll
+    for (int q = 0; q < E / 4; ++q) {
+        const int4 v = ldnc_v4_hint(prow + p + 4 * q, pol);
+        c.row[4 * q + 0] = v.x;
+        c.row[4 * q + 1] = v.y;
+        c.row[4 * q + 2] = v.z;
+        c.row[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int q = 0; q < E / 8; ++q) {
+        const int4 u = ldnc_v4_hint(pval + p + 8 * q, pol);
+        const uint32_t w[4] = {uint32_t(u.x), uint32_t(u.y), uint32_t(u.z), uint32_t(u.w)};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            c.val[8 * q + 2 * t + 0] = __uint_as_float(w[t] << 16);
+            c.val[8 * q + 2 * t + 1] = __uint_as_float(w[t] & 0xFFFF0000u);
+        }
+    }
+}
+
 template <int E, typename VT, typename XT>
 __device__ __forceinline__ void ld_chunk(Chunk<E, XT> &c, const int32_t *prow, const VT *pval, int64_t p)
 {
@@ -162,6 +244,27 @@ __device__ __forceinline__ void chunk_scatter(const Chunk<E, XT> &c, XT *g, XT h
 #pragma unroll
     for (int e = 0; e < E; ++e)
         if (e < valid) red_add(g + c.row[e], c.val[e] * h);
+}
+
+template <int E, typename XT>
+__device__ __forceinline__ void chunk_scatter_hint(const Chunk<E, XT> &c, XT *g, XT h, int valid, uint64_t pol)
+{
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (e < valid) red_add(g + c.row[e], c.val[e] * h, pol);
+}
+
+template <int E, typename XT, typename GT = XT>
+__device__ __forceinline__ GT chunk_dot_hint(const Chunk<E, XT> &c, const GT *v, int valid, uint64_t pol)
+{
+    GT gv[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) gv[e] = (e < valid) ? ldcg_hint(v + c.row[e], pol) : GT(0);
+    GT acc = GT(0);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+        if (e < valid) acc = fma(GT(c.val[e]), gv[e], acc);
+    return acc;
 }
 
 // a_i^T g over a whole column, chunk by chunk (all W lanes of the group together).
@@ -196,12 +299,14 @@ __device__ __forceinline__ void column_scatter(const IterArgs<VT, XT> &a, const 
 
 // The step of eq. (h(x)) for one coordinate: soft(x - grad/(beta L), lambda/(beta L)),
 // with 1/(beta L) = (1/L)(1/beta); an empty column (1/L stored as 0) goes to 0.
-template <typename XT>
-__device__ __forceinline__ XT prox_step(XT xi, XT grad, XT invL, XT inv_beta, XT lambda)
+// FP64 in every precision pair: the fixed point of the step (the optimality
+// condition -grad in lambda d|x|) does not depend on the step length, so an FP32
+// 1/L costs no accuracy, but x itself must not be rounded to FP32.
+__device__ __forceinline__ double prox_step(double xi, double grad, double invL, double inv_beta, double lambda)
 {
-    if (invL == XT(0)) return XT(0);
-    const XT ibl = invL * inv_beta;
-    return soft_threshold<XT>(fma(-grad, ibl, xi), lambda * ibl);
+    if (invL == 0.0) return 0.0;
+    const double ibl = invL * inv_beta;
+    return soft_threshold<double>(fma(-grad, ibl, xi), lambda * ibl);
 }
 
 // Phase 1 for sampled position j, columns read from memory (no prefetch).
@@ -211,15 +316,15 @@ __device__ __forceinline__ void gather_generic(const IterArgs<VT, XT> &a, const 
 {
     const int32_t i = ldcg(S + j);
     const Col<XT> c = load_col(a.desc, i);
-    const XT xi = ldcg(a.x + i);
+    const double xi = ldcg(a.x + i);
     const XT grad = column_dot<W>(a, c, lane, gmask);
-    const XT xn = prox_step<XT>(xi, grad, c.invL, a.inv_beta, a.lambda);
-    const XT h = xn - xi;
+    const double xn = prox_step(xi, double(grad), double(c.invL), a.inv_beta, a.lambda);
+    const double h64 = xn - xi;
     if (lane == 0) {
-        a.x[i] = xn;
-        a.h[j] = h;
+        if (h64 != 0.0) a.x[i] = xn;
+        a.h[j] = XT(h64);
         cnt.gathered += (unsigned long long)c.cnt;
-        if (h != XT(0)) {
+        if (h64 != 0.0) {
             cnt.nonzero += 1;
             cnt.scattered += (unsigned long long)c.cnt;
         }
@@ -307,7 +412,7 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
         int32_t i_next = 0;
         Col<XT> c_next = c0;
         if (own) {
-            const XT xi = ldcg(a.x + i0);
+            const double xi = ldcg(a.x + i0);
             XT gv[kE];
             const int valid0 = c0.cnt - lane * kE;
 #pragma unroll
@@ -325,12 +430,13 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
                 acc += chunk_dot<kE, XT, XT, XT>(t, a.g, c0.cnt - st);
             }
             acc = group_sum<W>(acc, gmask);
-            const XT xn = prox_step<XT>(xi, acc, c0.invL, a.inv_beta, a.lambda);
-            h0 = xn - xi;
+            const double xn = prox_step(xi, double(acc), double(c0.invL), a.inv_beta, a.lambda);
+            const double h64 = xn - xi;
+            h0 = XT(h64);
             if (lane == 0) {
-                a.x[i0] = xn;
+                if (h64 != 0.0) a.x[i0] = xn;
                 cnt.gathered += (unsigned long long)c0.cnt;
-                if (h0 != XT(0)) {
+                if (h64 != 0.0) {
                     cnt.nonzero += 1;
                     cnt.scattered += (unsigned long long)c0.cnt;
                 }
@@ -434,7 +540,7 @@ __host__ __device__ constexpr size_t pipe_smem_bytes(int threads)
 // (from memory) into g: g_r += a_ri * h.
 template <typename VT, typename XT>
 __device__ __forceinline__ void slot_scatter(const IterArgs<VT, XT> &a, const unsigned char *slot, const Col<XT> &d,
-                                             XT h, XT *g)
+                                             XT h, XT *g, uint64_t pf, uint64_t pl)
 {
     constexpr int VW = pipe_value_words<VT>();
     constexpr int EPW = 16 / int(sizeof(VT));
@@ -453,12 +559,12 @@ __device__ __forceinline__ void slot_scatter(const IterArgs<VT, XT> &a, const un
         decode_word<VT, XT>(reinterpret_cast<const uint4 *>(slot + 64)[w], vw);
 #pragma unroll
         for (int q = 0; q < EPW; ++q)
-            if (w * EPW + q < d.cnt) red_add(g + row[w * EPW + q], vw[q] * h);
+            if (w * EPW + q < d.cnt) red_add(g + row[w * EPW + q], vw[q] * h, pl);
     }
     for (int cs = kE; cs < d.cnt; cs += kE) {
         Chunk<kE, XT> t;
-        ld_chunk<kE>(t, a.prow, a.pval, d.pbeg + cs);
-        chunk_scatter<kE>(t, g, h, d.cnt - cs);
+        ld_chunk_hint<kE>(t, a.prow, a.pval, d.pbeg + cs, pf);
+        chunk_scatter_hint<kE>(t, g, h, d.cnt - cs, pl);
     }
 }
 
@@ -476,6 +582,8 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     unsigned long long target = 0;
     uint32_t phase = 0;   // bit b: parity of the next completion of mbar[b]
     Counters cnt;
+    const uint64_t pf = l2_evict_first();   // A, descriptors, x: touched once per iteration
+    const uint64_t pl = l2_evict_last();    // the residual buffers: gathered at random rows
 
     auto slot = [&](int b) { return smem + (size_t(b) * nt + t) * SB; };
     // the residual buffer that holds g_k at iteration k
@@ -488,8 +596,8 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
             const uint32_t e = uint32_t(pc < kE ? pc : kE);
             const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
             mbar_arrive_expect_tx(&mbar[b], br + bv);
-            bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b]);
-            bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b]);
+            bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b], pf);
+            bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b], pf);
         } else {
             mbar_arrive(&mbar[b]);
         }
@@ -516,9 +624,9 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     XT h_prev = XT(0);   // the step of the previous iteration's column (still owed to one buffer)
     if (own) {
         i_cur = ldcg(sample_buf(a, k0) + j0);
-        d_cur = load_col(a.desc, i_cur);
+        d_cur = load_col(a.desc, i_cur, pf);
         i_nxt = sample_index(uint32_t(j0), make_sample_key(a.seed, k0 + 1, a.n));
-        d_nxt = load_col(a.desc, i_nxt);
+        d_nxt = load_col(a.desc, i_nxt, pf);
     }
     fill(0, d_cur, own);
 
@@ -537,12 +645,13 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         // of the column's tail); the sample of k+2 (integer work only: no
         // shuffles or shared-memory traffic, which would queue behind the loads)
         // is drawn while they are in flight.
-        XT h = XT(0), xi = XT(0);
+        XT h = XT(0);
+        double xi = 0.0;
         int32_t i_nn = 0;
         Col<XT> d_nn = d_nxt;
         const int valid = own ? d_cur.cnt : 0;
         if (own) {
-            xi = ldcg(a.x + i_cur);
+            xi = ldcg_hint(a.x + i_cur, pf);
             int32_t row[kE];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -554,14 +663,14 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
             }
             XT gv[kE];
 #pragma unroll
-            for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg(gk + row[e]) : XT(0);
+            for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
             Chunk<kT, XT> tl;
-            if (valid > kE) ld_chunk<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE);
+            if (valid > kE) ld_chunk_hint<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE, pf);
             i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
-            d_nn = load_col(a.desc, i_nn);
+            d_nn = load_col(a.desc, i_nn, pf);
             XT gt[kT];
 #pragma unroll
-            for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg(gk + tl.row[e]) : XT(0);
+            for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg_hint(gk + tl.row[e], pl) : XT(0);
             constexpr int EPW = 16 / int(sizeof(VT));
             XT acc = XT(0);
 #pragma unroll
@@ -577,14 +686,15 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                 if (kE + e < valid) acc = fma(tl.val[e], gt[e], acc);
             for (int cs = kE + kT; cs < valid; cs += kE) {
                 Chunk<kE, XT> tc;
-                ld_chunk<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs);
-                acc += chunk_dot<kE, XT, XT, XT>(tc, gk, valid - cs);
+                ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
+                acc += chunk_dot_hint<kE, XT>(tc, gk, valid - cs, pl);
             }
-            const XT xn = prox_step<XT>(xi, acc, d_cur.invL, a.inv_beta, a.lambda);
-            h = xn - xi;
-            a.x[i_cur] = xn;
+            const double xn = prox_step(xi, double(acc), double(d_cur.invL), a.inv_beta, a.lambda);
+            const double h64 = xn - xi;
+            h = XT(h64);
+            if (h64 != 0.0) st_hint(a.x + i_cur, xn, pf);   // most steps are zero: x_i unchanged
             cnt.gathered += (unsigned long long)valid;
-            if (h != XT(0)) {
+            if (h64 != 0.0) {
                 cnt.nonzero += 1;
                 cnt.scattered += (unsigned long long)valid;
             }
@@ -595,8 +705,8 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         // which nobody writes during iteration k.  The other buffer holds g_{k-1}
         // and receives the steps of iterations k-1 and k.  The previous column's
         // chunk sits in slot b^1, so it is re-scattered before that slot is refilled.
-        if (own && h_prev != XT(0)) slot_scatter<VT, XT>(a, slot(b ^ 1), d_prev, h_prev, gn);
-        if (own && h != XT(0)) slot_scatter<VT, XT>(a, my, d_cur, h, gn);
+        if (own && h_prev != XT(0)) slot_scatter<VT, XT>(a, slot(b ^ 1), d_prev, h_prev, gn, pf, pl);
+        if (own && h != XT(0)) slot_scatter<VT, XT>(a, my, d_cur, h, gn, pf, pl);
         h_prev = h;
         d_prev = d_cur;
 
@@ -625,7 +735,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     // Both buffers equal again: the last iteration's steps (still in slot
     // (iters-1)&1) go into the buffer that holds g_{k0+iters-1}.
     if (iters > 0 && own && h_prev != XT(0))
-        slot_scatter<VT, XT>(a, slot(int((iters - 1) & 1)), d_prev, h_prev, gbuf(k0 + iters - 1));
+        slot_scatter<VT, XT>(a, slot(int((iters - 1) & 1)), d_prev, h_prev, gbuf(k0 + iters - 1), pf, pl);
     // the last fill (the chunks of i_{k0+iters}) lands before the block leaves
     wait_buf(int(iters & 1));
     // S_{k0+iters} for the caller (the sample of the next launch).
@@ -702,14 +812,14 @@ __global__ void k_build_layout(const int64_t *__restrict__ col_ptr, const int32_
 template <int W, typename VT, typename XT>
 __global__ void __launch_bounds__(kBlock) k_refresh_cols(const ColDesc<XT> *__restrict__ desc,
                                                          const int32_t *__restrict__ prow,
-                                                         const VT *__restrict__ pval, const XT *__restrict__ x,
+                                                         const VT *__restrict__ pval, const double *__restrict__ x,
                                                          int64_t n, double *__restrict__ g64)
 {
     constexpr int CH = W * kE;
     const int lane = threadIdx.x & (W - 1);
     const int64_t ngrp = int64_t(gridDim.x) * kBlock / W;
     for (int64_t i = (int64_t(blockIdx.x) * kBlock + threadIdx.x) / W; i < n; i += ngrp) {
-        const double xi = double(__ldg(x + i));
+        const double xi = __ldg(x + i);
         if (xi == 0.0) continue;
         const Col<XT> c = load_col(desc, int32_t(i));
         for (int cs = 0; cs < c.cnt; cs += CH) {
@@ -730,25 +840,27 @@ template <int W, typename VT, typename XT>
 __global__ void __launch_bounds__(kBlock) k_gap_cols(const ColDesc<XT> *__restrict__ desc,
                                                      const int32_t *__restrict__ prow,
                                                      const VT *__restrict__ pval, const double *__restrict__ r,
-                                                     const XT *__restrict__ x, int64_t n, double *__restrict__ part)
+                                                     const double *__restrict__ x, int64_t n, double *__restrict__ part)
 {
     constexpr int CH = W * kE;
     const int lane = threadIdx.x & (W - 1);
     const unsigned gmask = group_mask<W>(threadIdx.x & 31);
     const int64_t ngrp = int64_t(gridDim.x) * kBlock / W;
     double cmax = 0.0, l1 = 0.0, xc = 0.0;
+    // A streams through once (evict-first); r is gathered at random rows (evict-last)
+    const uint64_t pf = l2_evict_first(), pl = l2_evict_last();
     for (int64_t i = (int64_t(blockIdx.x) * kBlock + threadIdx.x) / W; i < n; i += ngrp) {
-        const Col<XT> c = load_col(desc, int32_t(i));
+        const Col<XT> c = load_col(desc, int32_t(i), pf);
         double acc = 0.0;
         for (int cs = 0; cs < c.cnt; cs += CH) {
             Chunk<kE, XT> t;
             const int st = cs + lane * kE;
-            if (st < c.cnt) ld_chunk<kE>(t, prow, pval, c.pbeg + st);
-            acc += chunk_dot<kE, XT, double, double>(t, r, c.cnt - st);
+            if (st < c.cnt) ld_chunk_hint<kE>(t, prow, pval, c.pbeg + st, pf);
+            acc += chunk_dot_hint<kE, XT, double>(t, r, c.cnt - st, pl);
         }
         acc = group_sum<W>(acc, gmask);
         if (lane == 0) {
-            const double xi = double(__ldg(x + i));
+            const double xi = __ldg(x + i);
             cmax = fmax(cmax, fabs(acc));
             l1 += fabs(xi);
             xc += xi * acc;
@@ -899,7 +1011,7 @@ cudaError_t Kernels<VT, XT>::build_layout(const int64_t *col_ptr, const int32_t 
 }
 
 template <typename VT, typename XT>
-cudaError_t Kernels<VT, XT>::refresh_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const XT *x,
+cudaError_t Kernels<VT, XT>::refresh_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *x,
                                           int64_t n, double *g64, int W, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
@@ -912,7 +1024,7 @@ cudaError_t Kernels<VT, XT>::refresh_cols(const ColDesc<XT> *desc, const int32_t
 
 template <typename VT, typename XT>
 cudaError_t Kernels<VT, XT>::gap_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *r,
-                                      const XT *x, int64_t n, double *part, int blocks, int W, cudaStream_t st)
+                                      const double *x, int64_t n, double *part, int blocks, int W, cudaStream_t st)
 {
     PCDM_DISPATCH_W(W, {
         k_gap_cols<W_, VT, XT><<<dim3(unsigned(blocks)), kBlock, 0, st>>>(desc, prow, pval, r, x, n, part);

@@ -103,27 +103,26 @@ class Lasso:
         return B.pcdm_solve(self._h, tau, seed, tol, max_iters)
 
     # -------------------------------------------------------------- state
-    def _np_xg(self, count):
+    def _np_g(self, count):
         return np.empty(count, dtype=np.float64 if self.xg_dtype == "f64" else np.float32)
 
     def x(self):
-        out = self._np_xg(self.n)
+        out = np.empty(self.n, dtype=np.float64)
         B.pcdm_get_x(self._h, out.ctypes.data, 0)
         return out
 
     def x_into(self, tensor):
-        """Copy x into a CUDA tensor of n entries of the iterate dtype."""
+        """Copy x into a CUDA float64 tensor of n entries."""
         B.pcdm_get_x(self._h, tensor.data_ptr(), 1)
         return tensor
 
     def set_x(self, x):
-        x = np.ascontiguousarray(x, dtype=np.float64 if self.xg_dtype == "f64" else np.float32) \
-            if not _is_tensor(x) else x
+        x = np.ascontiguousarray(x, dtype=np.float64) if not _is_tensor(x) else x
         p, d = _ptr_and_device(x)
         B.pcdm_set_x(self._h, p, d)
 
     def residual(self):
-        out = self._np_xg(self.m)
+        out = self._np_g(self.m)
         B.pcdm_get_residual(self._h, out.ctypes.data, 0)
         return out
 

@@ -157,3 +157,23 @@ def test_sample_rejects_bad_sizes(B, args):
 
 def test_selftest_rejects_bad_timeout(B):
     assert B.lib().pcdm_selftest_barrier_timeout(0, None) == B.PCDM_EINVAL
+
+
+def test_check_schedule_extrapolates_the_linear_rate(B):
+    """pcdm_solve's adaptive gap-check schedule: host arithmetic, no device."""
+    f = B.pcdm_next_check_interval
+    E = 62
+    # gap fell 1e-1 -> 1e-2 over one epoch: 4 more decades to 1e-6 is 4 epochs,
+    # + 5%, but at most twice the last interval
+    assert f(E, 0, 1e-1, E, 1e-2, 1e-6) == 2 * E
+    # the same rate over a 4-epoch window: ceil(1.05 * 4 E)
+    assert f(E, 0, 1e-1 ** 4, 4 * E, 1e-1 ** 8, 1e-12) == int(__import__("math").ceil(1.05 * 4 * E))
+    # almost there: never below a quarter epoch
+    assert f(E, 0, 2e-6, 10 * E, 1.0000001e-6, 1e-6) == (E + 3) // 4
+    # slow progress: never beyond 8 epochs
+    assert f(E, 0, 1.0, 100 * E, 0.5, 1e-9) == 8 * E
+    # no decrease, non-positive gaps, zero interval: one epoch
+    assert f(E, 0, 1e-3, E, 2e-3, 1e-6) == E
+    assert f(E, 0, 1e-3, E, 0.0, 1e-6) == E
+    assert f(E, E, 1e-2, E, 1e-3, 1e-6) == E
+    assert f(0, 0, 1e-1, 1, 1e-2, 1e-6) == 2      # epoch < 1 is taken as 1
