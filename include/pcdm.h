@@ -132,9 +132,13 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
  * continuing the handle's iteration counter k.  S_k depends only on
  * (seed, k, n, tau), so step(a) followed by step(b) equals step(a+b).
  * tau in [1, n]; iters >= 0.  EINVAL otherwise.
- * The sampler: Philox4x32-10 (Salmon et al., SC'11) keyed by seed drives a
- * 12-round Feistel permutation pi_k of [0, 2^w) (w the least even width with
- * 2^w >= n, at least 2), walked back into [0, n); S_k = (pi_k(0) .. pi_k(tau-1)).
+ * The sampler: a 12-round balanced Feistel permutation pi_k of [0, 2^w) (w the
+ * least even width with 2^w >= n, at least 2), walked back into [0, n) by
+ * re-applying it; S_k = (pi_k(0) .. pi_k(tau-1)).  Its round keys K[0..11] are
+ * the three Philox4x32-10 blocks (Salmon et al., SC'11) with counter
+ * (c, 0, lo32 k, hi32 k), c = 0, 1, 2, and key (lo32 seed, hi32 seed); round r
+ * maps (L, R) to (R, L xor (fmix32(R xor K[r]) & (2^(w/2) - 1))), fmix32 being
+ * the MurmurHash3 finaliser.
  */
 pcdm_status pcdm_step(pcdm_handle h, int64_t tau, int64_t iters, uint64_t seed);
 
