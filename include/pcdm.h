@@ -230,11 +230,42 @@ pcdm_status pcdm_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_
  */
 pcdm_status pcdm_selftest_barrier_timeout(uint64_t timeout_ns, void *cuda_stream);
 
+/*
+ * omega = the largest number of nonzeros in one row of A (the omega of the
+ * tau-nice ESO parameter beta, Theorem ESO-nice, Sec. 6.3) for a CSC matrix already in
+ * device memory, with no handle and WITHOUT ALLOCATING ANY MEMORY.  The paper
+ * has no counterpart: this is a library convenience.
+ *
+ * Who needs it: callers that cannot allocate device memory at the point where
+ * they need omega (and so beta for a new tau), for instance a process that has
+ * given all free device memory to its own pool or arena, where cudaMalloc would
+ * fail, or a loop that must not pay cudaMalloc/cudaFree, which can synchronise
+ * the whole device.  pcdm_create computes the same omega (pcdm_omega) but
+ * allocates a handle and an m-entry row-count buffer to do it.
+ *
+ * The row counters live in a fixed device array of PCDM_NOALLOC_MAX_ROWS ints
+ * (4 MiB) inside the library, so m may be at most PCDM_NOALLOC_MAX_ROWS; larger
+ * m returns PCDM_EINVAL before any device work.  A: col_ptr, row_idx on the
+ * device (A->on_device must be 1; host arrays would need a staging buffer), the
+ * values are not read.  The matrix is checked as pcdm_create checks it (col_ptr
+ * monotone from 0 to nnz, rows in [0, m), strictly increasing in a column);
+ * a violation returns PCDM_EINVAL.  The call clears the counters it uses, runs
+ * on cuda_stream and synchronises it before writing *omega (host memory).
+ *
+ * The first call on a device looks up the array's device address (a one-time
+ * set-up per device); make that first call before any stream capture begins.
+ * Calls that overlap in time (two host threads, or two streams, at once) share
+ * the one array and race: serialise them.
+ */
+#define PCDM_NOALLOC_MAX_ROWS 1048576
+pcdm_status pcdm_omega_noalloc(const pcdm_csc *A, int64_t *omega, void *cuda_stream);
+
 /* Free everything the handle owns.  NULL is ignored. */
 void pcdm_destroy(pcdm_handle h);
 
 /* Last error message of the handle ("" if none); valid until the next call on it.
- * With h == NULL: the last error of a failed pcdm_create or pcdm_sample on this thread. */
+ * With h == NULL: the last error of a failed pcdm_create, pcdm_sample or
+ * pcdm_omega_noalloc on this thread. */
 const char *pcdm_last_error(pcdm_handle h);
 
 /* Static name of a status code. */

@@ -45,6 +45,7 @@ SIGNATURES = {
     "pcdm_gap": (_i32, [_ptr, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
     "pcdm_solve": (_i32, [_ptr, _i64, _u64, _dbl, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "pcdm_next_check_interval": (_i64, [_i64, _i64, ctypes.c_double, _i64, ctypes.c_double, ctypes.c_double]),
+    "pcdm_omega_noalloc": (_i32, [ctypes.POINTER(pcdm_csc), ctypes.POINTER(_i64), _ptr]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -226,3 +227,13 @@ def pcdm_status_string(status):
 def pcdm_next_check_interval(epoch, k_prev, rel_prev, k_cur, rel_cur, rel_gap_tol):
     return int(lib().pcdm_next_check_interval(int(epoch), int(k_prev), float(rel_prev), int(k_cur), float(rel_cur),
                                               float(rel_gap_tol)))
+
+
+PCDM_NOALLOC_MAX_ROWS = 1048576
+
+
+def pcdm_omega_noalloc(csc, stream):
+    """omega of a device CSC (a pcdm_csc with on_device = 1) without any allocation."""
+    out = _i64(0)
+    _check(lib().pcdm_omega_noalloc(ctypes.byref(csc), ctypes.byref(out), _stream(stream)), None)
+    return int(out.value)

@@ -1,8 +1,11 @@
 // Type-independent kernels of libpcdm: the standalone tau-nice sampler, input
 // validation, conversions, the row part and the final reduction of the duality
-// gap, and the self-test of the bounded grid barrier.
+// gap, the self-test of the bounded grid barrier, and the row counts of
+// pcdm_omega_noalloc.
 #include <cmath>
+#include <mutex>
 
+#include "pcdm.h"
 #include "pcdm_internal.h"
 
 namespace pcdm {
@@ -351,6 +354,71 @@ cudaError_t launch_padded_scan(const int64_t *col_ptr, int64_t n, int granule, i
     k_scan_tiles<<<unsigned(nt), kScanThreads, 0, st>>>(col_ptr, n, granule, tile);
     k_scan_tile_prefix<<<1, kScanThreads, 0, st>>>(tile, nt);
     k_scan_apply<<<unsigned(nt), kScanThreads, 0, st>>>(col_ptr, n, granule, tile, nt, pbeg);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Row counts and omega with no allocation (pcdm_omega_noalloc).  The scratch is
+// this file-scope array: PCDM_NOALLOC_MAX_ROWS row counters, then a flags word
+// and the result word.  One array per device context, shared by every caller:
+// calls that overlap in time race on it.
+constexpr int64_t kNoAllocTail = 64;
+static __device__ __align__(256) int g_noalloc_rows[PCDM_NOALLOC_MAX_ROWS + kNoAllocTail];
+
+// One thread per column: the same checks as the set-up (col_ptr monotone and in
+// range, rows in [0, m) and strictly increasing within a column), then one count
+// per valid entry.
+__global__ void k_rows_checked(const int64_t *col_ptr, const int32_t *row_idx, int64_t m, int64_t n, int64_t nnz,
+                               int *cnt, int *flags)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int f = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= n; i += stride) {
+        const int64_t s = col_ptr[i];
+        if ((i == 0 && s != 0) || (i == n && s != nnz)) f |= FLAG_COLPTR;
+        if (i == n) continue;
+        const int64_t e = col_ptr[i + 1];
+        if (s < 0 || e < s || e > nnz) {
+            f |= FLAG_COLPTR;
+            continue;
+        }
+        int64_t prev = -1;
+        for (int64_t p = s; p < e; ++p) {
+            const int64_t r = row_idx[p];
+            if (r < 0 || r >= m) {
+                f |= FLAG_ROW_RANGE;
+                continue;
+            }
+            if (r <= prev) f |= FLAG_ROW_ORDER;
+            prev = r;
+            atomicAdd(cnt + r, 1);
+        }
+    }
+    if (f) atomicOr(flags, f);
+}
+
+cudaError_t noalloc_rows_scratch(int device, int **rows, int **tail)
+{
+    // cudaGetSymbolAddress once per device; later calls reuse the address.
+    static std::mutex mu;
+    static int *base[kMaxNoAllocDevices] = {};
+    if (device < 0 || device >= kMaxNoAllocDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!base[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_rows);
+        if (e != cudaSuccess) return e;
+        base[device] = static_cast<int *>(p);
+    }
+    *rows = base[device];
+    *tail = base[device] + PCDM_NOALLOC_MAX_ROWS;
+    return cudaSuccess;
+}
+
+cudaError_t launch_rows_checked(const int64_t *col_ptr, const int32_t *row_idx, int64_t m, int64_t n, int64_t nnz,
+                                int *cnt, int *flags, cudaStream_t st)
+{
+    k_rows_checked<<<grid_for(n + 1), 256, 0, st>>>(col_ptr, row_idx, m, n, nnz, cnt, flags);
     return cudaGetLastError();
 }
 

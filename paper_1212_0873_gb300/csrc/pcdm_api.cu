@@ -917,6 +917,39 @@ pcdm_status pcdm_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_
     return PCDM_OK;
 }
 
+pcdm_status pcdm_omega_noalloc(const pcdm_csc *A, int64_t *omega, void *cuda_stream)
+{
+    // Every check that needs no device comes first; nothing below allocates.
+    if (!A || !omega) return set_err(nullptr, PCDM_EINVAL, "A or omega is NULL");
+    if (A->on_device != 1) return set_err(nullptr, PCDM_EINVAL, "A must be in device memory (on_device = 1)");
+    if (A->m < 0 || A->n < 0 || A->nnz < 0) return set_err(nullptr, PCDM_EINVAL, "negative m, n or nnz");
+    if (A->m > PCDM_NOALLOC_MAX_ROWS)
+        return set_err(nullptr, PCDM_EINVAL, "m exceeds PCDM_NOALLOC_MAX_ROWS (" +
+                                                 std::to_string(PCDM_NOALLOC_MAX_ROWS) + ")");
+    if (!A->col_ptr || (A->nnz > 0 && !A->row_idx)) return set_err(nullptr, PCDM_EINVAL, "col_ptr or row_idx is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    int *cnt = nullptr, *tail = nullptr;
+    e = noalloc_rows_scratch(dev, &cnt, &tail);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress of the row-count scratch");
+    // counters and the flags / result words start at zero
+    if (A->m > 0) e = cudaMemsetAsync(cnt, 0, size_t(A->m) * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tail, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) e = launch_rows_checked(A->col_ptr, A->row_idx, A->m, A->n, A->nnz, cnt, tail, st);
+    if (e == cudaSuccess) e = launch_max_int(cnt, A->m, tail + 1, st);
+    int host[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, tail, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "pcdm_omega_noalloc");
+    if (host[0] & FLAG_COLPTR) return set_err(nullptr, PCDM_EINVAL, "col_ptr not monotone from 0 to nnz");
+    if (host[0] & FLAG_ROW_RANGE) return set_err(nullptr, PCDM_EINVAL, "a row index outside [0, m)");
+    if (host[0] & FLAG_ROW_ORDER) return set_err(nullptr, PCDM_EINVAL, "rows of a column not strictly increasing");
+    *omega = host[1];
+    return PCDM_OK;
+}
+
 pcdm_status pcdm_selftest_barrier_timeout(uint64_t timeout_ns, void *cuda_stream)
 {
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

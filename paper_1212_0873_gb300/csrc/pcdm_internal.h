@@ -136,6 +136,13 @@ int64_t scan_tile_count(int64_t n);
 cudaError_t launch_padded_scan(const int64_t *col_ptr, int64_t n, int granule, int64_t *pbeg, int64_t *tile,
                                cudaStream_t st);
 
+// No-allocation row counts (kernels_common.cu): the static scratch of the
+// current device (row counters, then flags and result words) and its kernel.
+constexpr int kMaxNoAllocDevices = 64;
+cudaError_t noalloc_rows_scratch(int device, int **rows, int **tail);
+cudaError_t launch_rows_checked(const int64_t *col_ptr, const int32_t *row_idx, int64_t m, int64_t n, int64_t nnz,
+                                int *cnt, int *flags, cudaStream_t st);
+
 // Validation flag bits (setup kernels).
 enum : int {
     FLAG_COLPTR = 1,      // col_ptr not monotone, not starting at 0 or not ending at nnz

@@ -177,3 +177,19 @@ def test_check_schedule_extrapolates_the_linear_rate(B):
     assert f(E, 0, 1e-3, E, 0.0, 1e-6) == E
     assert f(E, E, 1e-2, E, 1e-3, 1e-6) == E
     assert f(0, 0, 1e-1, 1, 1e-2, 1e-6) == 2      # epoch < 1 is taken as 1
+
+
+def test_omega_noalloc_host_checks(B):
+    """pcdm_omega_noalloc rejects, before any device work, what it cannot serve."""
+    L = B.lib()
+    out = ctypes.c_int64(-1)
+    ok = dict(m=10, n=4, nnz=0, col_ptr=1, row_idx=0, val=0, val_dtype=B.PCDM_F64, on_device=1)
+    for case, change in [("host arrays", dict(on_device=0)), ("too many rows", dict(m=B.PCDM_NOALLOC_MAX_ROWS + 1)),
+                         ("negative n", dict(n=-1)), ("no col_ptr", dict(col_ptr=0)),
+                         ("no row_idx", dict(nnz=5))]:
+        csc = B.pcdm_csc(**dict(ok, **change))
+        assert L.pcdm_omega_noalloc(ctypes.byref(csc), ctypes.byref(out), None) == B.PCDM_EINVAL, case
+    assert L.pcdm_omega_noalloc(None, ctypes.byref(out), None) == B.PCDM_EINVAL
+    assert out.value == -1
+    assert B.PCDM_NOALLOC_MAX_ROWS == int(re.search(r"#define PCDM_NOALLOC_MAX_ROWS (\d+)",
+                                                    open(HEADER).read()).group(1))
