@@ -305,7 +305,8 @@ def run_pcdm(a, rank, local, world):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (tpu * st["updates"] / launches) if tpu is not None else None,
-                "kernel": "k_fused (persistent PCDM1 iterations)", "peak_source": peak_kind,
+                "kernel": ("k_gather + k_scatter (two-kernel PCDM1 iterations)" if a.unfused else
+                           "k_fused_pipe (persistent PCDM1 iterations)"), "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes / launches, "avg_launch_ms": avg_launch_s * 1e3,
                 "launches": st["iter_launches"]}
 

@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
 //            then gradient, step, x;
 //   scatter  steps of k-1 and k into the other buffer;
 //   barrier  release-arrive; then TMA copies of the first chunk of column i_{k+1}
-//            into the other slot and L2 prefetch of its tail; then wait
+//            into the other slot; then wait
 // On GB300 the scattered gathers saturate each SM's load/store pipe, so the
 // bulk copies run on the TMA engine and the sampling is integer work only.
 // Values of one 16-byte word of a shared chunk (16 / sizeof(VT) entries).
@@ -714,15 +714,12 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         // Split: the release-arrive publishes x and the scatter; the bulk copies of
         // the next columns (reads of A only, nothing to publish) are issued after
         // it, so the release does not wait for them, and they overlap the wait.
+        // (The column's tail is not prefetched into L2: the extra TMA issue cost
+        // on the last block to arrive outweighed the shorter tail loads.)
         target += gridDim.x;
         grid_arrive(a.bar);
         fence_proxy_async_shared();
         fill(b ^ 1, d_nxt, own);
-        if (own && d_nxt.cnt > kE) {
-            const int64_t tail = ((int64_t(d_nxt.cnt) + G - 1) / G) * G - kE;
-            prefetch_l2_bulk(a.prow + d_nxt.pbeg + kE, uint32_t(tail * 4));
-            prefetch_l2_bulk(a.pval + d_nxt.pbeg + kE, uint32_t(tail * int64_t(sizeof(VT))));
-        }
         if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) {
             wait_buf(b ^ 1);   // the copies just issued land before the block leaves
             return;
