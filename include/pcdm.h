@@ -260,6 +260,82 @@ pcdm_status pcdm_selftest_barrier_timeout(uint64_t timeout_ns, void *cuda_stream
 #define PCDM_NOALLOC_MAX_ROWS 1048576
 pcdm_status pcdm_omega_noalloc(const pcdm_csc *A, int64_t *omega, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched solver: nrhs <= 32 LASSO problems that share A,
+ *   min_x 1/2 ||A x - b_l||^2 + lambda_l ||x||_1,  l = 0 .. nrhs-1,
+ * solved together.  Each problem runs Algorithm 1 exactly as pcdm_step would
+ * (the same sampler, the same S_k for every problem, beta of Theorem ESO-nice),
+ * so problem l follows the trajectory of a single-problem handle created with
+ * b_l and lambda_l and stepped with the same seed.  What the batch shares is
+ * the read of each sampled column of A: the residuals and iterates are stored
+ * interleaved by problem, so one column's gathers read nrhs consecutive
+ * residual entries of a row.  The paper's PCDM1 is one problem; the batch is
+ * this library's data-parallel form of many (regularisation paths, multiple
+ * right-hand sides).  Conventions as above: one stream (from opts/cuda_stream),
+ * status returns, not thread-safe.
+ * ------------------------------------------------------------------------ */
+typedef struct pcdm_batch_ctx *pcdm_batch_handle;
+
+/*
+ * A           as for pcdm_create (validated the same way)
+ * nrhs        number of problems, 1 .. 32
+ * B           nrhs right-hand sides, each m entries of b_dtype, stored one after
+ *             the other (b_l at B + l*m); host or device as A->on_device says;
+ *             copied and kept in FP64
+ * lambdas     nrhs host doubles, finite and >= 0
+ * opts        as for pcdm_create (xg_dtype, refresh_every, check_every,
+ *             barrier_timeout_ns, profile are used)
+ * Errors: those of pcdm_create, EINVAL for nrhs out of range, a bad lambda or a
+ * non-finite value in B.
+ */
+pcdm_status pcdm_batch_create(const pcdm_csc *A, int64_t nrhs, const void *B, int32_t b_dtype,
+                              const double *lambdas, const pcdm_opts *opts, void *cuda_stream,
+                              pcdm_batch_handle *out);
+
+/* `iters` iterations of every active problem, continuing the batch's counter k. */
+pcdm_status pcdm_batch_step(pcdm_batch_handle h, int64_t tau, int64_t iters, uint64_t seed);
+
+/* Recompute every residual g_l = A x_l - b_l in FP64. */
+pcdm_status pcdm_batch_refresh(pcdm_batch_handle h);
+
+/* Refresh, then the duality gap of every problem as pcdm_gap defines it;
+ * primal, dual, gap: nrhs host doubles each, any may be NULL. */
+pcdm_status pcdm_batch_gap(pcdm_batch_handle h, double *primal, double *dual, double *gap);
+
+/* Iterate until every problem has gap / primal <= rel_gap_tol.  A problem that
+ * reaches the tolerance at a check is frozen (its x no longer changes) for the
+ * rest of the call; the checks follow opts.check_every or, when 0, the schedule
+ * of pcdm_next_check_interval applied to the largest relative gap among the
+ * problems still running.  rel_gaps: nrhs host doubles (may be NULL).
+ * PCDM_ENOTCONV when max_iters ran out first. */
+pcdm_status pcdm_batch_solve(pcdm_batch_handle h, int64_t tau, uint64_t seed, double rel_gap_tol,
+                             int64_t max_iters, int64_t *iters_done, double *rel_gaps);
+
+/* x of every problem, x_l at X + l*n (n x nrhs doubles), host or device. */
+pcdm_status pcdm_batch_get_x(pcdm_batch_handle h, double *X_out, int32_t on_device);
+
+/* Replace every x (same layout; warm start) and recompute the residuals. */
+pcdm_status pcdm_batch_set_x(pcdm_batch_handle h, const double *X_in, int32_t on_device);
+
+/* New lambdas (nrhs host doubles, finite and >= 0); x and the residuals are kept
+ * (the next point of a regularisation path starts from the current x). */
+pcdm_status pcdm_batch_set_lambda(pcdm_batch_handle h, const double *lambdas);
+
+/* x = 0, g_l = -b_l, k = 0; clears a failed state. */
+pcdm_status pcdm_batch_reset(pcdm_batch_handle h);
+
+/* Counters as in pcdm_stats, with updates counted per problem (tau per active
+ * problem per iteration) and gathered / scattered nonzeros counted per column
+ * read. */
+pcdm_status pcdm_batch_get_stats(pcdm_batch_handle h, pcdm_stats *out);
+pcdm_status pcdm_batch_reset_stats(pcdm_batch_handle h);
+
+void pcdm_batch_destroy(pcdm_batch_handle h);
+
+/* Last error of the batch handle; with NULL, that of a failed pcdm_batch_create
+ * on this thread. */
+const char *pcdm_batch_last_error(pcdm_batch_handle h);
+
 /* Free everything the handle owns.  NULL is ignored. */
 void pcdm_destroy(pcdm_handle h);
 

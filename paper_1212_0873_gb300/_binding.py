@@ -46,6 +46,20 @@ SIGNATURES = {
     "pcdm_solve": (_i32, [_ptr, _i64, _u64, _dbl, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "pcdm_next_check_interval": (_i64, [_i64, _i64, ctypes.c_double, _i64, ctypes.c_double, ctypes.c_double]),
     "pcdm_omega_noalloc": (_i32, [ctypes.POINTER(pcdm_csc), ctypes.POINTER(_i64), _ptr]),
+    "pcdm_batch_create": (_i32, [ctypes.POINTER(pcdm_csc), _i64, _ptr, _i32, _ptr, ctypes.POINTER(pcdm_opts), _ptr,
+                                 _ptr]),
+    "pcdm_batch_step": (_i32, [_ptr, _i64, _i64, _u64]),
+    "pcdm_batch_refresh": (_i32, [_ptr]),
+    "pcdm_batch_gap": (_i32, [_ptr, _ptr, _ptr, _ptr]),
+    "pcdm_batch_solve": (_i32, [_ptr, _i64, _u64, _dbl, _i64, _ptr, _ptr]),
+    "pcdm_batch_get_x": (_i32, [_ptr, _ptr, _i32]),
+    "pcdm_batch_set_x": (_i32, [_ptr, _ptr, _i32]),
+    "pcdm_batch_set_lambda": (_i32, [_ptr, _ptr]),
+    "pcdm_batch_reset": (_i32, [_ptr]),
+    "pcdm_batch_get_stats": (_i32, [_ptr, ctypes.POINTER(pcdm_stats)]),
+    "pcdm_batch_reset_stats": (_i32, [_ptr]),
+    "pcdm_batch_destroy": (None, [_ptr]),
+    "pcdm_batch_last_error": (ctypes.c_char_p, [_ptr]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -237,3 +251,81 @@ def pcdm_omega_noalloc(csc, stream):
     out = _i64(0)
     _check(lib().pcdm_omega_noalloc(ctypes.byref(csc), ctypes.byref(out), _stream(stream)), None)
     return int(out.value)
+
+
+# ---------------------------------------------------------------------------- batched solver
+def _bcheck(status, handle=None):
+    if status != PCDM_OK:
+        msg = lib().pcdm_batch_last_error(handle)
+        raise PcdmError(status, (msg or b"").decode(errors="replace"))
+
+
+def pcdm_batch_create(A, nrhs, B_ptr, b_dtype, lambdas, opts=None, stream=0):
+    lam = (ctypes.c_double * int(nrhs))(*[float(v) for v in lambdas])
+    h = _ptr()
+    st = lib().pcdm_batch_create(ctypes.byref(A), int(nrhs), _ptr(B_ptr), int(b_dtype), ctypes.cast(lam, _ptr),
+                                 ctypes.byref(opts) if opts is not None else None, _stream(stream), ctypes.byref(h))
+    _bcheck(st, None)
+    return h
+
+
+def pcdm_batch_step(h, tau, iters, seed):
+    _bcheck(lib().pcdm_batch_step(h, int(tau), int(iters), int(seed) & (2**64 - 1)), h)
+
+
+def pcdm_batch_refresh(h):
+    _bcheck(lib().pcdm_batch_refresh(h), h)
+
+
+def pcdm_batch_gap(h, nrhs):
+    p, d, g = (ctypes.c_double * nrhs)(), (ctypes.c_double * nrhs)(), (ctypes.c_double * nrhs)()
+    _bcheck(lib().pcdm_batch_gap(h, ctypes.cast(p, _ptr), ctypes.cast(d, _ptr), ctypes.cast(g, _ptr)), h)
+    return list(p), list(d), list(g)
+
+
+def pcdm_batch_solve(h, nrhs, tau, seed, rel_gap_tol, max_iters):
+    """Returns (converged, iters_done, [rel_gap per problem])."""
+    it = _i64()
+    rel = (ctypes.c_double * nrhs)()
+    st = lib().pcdm_batch_solve(h, int(tau), int(seed) & (2**64 - 1), float(rel_gap_tol), int(max_iters),
+                                ctypes.byref(it), ctypes.cast(rel, _ptr))
+    if st == PCDM_ENOTCONV:
+        return False, it.value, list(rel)
+    _bcheck(st, h)
+    return True, it.value, list(rel)
+
+
+def pcdm_batch_get_x(h, ptr, on_device):
+    _bcheck(lib().pcdm_batch_get_x(h, _ptr(ptr), int(on_device)), h)
+
+
+def pcdm_batch_set_x(h, ptr, on_device):
+    _bcheck(lib().pcdm_batch_set_x(h, _ptr(ptr), int(on_device)), h)
+
+
+def pcdm_batch_set_lambda(h, lambdas):
+    lam = (ctypes.c_double * len(lambdas))(*[float(v) for v in lambdas])
+    _bcheck(lib().pcdm_batch_set_lambda(h, ctypes.cast(lam, _ptr)), h)
+
+
+def pcdm_batch_reset(h):
+    _bcheck(lib().pcdm_batch_reset(h), h)
+
+
+def pcdm_batch_get_stats(h):
+    s = pcdm_stats()
+    _bcheck(lib().pcdm_batch_get_stats(h, ctypes.byref(s)), h)
+    return {name: getattr(s, name) for name, _ in pcdm_stats._fields_}
+
+
+def pcdm_batch_reset_stats(h):
+    _bcheck(lib().pcdm_batch_reset_stats(h), h)
+
+
+def pcdm_batch_destroy(h):
+    lib().pcdm_batch_destroy(h)
+
+
+def pcdm_batch_last_error(h=None):
+    msg = lib().pcdm_batch_last_error(h)
+    return (msg or b"").decode(errors="replace")

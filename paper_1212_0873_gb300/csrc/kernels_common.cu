@@ -235,6 +235,153 @@ cudaError_t launch_gap_finish(const double *pc, int nbc, const double *pr, int n
     return cudaGetLastError();
 }
 
+// Interleaving of nsrc vectors of length len (src[l * len + r], FP64 or FP32)
+// into dst[r * bp + l] (FP64); the padding lanes l >= nsrc get 0.
+__global__ void k_interleave(const void *src, int src_is_f32, int64_t len, int nsrc, int bp, double *dst)
+{
+    const int64_t total = len * bp;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int64_t r = e / bp;
+        const int l = int(e - r * bp);
+        double v = 0.0;
+        if (l < nsrc) {
+            const int64_t q = int64_t(l) * len + r;
+            v = src_is_f32 ? double(static_cast<const float *>(src)[q]) : static_cast<const double *>(src)[q];
+        }
+        dst[e] = v;
+    }
+}
+
+cudaError_t launch_interleave(const void *src, int src_is_f32, int64_t len, int nsrc, int bp, double *dst,
+                              cudaStream_t st)
+{
+    if (len <= 0) return cudaSuccess;
+    k_interleave<<<grid_for(len * bp), 256, 0, st>>>(src, src_is_f32, len, nsrc, bp, dst);
+    return cudaGetLastError();
+}
+
+// The inverse for the first nout lanes: dst[l * len + r] = src[r * bp + l].
+__global__ void k_deinterleave(const double *src, int64_t len, int nout, int bp, double *dst)
+{
+    const int64_t total = len * nout;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int64_t r = e / nout;
+        const int l = int(e - r * nout);
+        dst[int64_t(l) * len + r] = src[r * bp + l];
+    }
+}
+
+cudaError_t launch_deinterleave(const double *src, int64_t len, int nout, int bp, double *dst, cudaStream_t st)
+{
+    if (len <= 0) return cudaSuccess;
+    k_deinterleave<<<grid_for(len * nout), 256, 0, st>>>(src, len, nout, bp, dst);
+    return cudaGetLastError();
+}
+
+// Batched gap, row part: for right-hand side l (element e = r * bp + l of the
+// interleaved vectors) block partials part[(block * bp + l) * 2 + {0,1}] of
+// ||r_l||^2 and b_l^T r_l.  The grid stride is a multiple of bp, so each thread
+// keeps one l.
+__global__ void __launch_bounds__(kBlock) k_batch_gap_rows(const double *__restrict__ R,
+                                                           const double *__restrict__ Bm, int64_t total, int bp,
+                                                           double *__restrict__ part)
+{
+    const int64_t stride = int64_t(gridDim.x) * kBlock;
+    double rr = 0.0, br = 0.0;
+    for (int64_t e = int64_t(blockIdx.x) * kBlock + threadIdx.x; e < total; e += stride) {
+        const double r = R[e];
+        rr += r * r;
+        br += Bm[e] * r;
+    }
+    __shared__ double sm[2][kBlock];
+    sm[0][threadIdx.x] = rr;
+    sm[1][threadIdx.x] = br;
+    __syncthreads();
+    if (threadIdx.x < bp) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int q = threadIdx.x; q < kBlock; q += bp) {
+            a0 += sm[0][q];
+            a1 += sm[1][q];
+        }
+        part[(int64_t(blockIdx.x) * bp + threadIdx.x) * 2 + 0] = a0;
+        part[(int64_t(blockIdx.x) * bp + threadIdx.x) * 2 + 1] = a1;
+    }
+}
+
+cudaError_t launch_batch_gap_rows(const double *R, const double *Bm, int64_t m, int bp, double *part, int blocks,
+                                  cudaStream_t st)
+{
+    if (bp < 1 || kBlock % bp != 0) return cudaErrorInvalidValue;
+    k_batch_gap_rows<<<blocks, kBlock, 0, st>>>(R, Bm, m * bp, bp, part);
+    return cudaGetLastError();
+}
+
+// Batched gap records: block l of the grid reduces right-hand side l's partials
+// and writes out[l * 9 + q] with the formulas of k_gap_finish.
+__global__ void __launch_bounds__(kFinishBlock) k_batch_gap_finish(const double *pc, int nbc, const double *pr,
+                                                                   int nbr, int bp, const double *lambda,
+                                                                   double *out)
+{
+    const int l = blockIdx.x;
+    double cmax = 0.0, l1 = 0.0, xc = 0.0, rr = 0.0, br = 0.0;
+    for (int q = threadIdx.x; q < nbc; q += kFinishBlock) {
+        const double *p = pc + (int64_t(q) * bp + l) * 3;
+        cmax = fmax(cmax, p[0]);
+        l1 += p[1];
+        xc += p[2];
+    }
+    for (int q = threadIdx.x; q < nbr; q += kFinishBlock) {
+        const double *p = pr + (int64_t(q) * bp + l) * 2;
+        rr += p[0];
+        br += p[1];
+    }
+    __shared__ double sm[5][kFinishBlock / 32];
+    cmax = warp_max(cmax);
+    l1 = warp_sum(l1);
+    xc = warp_sum(xc);
+    rr = warp_sum(rr);
+    br = warp_sum(br);
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        sm[0][w] = cmax;
+        sm[1][w] = l1;
+        sm[2][w] = xc;
+        sm[3][w] = rr;
+        sm[4][w] = br;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < kFinishBlock / 32; ++w) {
+            a[0] = fmax(a[0], sm[0][w]);
+            for (int q = 1; q < 5; ++q) a[q] += sm[q][w];
+        }
+        const double lam = lambda[l];
+        const double cinf = a[0], l1s = a[1], xcs = a[2], rrs = a[3], brs = a[4];
+        double s = 1.0;
+        if (cinf > 0.0 && lam / cinf < 1.0) s = lam / cinf;
+        double *o = out + int64_t(l) * 9;
+        o[0] = 0.5 * rrs + lam * l1s;
+        o[1] = -0.5 * s * s * rrs - s * brs;
+        o[2] = 0.5 * (1.0 - s) * (1.0 - s) * rrs + (lam * l1s + s * xcs);
+        o[3] = cinf;
+        o[4] = s;
+        o[5] = rrs;
+        o[6] = brs;
+        o[7] = l1s;
+        o[8] = xcs;
+    }
+}
+
+cudaError_t launch_batch_gap_finish(const double *pc, int nbc, const double *pr, int nbr, int bp,
+                                    const double *lambda, double *out, cudaStream_t st)
+{
+    k_batch_gap_finish<<<bp, kFinishBlock, 0, st>>>(pc, nbc, pr, nbr, bp, lambda, out);
+    return cudaGetLastError();
+}
+
 // Barrier self-test: the wait target is one arrival more than the grid has, so
 // every block's wait must end by its time budget.
 __global__ void k_barrier_selftest(unsigned long long *bar, int *status, uint64_t timeout_ns)

@@ -10,119 +10,14 @@
 #include <utility>
 #include <vector>
 
-#include "pcdm.h"
-#include "pcdm_internal.h"
+#include "pcdm_host.h"
 
 using namespace pcdm;
+using namespace pcdm_host;
+
+thread_local std::string pcdm_host::g_free_error;
 
 namespace {
-
-thread_local std::string g_free_error;   // errors of calls without a handle
-
-constexpr int64_t kMaxItersPerLaunch = 1 << 16;
-constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
-
-int64_t dtype_bytes(int dt)
-{
-    switch (dt) {
-    case PCDM_F64: return 8;
-    case PCDM_F32: return 4;
-    case PCDM_BF16: return 2;
-    default: return 0;
-    }
-}
-
-}  // namespace
-
-struct pcdm_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int64_t m = 0, n = 0, nnz = 0;
-    int val_dtype = PCDM_F64, xg_dtype = PCDM_F64;
-    double lambda = 0.0;
-    pcdm_opts opts{};
-    int W = 8;
-    int sms = 0;
-
-    void *desc = nullptr;         // ColDesc<XT>[n]: padded start, count, 1/L_i
-    int32_t *prow = nullptr;      // padded row indices (P + kSlack)
-    void *pval = nullptr;         // padded values (P + kSlack)
-    int64_t P = 0;                // padded entries
-    double *b = nullptr;          // FP64 copy of b
-    double *L64 = nullptr;        // L_i in FP64
-    double *x = nullptr;          // n FP64 entries
-    void *g = nullptr;            // m entries of xg dtype
-    void *g2 = nullptr;           // second residual buffer of the pipelined kernel
-    bool g2_valid = false;        // g2 holds the same residual as g
-    double *g64 = nullptr;        // FP64 residual of the refresh (aliases g in the FP64 form)
-    int32_t *S[2] = {nullptr, nullptr};
-    void *h = nullptr;
-    int64_t tau_cap = 0;
-    unsigned long long *counters = nullptr;   // [3]
-    unsigned long long *bar = nullptr;
-    int *status = nullptr;
-    double *gap_part = nullptr;
-    double *gap_out = nullptr;    // 9 doubles
-    int gap_blocks = 0, gap_row_blocks = 0;
-    double *host_buf = nullptr;   // pinned: 9 gap doubles + status + counters
-
-    int64_t omega = 0;
-    int64_t k = 0;
-    bool sample_valid = false;
-    uint64_t sample_seed = 0;
-    int64_t sample_tau = 0, sample_k = -1;
-    bool failed = false;
-    std::string err;
-
-    int64_t st_iterations = 0, st_updates = 0, st_launches = 0, st_refreshes = 0, st_gaps = 0;
-    int64_t st_kernels = 0;   // every kernel launched by this handle
-    double st_kernel_ms = 0.0;
-    std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
-};
-
-namespace {
-
-pcdm_status set_err(pcdm_handle h, pcdm_status s, const std::string &msg)
-{
-    if (h)
-        h->err = msg;
-    else
-        g_free_error = msg;
-    return s;
-}
-
-pcdm_status cuda_fail(pcdm_handle h, cudaError_t e, const char *what)
-{
-    std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
-    if (e == cudaErrorMemoryAllocation) {
-        cudaGetLastError();
-        return set_err(h, PCDM_ENOMEM, msg);
-    }
-    if (h) h->failed = true;
-    return set_err(h, PCDM_ECUDA, msg);
-}
-
-#define CK(h, ...)                                                   \
-    do {                                                             \
-        cudaError_t e_ = (__VA_ARGS__);                              \
-        if (e_ != cudaSuccess) return cuda_fail((h), e_, #__VA_ARGS__); \
-    } while (0)
-
-template <typename T>
-cudaError_t dalloc(T **p, int64_t count)
-{
-    *p = nullptr;
-    if (count <= 0) count = 1;
-    return cudaMalloc(reinterpret_cast<void **>(p), size_t(count) * sizeof(T));
-}
-
-cudaError_t dalloc_bytes(void **p, int64_t bytes)
-{
-    *p = nullptr;
-    if (bytes <= 0) bytes = 16;
-    return cudaMalloc(p, size_t(bytes));
-}
 
 void free_all(pcdm_handle h)
 {
@@ -147,53 +42,6 @@ int auto_lanes(int64_t nnz, int64_t n)
     int W = 1;
     while (W < 32 && double(W * kLaneRun) < mean) W *= 2;
     return W;
-}
-
-double beta_nice(int64_t omega, int64_t tau, int64_t n)
-{
-    const double om = double(omega < 1 ? 1 : omega);
-    const double denom = double(n - 1 > 1 ? n - 1 : 1);
-    return 1.0 + (om - 1.0) * (double(tau) - 1.0) / denom;
-}
-
-cudaMemcpyKind copy_kind(int on_device_src, int on_device_dst)
-{
-    if (on_device_src && on_device_dst) return cudaMemcpyDeviceToDevice;
-    if (on_device_src) return cudaMemcpyDeviceToHost;
-    if (on_device_dst) return cudaMemcpyHostToDevice;
-    return cudaMemcpyHostToHost;
-}
-
-// Synchronise, fold finished event timings into the stats, and read the
-// device status word.  Every call that returns host values goes through here.
-pcdm_status sync_check(pcdm_handle h)
-{
-    int *hs = reinterpret_cast<int *>(h->host_buf + 9);
-    CK(h, cudaMemcpyAsync(hs, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
-    for (auto &pr : h->ev_pending) {
-        float ms = 0.f;
-        CK(h, cudaEventElapsedTime(&ms, pr.first, pr.second));
-        h->st_kernel_ms += ms;
-        h->ev_free.push_back(pr.first);
-        h->ev_free.push_back(pr.second);
-    }
-    h->ev_pending.clear();
-    if (*hs != DEV_OK) {
-        h->failed = true;
-        return set_err(h, PCDM_ETIMEOUT, "a grid-barrier wait of the fused kernel ran out of its time budget");
-    }
-    return PCDM_OK;
-}
-
-cudaError_t take_event(pcdm_handle h, cudaEvent_t *e)
-{
-    if (!h->ev_free.empty()) {
-        *e = h->ev_free.back();
-        h->ev_free.pop_back();
-        return cudaSuccess;
-    }
-    return cudaEventCreate(e);
 }
 
 pcdm_status ensure_tau(pcdm_handle h, int64_t tau)
@@ -374,16 +222,6 @@ pcdm_status gap_t(pcdm_handle h)
     return sync_check(h);
 }
 
-// Dispatch on the (value, iterate) dtype pair.
-template <typename F>
-pcdm_status dispatch(pcdm_handle h, F &&f)
-{
-    if (h->val_dtype == PCDM_F64 && h->xg_dtype == PCDM_F64) return f((double *)nullptr, (double *)nullptr);
-    if (h->val_dtype == PCDM_F32 && h->xg_dtype == PCDM_F32) return f((float *)nullptr, (float *)nullptr);
-    if (h->val_dtype == PCDM_BF16 && h->xg_dtype == PCDM_F32) return f((bf16_t *)nullptr, (float *)nullptr);
-    return set_err(h, PCDM_EINVAL, "unsupported dtype pair");
-}
-
 pcdm_status do_refresh(pcdm_handle h)
 {
     return dispatch(h, [&](auto *vt, auto *xt) {
@@ -402,13 +240,6 @@ pcdm_status do_gap(pcdm_handle h, double *rec)
     });
     if (s != PCDM_OK) return s;
     for (int q = 0; q < 9; ++q) rec[q] = h->host_buf[q];
-    return PCDM_OK;
-}
-
-pcdm_status usable(pcdm_handle h)
-{
-    if (!h) return set_err(nullptr, PCDM_EINVAL, "NULL handle");
-    if (h->failed) return set_err(h, PCDM_ESTATE, "handle is in a failed state (" + h->err + "); call pcdm_reset");
     return PCDM_OK;
 }
 

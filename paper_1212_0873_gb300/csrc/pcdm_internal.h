@@ -114,6 +114,53 @@ struct Kernels {
                                 const double *x, int64_t n, double *part, int blocks, int W, cudaStream_t st);
 };
 
+template <typename VT, typename XT>
+struct BatchArgs {
+    const ColDesc<XT> *desc;
+    const int32_t *prow;
+    const VT *pval;
+    double *X;                  // n x bp, FP64
+    XT *G;                      // m x bp
+    XT *H;                      // tau x bp: the steps of the current iteration
+    int32_t *S;                 // tau: S_k of the current iteration
+    const double *lambda;       // bp
+    const int *active;          // bp: 0 = this problem is frozen (converged or padding)
+    double inv_beta;
+    int64_t n, tau;
+    uint64_t seed;
+    unsigned long long *counters;   // [0] gathered nnz (per column), [1] scattered nnz (per column), [2] nonzero steps
+    unsigned long long *bar;
+    int *status;
+    uint64_t timeout_ns;
+};
+
+constexpr int kBatchBlock = 256;
+
+// Batched kernels (batch_kernels.cuh), bp in {4, 8, 16, 32} right-hand sides.
+template <typename VT, typename XT>
+struct BatchKernels {
+    // Persistent cooperative iterations k0 .. k0+iters-1 (two bounded grid barriers each).
+    static cudaError_t iter(const BatchArgs<VT, XT> &a, int bp, int blocks, int64_t k0, int64_t iters,
+                            cudaStream_t st);
+    static int iter_max_blocks(int bp);
+    // G64 (m x bp, holding -b) += A X over the columns with a nonzero x.
+    static cudaError_t refresh(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *X,
+                               int64_t n, int bp, double *G64, int blocks, cudaStream_t st);
+    // Block partials of max|c|, sum|x|, sum x c per right-hand side, c = A^T R.
+    static cudaError_t gap_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *R,
+                                const double *X, int64_t n, int bp, double *part, int blocks, cudaStream_t st);
+};
+// Per right-hand side: block partials of ||r||^2, b^T r over the interleaved m x bp
+// vectors, and the final gap records out[l * 9 + q] (q as in launch_gap_finish).
+cudaError_t launch_batch_gap_rows(const double *R, const double *Bm, int64_t m, int bp, double *part, int blocks,
+                                  cudaStream_t st);
+// src[l * len + r] (FP64, or FP32 when src_is_f32) -> dst[r * bp + l] (FP64, 0 for l >= nsrc), and back.
+cudaError_t launch_interleave(const void *src, int src_is_f32, int64_t len, int nsrc, int bp, double *dst,
+                              cudaStream_t st);
+cudaError_t launch_deinterleave(const double *src, int64_t len, int nout, int bp, double *dst, cudaStream_t st);
+cudaError_t launch_batch_gap_finish(const double *pc, int nbc, const double *pr, int nbr, int bp,
+                                    const double *lambda, double *out, cudaStream_t st);
+
 // Type-independent kernels (kernels_common.cu).
 cudaError_t launch_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S, cudaStream_t st);
 cudaError_t launch_check_colptr(const int64_t *col_ptr, int64_t n, int64_t nnz, int *flags, cudaStream_t st);

@@ -175,3 +175,101 @@ class Lasso:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchLasso:
+    """nrhs <= 32 problems min 1/2 ||A x - b_l||^2 + lam_l ||x||_1 sharing A, solved together
+    (pcdm_batch_*).  B is (nrhs, m): row l is b_l."""
+
+    def __init__(self, m, n, col_ptr, row_idx, val, B_rhs, lams, *, xg_dtype=None, refresh_every=0, check_every=0,
+                 profile=False, barrier_timeout_ns=None, stream=None):
+        val_dtype = _val_code(val)
+        if xg_dtype is None:
+            xg_dtype = "f64" if val_dtype == "f64" else "f32"
+        self.m, self.n = int(m), int(n)
+        self.nrhs = int(B_rhs.shape[0])
+        if tuple(B_rhs.shape) != (self.nrhs, self.m):
+            raise ValueError("B must have shape (nrhs, m)")
+        self.val_dtype, self.xg_dtype = val_dtype, xg_dtype
+        p_cp, d_cp = _ptr_and_device(col_ptr)
+        p_ri, d_ri = _ptr_and_device(row_idx)
+        p_v, d_v = _ptr_and_device(val)
+        p_b, d_b = _ptr_and_device(B_rhs)
+        if len({d_cp, d_ri, d_v, d_b}) != 1:
+            raise ValueError("A and B must all be host arrays or all be device tensors")
+        nnz = int(col_ptr[-1]) if not _is_tensor(col_ptr) else int(col_ptr[-1].item())
+        A = B.pcdm_csc(self.m, self.n, nnz, p_cp, p_ri, p_v, B.DTYPE_CODES[val_dtype], d_cp)
+        opts = B.pcdm_default_opts()
+        opts.xg_dtype = B.DTYPE_CODES[xg_dtype]
+        opts.refresh_every = int(refresh_every)
+        opts.check_every = int(check_every)
+        opts.profile = 1 if profile else 0
+        if barrier_timeout_ns is not None:
+            opts.barrier_timeout_ns = int(barrier_timeout_ns)
+        b_dt = B.PCDM_F32 if (str(getattr(B_rhs, "dtype", "")) in ("float32", "torch.float32")) else B.PCDM_F64
+        self.stream = current_stream() if stream is None else stream
+        self.lams = [float(v) for v in lams]
+        if len(self.lams) != self.nrhs:
+            raise ValueError("one lambda per right-hand side")
+        self._h = B.pcdm_batch_create(A, self.nrhs, p_b, b_dt, self.lams, opts, self.stream)
+
+    def step(self, tau, iters, seed=0):
+        B.pcdm_batch_step(self._h, tau, iters, seed)
+
+    def refresh(self):
+        B.pcdm_batch_refresh(self._h)
+
+    def gap(self):
+        p, d, g = B.pcdm_batch_gap(self._h, self.nrhs)
+        p, d, g = np.array(p), np.array(d), np.array(g)
+        return dict(primal=p, dual=d, gap=g, rel_gap=g / np.maximum(p, 1e-300))
+
+    def solve(self, tau, seed=0, tol=1e-6, max_iters=10**9):
+        """Returns (all converged, iterations, relative gap per problem)."""
+        ok, it, rel = B.pcdm_batch_solve(self._h, self.nrhs, tau, seed, tol, max_iters)
+        return ok, it, np.array(rel)
+
+    def x(self):
+        out = np.empty((self.nrhs, self.n), dtype=np.float64)
+        B.pcdm_batch_get_x(self._h, out.ctypes.data, 0)
+        return out
+
+    def set_x(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64) if not _is_tensor(X) else X
+        if tuple(X.shape) != (self.nrhs, self.n):
+            raise ValueError("X must have shape (nrhs, n)")
+        p, d = _ptr_and_device(X)
+        B.pcdm_batch_set_x(self._h, p, d)
+
+    def set_lambda(self, lams):
+        lams = [float(v) for v in lams]
+        if len(lams) != self.nrhs:
+            raise ValueError("one lambda per right-hand side")
+        B.pcdm_batch_set_lambda(self._h, lams)
+        self.lams = lams
+
+    def reset(self):
+        B.pcdm_batch_reset(self._h)
+
+    def stats(self):
+        return B.pcdm_batch_get_stats(self._h)
+
+    def reset_stats(self):
+        B.pcdm_batch_reset_stats(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.pcdm_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -193,3 +193,19 @@ def test_omega_noalloc_host_checks(B):
     assert out.value == -1
     assert B.PCDM_NOALLOC_MAX_ROWS == int(re.search(r"#define PCDM_NOALLOC_MAX_ROWS (\d+)",
                                                     open(HEADER).read()).group(1))
+
+
+def test_batch_create_host_checks(B):
+    """pcdm_batch_create rejects its own arguments before any device work."""
+    L = B.lib()
+    h = ctypes.c_void_p()
+    csc = B.pcdm_csc(m=10, n=4, nnz=0, col_ptr=1, row_idx=0, val=0, val_dtype=B.PCDM_F64, on_device=1)
+    lam = (ctypes.c_double * 40)(*([0.5] * 40))
+    bad = (ctypes.c_double * 2)(0.5, -1.0)
+    for nrhs, lams in [(0, lam), (33, lam), (2, bad)]:
+        st = L.pcdm_batch_create(ctypes.byref(csc), nrhs, ctypes.c_void_p(1), B.PCDM_F64,
+                                 ctypes.cast(lams, ctypes.c_void_p), None, None, ctypes.byref(h))
+        assert st == B.PCDM_EINVAL and not h.value
+    assert L.pcdm_batch_step(None, 1, 1, 0) == B.PCDM_EINVAL
+    assert L.pcdm_batch_gap(None, None, None, None) == B.PCDM_EINVAL
+    L.pcdm_batch_destroy(None)
