@@ -20,53 +20,117 @@
 
 namespace pcdm {
 
-// The step of eq. (h(x)) for one coordinate of one problem, returning h and
-// the new x.  FP64 iterates: the FP64 step of prox_step.  FP32 iterates: the
-// step is formed in FP32 from the gradient, without rounding x: with
+// The step of eq. (h(x)) for one coordinate of one problem: returns h in the
+// iterate dtype and sets the new x.  FP64 iterates: prox_step.  FP32 iterates:
+// the step is formed in FP32 from the gradient, without rounding x: with
 // d = -grad/(beta L) and t = lambda/(beta L),
-//   x + d >  t  ->  h = d - t,   x + d < -t  ->  h = d + t,   else h = -x,
-// which is soft(x + d, t) - x; only the comparison sees x in FP32.  x + h is
+//   x + d >  t  ->  h = d - t,   x + d < -t  ->  h = d + t,   else x -> 0,
+// which is soft(x + d, t) - x; only the comparison sees x in FP32, and x + h is
 // formed in FP64.  The fixed point (h = 0 exactly when d = -/+ t, i.e.
-// grad = -/+ lambda) does not depend on the precision of x.
+// grad = -/+ lambda) does not depend on the precision of x.  Apart from the
+// conversion of x, FP64 work happens only when x moves (GB300 issues about 2
+// FP64 operations per clock per SM).
 template <typename XT>
-__device__ __forceinline__ double step_delta(double xi, XT grad, XT invL, double inv_beta, double lambda, double &xn)
+__device__ __forceinline__ XT step_delta(double xi, XT grad, XT invL, XT inv_beta, XT lambda, double &xn)
 {
     if constexpr (sizeof(XT) == 8) {
         xn = prox_step(xi, grad, invL, inv_beta, lambda);
         return xn - xi;
     } else {
+        const float xf = float(xi);
         if (invL == 0.f) {
             xn = 0.0;
-            return -xi;
+            return -xf;
         }
-        const float ibl = invL * float(inv_beta);
-        const float t = float(lambda) * ibl;
+        const float ibl = invL * inv_beta;
+        const float t = lambda * ibl;
         const float d = -grad * ibl;
-        const float u = float(xi) + d;
-        double h;
-        if (u > t) {
-            h = double(d - t);
-            xn = xi + h;
-        } else if (u < -t) {
-            h = double(d + t);
-            xn = xi + h;
-        } else {
-            h = -xi;
-            xn = 0.0;
+        const float u = xf + d;
+        if (u > t || u < -t) {
+            const float h = u > t ? d - t : d + t;
+            xn = xi + double(h);
+            return h;
         }
-        return h;
+        xn = 0.0;
+        return -xf;
     }
 }
 
+// Shared-memory slot of one column of a round: the raw 16-byte descriptor,
+// then the first kE row indices, then the first kE values.
+template <typename VT>
+__host__ __device__ constexpr int batch_slot_bytes()
+{
+    return 16 + 4 * kE + kE * int(sizeof(VT));
+}
 
+template <typename VT>
+__host__ __device__ constexpr size_t batch_smem_bytes()
+{
+    return size_t(kBatchBlock) * size_t(batch_slot_bytes<VT>());
+}
+
+// The gradients of one column for the group's BP problems, from its slot
+// (rows and values broadcast to every lane) and, past kE entries, from memory.
+template <typename VT, typename XT, int BP>
+__device__ __forceinline__ XT batch_column_dot(const BatchArgs<VT, XT> &a, const unsigned char *slot,
+                                               const Col<XT> &c, int lane)
+{
+    constexpr int EPW = 16 / int(sizeof(VT));
+    const int valid = c.cnt < kE ? c.cnt : kE;
+    XT gv[kE];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 r4 = reinterpret_cast<const uint4 *>(slot + 16)[q];
+        const int32_t r[4] = {int32_t(r4.x), int32_t(r4.y), int32_t(r4.z), int32_t(r4.w)};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            gv[4 * q + t] = (4 * q + t < valid) ? ldcg(a.G + int64_t(r[t]) * BP + lane) : XT(0);
+    }
+    XT acc = XT(0);
+#pragma unroll
+    for (int w = 0; w < kE / EPW; ++w) {
+        XT vw[EPW];
+        decode_word<VT, XT>(reinterpret_cast<const uint4 *>(slot + 16 + 4 * kE)[w], vw);
+#pragma unroll
+        for (int q = 0; q < EPW; ++q)
+            if (w * EPW + q < valid) acc = fma(vw[q], gv[w * EPW + q], acc);
+    }
+    for (int cs = kE; cs < c.cnt; cs += kE) {   // long columns: the rest from memory
+        Chunk<kE, XT> t;
+        ld_chunk<kE>(t, a.prow, a.pval, c.pbeg + cs);
+        const int v = c.cnt - cs;
+#pragma unroll
+        for (int e = 0; e < kE; ++e) gv[e] = (e < v) ? ldcg(a.G + int64_t(t.row[e]) * BP + lane) : XT(0);
+#pragma unroll
+        for (int e = 0; e < kE; ++e)
+            if (e < v) acc = fma(t.val[e], gv[e], acc);
+    }
+    return acc;
+}
+
+// Persistent iterations k0 .. k0+iters-1.  A group of BP lanes takes the
+// positions grp + (r*BP + q)*ngrp (q < BP) in rounds r.  In a round, lane q
+// draws the q-th sample, loads its descriptor and copies the column's first
+// chunk into the group's slot q (cp.async), so that the round's columns
+// arrive with one memory latency; then the group walks the slots, every lane
+// computing its own problem's gradient, step and x.  Phase 2 scatters the
+// nonzero steps after a bounded grid barrier; a second barrier ends the
+// iteration.
 template <typename VT, typename XT, int BP>
 __global__ void __launch_bounds__(kBatchBlock) k_batch_iter(const BatchArgs<VT, XT> a, int64_t k0, int64_t iters)
 {
+    extern __shared__ __align__(16) unsigned char bsm[];
+    constexpr int SB = batch_slot_bytes<VT>();
+    constexpr int G = pad_granule<VT>();
     const int lane = threadIdx.x & (BP - 1);
     const unsigned gmask = group_mask<BP>(threadIdx.x & 31);
     const int64_t grp = (int64_t(blockIdx.x) * kBatchBlock + threadIdx.x) / BP;
     const int64_t ngrp = int64_t(gridDim.x) * kBatchBlock / BP;
-    const double lam = a.lambda[lane];
+    unsigned char *gslots = bsm + size_t(threadIdx.x - lane) * SB;   // the group's BP slots
+    unsigned char *myslot = bsm + size_t(threadIdx.x) * SB;           // slot `lane` of the group
+    const XT lam = XT(a.lambda[lane]);
+    const XT ib = XT(a.inv_beta);
     const bool act = a.active[lane] != 0;
     unsigned long long target = 0;
     Counters cnt;
@@ -74,54 +138,68 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_iter(const BatchArgs<VT, 
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t k = k0 + it;
         const SampleKey key = make_sample_key(a.seed, k, a.n);
+        unsigned *cnt_k = a.list_cnt + (k & 1);
+        // the other counter was last read in phase 2 of iteration k-1 (before
+        // its second barrier) and is next appended to in iteration k+1
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.list_cnt[(k + 1) & 1] = 0u;
         // ---------------- phase 1: gradients, steps, x
-        // Round r of this group covers positions grp + (r*BP + q)*ngrp, q < BP;
-        // lane q draws the sample of the q-th one.
         for (int64_t base = grp; base < a.tau; base += ngrp * BP) {
             const int64_t jq = base + int64_t(lane) * ngrp;
             int32_t iq = 0;
             if (jq < a.tau) {
                 iq = sample_index(uint32_t(jq), key);
-                a.S[jq] = iq;
+                const int4 w = __ldg(reinterpret_cast<const int4 *>(a.desc + iq));
+                *reinterpret_cast<int4 *>(myslot) = w;
+                const Col<XT> c = col_from_word<XT>(w);
+                if (c.cnt > 0) {
+                    const int64_t pc = (int64_t(c.cnt) + G - 1) / G * G;
+                    const int e = int(pc < kE ? pc : kE);
+                    for (int q = 0; q < e / 4; ++q) cp_async16(myslot + 16 + 16 * q, a.prow + c.pbeg + 4 * q);
+                    for (int q = 0; q < e * int(sizeof(VT)) / 16; ++q)
+                        cp_async16(myslot + 16 + 4 * kE + 16 * q,
+                                   reinterpret_cast<const unsigned char *>(a.pval + c.pbeg) + 16 * q);
+                }
             }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp(gmask);
             for (int q = 0; q < BP; ++q) {
                 const int64_t j = base + int64_t(q) * ngrp;
                 if (j >= a.tau) break;   // the same for every lane of the group
                 const int32_t i = __shfl_sync(gmask, iq, q, BP);
-                const Col<XT> c = load_col(a.desc, i);
+                const unsigned char *slot = gslots + size_t(q) * SB;
+                const Col<XT> c = col_from_word<XT>(*reinterpret_cast<const int4 *>(slot));
                 const double xi = ldcg(a.X + int64_t(i) * BP + lane);
-                XT acc = XT(0);
-                for (int cs = 0; cs < c.cnt; cs += kE) {
-                    Chunk<kE, XT> t;
-                    ld_chunk<kE>(t, a.prow, a.pval, c.pbeg + cs);
-                    const int valid = c.cnt - cs;
-                    XT gv[kE];
-#pragma unroll
-                    for (int e = 0; e < kE; ++e)
-                        gv[e] = (e < valid) ? ldcg(a.G + int64_t(t.row[e]) * BP + lane) : XT(0);
-#pragma unroll
-                    for (int e = 0; e < kE; ++e)
-                        if (e < valid) acc = fma(t.val[e], gv[e], acc);
-                }
-                double h = 0.0;
+                const XT acc = batch_column_dot<VT, XT, BP>(a, slot, c, lane);
+                XT h = XT(0);
                 if (act) {
                     double xn;
-                    h = step_delta<XT>(xi, acc, c.invL, a.inv_beta, lam, xn);
-                    if (h != 0.0) a.X[int64_t(i) * BP + lane] = xn;
+                    h = step_delta<XT>(xi, acc, c.invL, ib, lam, xn);
+                    if (h != XT(0)) a.X[int64_t(i) * BP + lane] = xn;
                 }
-                a.H[j * BP + lane] = XT(h);
+                // columns with a nonzero step go on the iteration's list
+                if (__any_sync(gmask, h != XT(0))) {
+                    unsigned sl = 0;
+                    if (lane == 0) {
+                        sl = atomicAdd(cnt_k, 1u);
+                        a.list[sl] = i;
+                    }
+                    sl = __shfl_sync(gmask, sl, 0, BP);
+                    a.H[int64_t(sl) * BP + lane] = h;
+                }
                 if (lane == 0) cnt.gathered += (unsigned long long)c.cnt;
-                if (h != 0.0) cnt.nonzero += 1;
+                if (h != XT(0)) cnt.nonzero += 1;
             }
+            __syncwarp(gmask);   // the slots are refilled by the next round
         }
         target += gridDim.x;
         if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) return;
 
-        // ---------------- phase 2: scatter of the nonzero steps
-        for (int64_t j = grp; j < a.tau; j += ngrp) {
-            const XT h = ldcg(a.H + j * BP + lane);
-            if (!__any_sync(gmask, h != XT(0))) continue;
-            const int32_t i = ldcg(a.S + j);
+        // ---------------- phase 2: scatter of the listed columns' steps
+        const int64_t total = int64_t(ld_volatile_u32(cnt_k));
+        for (int64_t sl = grp; sl < total; sl += ngrp) {
+            const int32_t i = ldcg(a.list + sl);
+            const XT h = ldcg(a.H + sl * BP + lane);
             const Col<XT> c = load_col(a.desc, i);
             for (int cs = 0; cs < c.cnt; cs += kE) {
                 Chunk<kE, XT> t;
@@ -228,16 +306,24 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_gap_cols(const ColDesc<XT
     default: return cudaErrorInvalidValue;               \
     }
 
+template <typename K>
+cudaError_t batch_occupancy(int *per_sm, K kernel, size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kernel, kBatchBlock, smem);
+}
+
 template <typename VT, typename XT>
 int BatchKernels<VT, XT>::iter_max_blocks(int bp)
 {
     int per_sm = 0, dev = 0, sms = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (bp) {
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iter<VT, XT, 4>, kBatchBlock, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iter<VT, XT, 8>, kBatchBlock, 0); break;
-    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iter<VT, XT, 16>, kBatchBlock, 0); break;
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_iter<VT, XT, 32>, kBatchBlock, 0); break;
+    case 4: e = batch_occupancy(&per_sm, k_batch_iter<VT, XT, 4>, batch_smem_bytes<VT>()); break;
+    case 8: e = batch_occupancy(&per_sm, k_batch_iter<VT, XT, 8>, batch_smem_bytes<VT>()); break;
+    case 16: e = batch_occupancy(&per_sm, k_batch_iter<VT, XT, 16>, batch_smem_bytes<VT>()); break;
+    case 32: e = batch_occupancy(&per_sm, k_batch_iter<VT, XT, 32>, batch_smem_bytes<VT>()); break;
     default: return 0;
     }
     if (e != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
@@ -254,7 +340,7 @@ cudaError_t BatchKernels<VT, XT>::iter(const BatchArgs<VT, XT> &a, int bp, int b
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
     PCDM_DISPATCH_BP(bp, {
         return cudaLaunchCooperativeKernel((const void *)k_batch_iter<VT, XT, BP_>, dim3(unsigned(blocks)),
-                                           dim3(kBatchBlock), params, 0, st);
+                                           dim3(kBatchBlock), params, batch_smem_bytes<VT>(), st);
     });
     return cudaSuccess;
 }

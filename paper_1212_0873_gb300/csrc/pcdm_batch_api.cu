@@ -23,8 +23,9 @@ struct pcdm_batch_ctx {
     void *G = nullptr;            // m x bp residuals in the iterate dtype
     double *G64 = nullptr;        // m x bp FP64 refresh target (aliases G in the FP64 form)
     double *Bm = nullptr;         // m x bp right-hand sides, FP64
-    void *H = nullptr;            // tau_cap x bp steps of the current iteration
-    int32_t *S = nullptr;         // tau_cap: S_k of the current iteration
+    void *H = nullptr;            // tau_cap x bp steps of the listed columns
+    int32_t *list = nullptr;      // tau_cap: columns with a nonzero step in the current iteration
+    unsigned *list_cnt = nullptr; // [2]
     int64_t tau_cap = 0;
     double *lam_d = nullptr;      // bp lambdas (0 for padding lanes)
     int *active_d = nullptr;      // bp flags
@@ -80,7 +81,7 @@ cudaStream_t bstream(pcdm_batch_handle h) { return h->base->stream; }
 
 void bfree_all(pcdm_batch_handle h)
 {
-    void *ptrs[] = {h->X, h->G, h->Bm, h->H, h->S, h->lam_d, h->active_d, h->stage,
+    void *ptrs[] = {h->X, h->G, h->Bm, h->H, h->list, h->list_cnt, h->lam_d, h->active_d, h->stage,
                     h->counters, h->bar, h->status, h->gap_part, h->gap_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -155,12 +156,12 @@ pcdm_status ensure_btau(pcdm_batch_handle h, int64_t tau)
 {
     if (tau <= h->tau_cap) return PCDM_OK;
     BCK(h, cudaStreamSynchronize(bstream(h)));
-    if (h->S) cudaFree(h->S);
+    if (h->list) cudaFree(h->list);
     if (h->H) cudaFree(h->H);
-    h->S = nullptr;
+    h->list = nullptr;
     h->H = nullptr;
     h->tau_cap = 0;
-    BCK(h, dalloc(&h->S, tau));
+    BCK(h, dalloc(&h->list, tau));
     BCK(h, dalloc_bytes(&h->H, tau * h->bp * dtype_bytes(h->base->xg_dtype)));
     h->tau_cap = tau;
     return PCDM_OK;
@@ -243,7 +244,8 @@ pcdm_status bsegment_t(pcdm_batch_handle h, int64_t tau, uint64_t seed, int64_t 
     a.X = h->X;
     a.G = static_cast<XT *>(h->G);
     a.H = static_cast<XT *>(h->H);
-    a.S = h->S;
+    a.list = h->list;
+    a.list_cnt = h->list_cnt;
     a.lambda = h->lam_d;
     a.active = h->active_d;
     a.inv_beta = 1.0 / beta_nice(b->omega, tau, b->n);
@@ -266,6 +268,7 @@ pcdm_status bsegment_t(pcdm_batch_handle h, int64_t tau, uint64_t seed, int64_t 
         BCK(h, cudaEventRecord(e0, bstream(h)));
     }
     BCK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), bstream(h)));
+    BCK(h, cudaMemsetAsync(h->list_cnt, 0, 2 * sizeof(unsigned), bstream(h)));
     BCK(h, BatchKernels<VT, XT>::iter(a, h->bp, int(blocks), h->k, iters, bstream(h)));
     if (b->opts.profile) {
         BCK(h, cudaEventRecord(e1, bstream(h)));
@@ -387,6 +390,7 @@ pcdm_status pcdm_batch_create(const pcdm_csc *A, int64_t nrhs, const void *B, in
     BCKC(dalloc(&h->lam_d, bp));
     BCKC(dalloc(&h->active_d, bp));
     BCKC(dalloc(&h->counters, 3));
+    BCKC(dalloc(&h->list_cnt, 2));
     BCKC(dalloc(&h->bar, 1));
     BCKC(dalloc(&h->status, 4));
     BCKC(dalloc(&h->gap_part, int64_t(h->gap_blocks) * bp * 3 + int64_t(h->gap_row_blocks) * bp * 2));

@@ -356,6 +356,10 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsig
 }
 
 __device__ __forceinline__ int ld_volatile_int(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
+{
+    return *reinterpret_cast<const volatile unsigned *>(p);
+}
 
 __device__ __forceinline__ bool wait_counter(unsigned long long *counter, unsigned long long target, int *status,
                                              uint64_t timeout_ns)

@@ -121,8 +121,9 @@ struct BatchArgs {
     const VT *pval;
     double *X;                  // n x bp, FP64
     XT *G;                      // m x bp
-    XT *H;                      // tau x bp: the steps of the current iteration
-    int32_t *S;                 // tau: S_k of the current iteration
+    XT *H;                      // tau x bp: steps of the listed columns (list slot s at H[s * bp])
+    int32_t *list;              // tau: the columns of the current iteration with a nonzero step
+    unsigned *list_cnt;         // [2]: list length of iterations k with k & 1 = 0, 1 (0 at launch)
     const double *lambda;       // bp
     const int *active;          // bp: 0 = this problem is frozen (converged or padding)
     double inv_beta;

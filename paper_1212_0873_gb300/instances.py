@@ -199,3 +199,33 @@ def dense(inst: Instance):
         s, e = inst.col_ptr[i], inst.col_ptr[i + 1]
         A[inst.row_idx[s:e], i] = inst.val64[s:e]
     return A
+
+
+def multi_rhs(inst, nrhs, density=0.005, noise=0.01, seed=1004):
+    """nrhs right-hand sides on inst's matrix (its stored values): b_l = A x*_l +
+    N(0, noise^2), x*_l `density`-dense with +-U[1,2] entries.  Returns
+    (B of shape (nrhs, m), the nrhs values lambda_max,l = ||A^T b_l||_inf)."""
+    rng = np.random.default_rng(seed)
+    cols = np.repeat(np.arange(inst.n, dtype=np.int64), np.diff(inst.col_ptr))
+    rows = inst.row_idx.astype(np.int64)
+    B = np.empty((nrhs, inst.m))
+    lam_max = []
+    for l in range(nrhs):
+        xs = _planted(rng, inst.n, int(round(density * inst.n)))
+        b = np.bincount(rows, weights=inst.val64 * xs[cols], minlength=inst.m)
+        if noise > 0:
+            b = b + rng.normal(0.0, noise, size=inst.m)
+        B[l] = b
+        atb = np.bincount(cols, weights=inst.val64 * b[rows], minlength=inst.n)
+        lam_max.append(float(np.max(np.abs(atb))))
+    return B, lam_max
+
+
+def batched_path_instance(m=4_000_000, n=2_000_000, per_col=15, nrhs=16, val_dtype="bf16", seed=1003):
+    """The batched regularisation-path workload: A is m x n with `per_col` N(0,1)
+    nonzeros per column at distinct uniform rows (stored as val_dtype), and nrhs
+    right-hand sides b_l = A x*_l + N(0, 1e-4), x*_l 0.5%-dense +-U[1,2].
+    Returns (inst, B, lambda_max)."""
+    inst = per_col_instance(m, n, per_col, density=0.005, noise=0.01, lam_frac=0.1, val_dtype=val_dtype, seed=seed)
+    B, lam_max = multi_rhs(inst, nrhs, density=0.005, noise=0.01, seed=seed + 1)
+    return inst, B, lam_max
