@@ -157,8 +157,10 @@ pcdm_status pcdm_gap(pcdm_handle h, double *primal, double *dual, double *gap);
 /*
  * Iterate until gap / primal <= rel_gap_tol: check the gap first, then run
  * chunks of iterations, checking after each: opts.check_every iterations when
- * it is positive, else the adaptive schedule of pcdm_next_check_interval (the
- * first chunk one epoch, ceil(n / tau) iterations).  The gap check is not part
+ * it is positive, else the adaptive schedule of pcdm_next_check_interval.  Its
+ * first chunk is one epoch, ceil(n / tau) iterations, or, when the handle's
+ * previous pcdm_solve ran K iterations since pcdm_create / pcdm_reset (a warm
+ * start such as the next lambda of a path), max(epoch, K / 2).  The gap check is not part
  * of Algorithm 1; it is the stopping test.  iters_done and rel_gap (either may
  * be NULL) receive the iterations run and the last relative gap.  Returns
  * PCDM_ENOTCONV when max_iters ran out first.
@@ -171,7 +173,7 @@ pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap
  * handle and no device).  After checks at iterations k_prev and k_cur with
  * relative gaps rel_prev > rel_cur > rel_gap_tol, the rate of the last interval,
  * log(rel_prev / rel_cur) / (k_cur - k_prev), is extrapolated to the tolerance
- * with a 5% margin; the result is clamped to [ceil(epoch / 4), 8 epoch] and to
+ * with a 5% margin; the result is clamped to [ceil(epoch / 4), 64 epoch] and to
  * twice the last interval.  Without a decrease (or with a non-positive input) it
  * returns epoch.  A gap evaluation is a full FP64 pass over A, costing about as
  * much as 20 iterations at tau = 65536, so fewer checks near the end of a solve
@@ -306,7 +308,8 @@ pcdm_status pcdm_batch_gap(pcdm_batch_handle h, double *primal, double *dual, do
  * reaches the tolerance at a check is frozen (its x no longer changes) for the
  * rest of the call; the checks follow opts.check_every or, when 0, the schedule
  * of pcdm_next_check_interval applied to the largest relative gap among the
- * problems still running.  rel_gaps: nrhs host doubles (may be NULL).
+ * problems still running (first chunk as in pcdm_solve, from the batch's
+ * previous solve).  rel_gaps: nrhs host doubles (may be NULL).
  * PCDM_ENOTCONV when max_iters ran out first. */
 pcdm_status pcdm_batch_solve(pcdm_batch_handle h, int64_t tau, uint64_t seed, double rel_gap_tol,
                              int64_t max_iters, int64_t *iters_done, double *rel_gaps);

@@ -556,7 +556,7 @@ int64_t pcdm_next_check_interval(int64_t epoch, int64_t k_prev, double rel_prev,
                                  double rel_gap_tol)
 {
     if (epoch < 1) epoch = 1;
-    const int64_t lo = (epoch + 3) / 4, hi = 8 * epoch;
+    const int64_t lo = (epoch + 3) / 4, hi = 64 * epoch;
     const int64_t last = k_cur - k_prev;
     if (last < 1 || !(rel_prev > rel_cur) || !(rel_cur > 0.0) || !(rel_gap_tol > 0.0) || !(rel_cur > rel_gap_tol))
         return epoch;
@@ -579,7 +579,7 @@ pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap
     if (max_iters < 0 || !(rel_gap_tol >= 0.0)) return set_err(h, PCDM_EINVAL, "max_iters < 0 or bad tolerance");
     const int64_t epoch = (h->n + tau - 1) / tau;
     const bool fixed = h->opts.check_every > 0;
-    int64_t every = fixed ? h->opts.check_every : epoch;
+    int64_t every = fixed ? h->opts.check_every : first_check_interval(epoch, h->last_solve_iters);
     double rec[9];
     int64_t done = 0;
     s = do_gap(h, rec);
@@ -598,6 +598,7 @@ pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap
     }
     if (iters_done) *iters_done = done;
     if (rel_gap) *rel_gap = rel;
+    h->last_solve_iters = done;
     if (rel > rel_gap_tol) return set_err(h, PCDM_ENOTCONV, "max_iters reached before the gap tolerance");
     return PCDM_OK;
 }
@@ -693,6 +694,7 @@ pcdm_status pcdm_reset(pcdm_handle h)
         h->ev_free.push_back(pr.second);
     }
     h->ev_pending.clear();
+    h->last_solve_iters = 0;
     pcdm_status s = reset_state(h);
     if (s != PCDM_OK) return s;
     CK(h, cudaStreamSynchronize(h->stream));

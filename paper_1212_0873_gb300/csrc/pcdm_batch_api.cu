@@ -41,6 +41,7 @@ struct pcdm_batch_ctx {
     std::vector<double> lam;
     std::vector<int> active;
     int64_t k = 0;
+    int64_t last_solve_iters = 0;   // iterations of the last pcdm_batch_solve (0 after create / reset)
     bool failed = false;
     std::string err;
     int64_t st_iterations = 0, st_updates = 0, st_launches = 0, st_kernels = 0, st_refreshes = 0, st_gaps = 0;
@@ -322,6 +323,7 @@ pcdm_status breset_state(pcdm_batch_handle h)
         BCK(h, launch_neg_store<float>(static_cast<float *>(h->G), h->Bm, total, bstream(h)));
     BCK(h, cudaMemsetAsync(h->status, 0, sizeof(int), bstream(h)));
     h->k = 0;
+    h->last_solve_iters = 0;
     h->failed = false;
     return PCDM_OK;
 }
@@ -480,7 +482,7 @@ pcdm_status pcdm_batch_solve(pcdm_batch_handle h, int64_t tau, uint64_t seed, do
     if (max_iters < 0 || !(rel_gap_tol >= 0.0)) return berr(h, PCDM_EINVAL, "max_iters < 0 or bad tolerance");
     const int64_t epoch = (h->base->n + tau - 1) / tau;
     const bool fixed = h->base->opts.check_every > 0;
-    int64_t every = fixed ? h->base->opts.check_every : epoch;
+    int64_t every = fixed ? h->base->opts.check_every : first_check_interval(epoch, h->last_solve_iters);
     std::vector<double> rel(size_t(h->nrhs), 0.0);
     int64_t done = 0, prev_check = 0;
     double worst_prev = 0.0;
@@ -524,6 +526,7 @@ pcdm_status pcdm_batch_solve(pcdm_batch_handle h, int64_t tau, uint64_t seed, do
     s = upload_controls(h);
     if (s != PCDM_OK) return s;
     if (iters_done) *iters_done = done;
+    h->last_solve_iters = done;
     if (!all) return berr(h, PCDM_ENOTCONV, "max_iters reached before every problem met the gap tolerance");
     return PCDM_OK;
 }

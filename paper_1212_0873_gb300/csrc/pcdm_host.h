@@ -69,6 +69,7 @@ struct pcdm_ctx {
 
     int64_t omega = 0;
     int64_t k = 0;
+    int64_t last_solve_iters = 0;   // iterations of the last pcdm_solve (0 after create / reset)
     bool sample_valid = false;
     uint64_t sample_seed = 0;
     int64_t sample_tau = 0, sample_k = -1;
@@ -180,6 +181,15 @@ inline pcdm_status dispatch(pcdm_handle h, F &&f)
     if (h->val_dtype == PCDM_F32 && h->xg_dtype == PCDM_F32) return f((float *)nullptr, (float *)nullptr);
     if (h->val_dtype == PCDM_BF16 && h->xg_dtype == PCDM_F32) return f((bf16_t *)nullptr, (float *)nullptr);
     return set_err(h, PCDM_EINVAL, "unsupported dtype pair");
+}
+
+// First gap-check interval of a solve: one epoch, or, when the handle's last
+// solve ran K iterations (a warm start, e.g. the next lambda of a path), half
+// of K, so that a solve of similar length needs only a few checks.
+inline int64_t first_check_interval(int64_t epoch, int64_t last_solve_iters)
+{
+    const int64_t guess = last_solve_iters / 2;
+    return guess > epoch ? guess : epoch;
 }
 
 inline pcdm_status usable(pcdm_handle h)

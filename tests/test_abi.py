@@ -170,8 +170,8 @@ def test_check_schedule_extrapolates_the_linear_rate(B):
     assert f(E, 0, 1e-1 ** 4, 4 * E, 1e-1 ** 8, 1e-12) == int(__import__("math").ceil(1.05 * 4 * E))
     # almost there: never below a quarter epoch
     assert f(E, 0, 2e-6, 10 * E, 1.0000001e-6, 1e-6) == (E + 3) // 4
-    # slow progress: never beyond 8 epochs
-    assert f(E, 0, 1.0, 100 * E, 0.5, 1e-9) == 8 * E
+    # slow progress: never beyond 64 epochs
+    assert f(E, 0, 1.0, 100 * E, 0.5, 1e-9) == 64 * E
     # no decrease, non-positive gaps, zero interval: one epoch
     assert f(E, 0, 1e-3, E, 2e-3, 1e-6) == E
     assert f(E, 0, 1e-3, E, 0.0, 1e-6) == E
