@@ -263,6 +263,47 @@ pcdm_status pcdm_selftest_barrier_timeout(uint64_t timeout_ns, void *cuda_stream
 pcdm_status pcdm_omega_noalloc(const pcdm_csc *A, int64_t *omega, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Derivatives of the LASSO solution (implicit function theorem on the active
+ * set).  With S = {i : x_i != 0} and s = sign(x_S), a solution satisfies
+ *   A_S^T (A_S x_S - b) + lambda s = 0,
+ * so for a loss L(x) with v = dL/dx restricted to S and u solving
+ * (A_S^T A_S) u = v:  dL/db = A_S u  and  dL/dlambda = -s^T u.
+ * Both solves below run the coordinate kernel of Algorithm 1 on the positions
+ * of S (tau-nice sampling over S, beta of Theorem ESO-nice with omega_S = the
+ * largest row count of A_S) without the prox, in FP64 for every precision
+ * pair.  The paper has no derivatives; this is the differentiation layer
+ * (torch.autograd) of the package.  Memory: O(n + m) beyond the handle.
+ * ------------------------------------------------------------------------ */
+
+/* Replace b (m entries of b_dtype, host or device) keeping x; g = A x - b.
+ * EINVAL for a non-finite value (for an FP32 b the handle then needs
+ * pcdm_set_b or pcdm_reset before further work). */
+pcdm_status pcdm_set_b(pcdm_handle h, const void *b, int32_t b_dtype, int32_t on_device);
+
+/* |S| = number of nonzero x_i. */
+pcdm_status pcdm_support_size(pcdm_handle h, int64_t *count);
+
+/* Polish x on its current support: solve A_S^T (A_S x_S - b) + lambda s = 0
+ * for x_S (x fixed at 0 off S) from the current x, until
+ * ||A_S^T (A_S x_S - b) + lambda s|| / ||lambda s|| <= tol, then recompute g.
+ * Meant after pcdm_solve has settled the support and signs: it does not move
+ * coordinates off S, and pcdm_gap tells whether the result is optimal.
+ * tau = 0: all of S per iteration.  iters, rel_res may be NULL.
+ * PCDM_ENOTCONV when max_iters ran out first. */
+pcdm_status pcdm_polish(pcdm_handle h, int64_t tau, uint64_t seed, double tol, int64_t max_iters,
+                        int64_t *iters, double *rel_res);
+
+/* Backward pass at the current x: given dx = dL/dx (n doubles, host or device;
+ * entries off S are ignored), solve (A_S^T A_S) u = dx_S to relative residual
+ * tol and write db = A_S u (m doubles, host or device as db_on_device says;
+ * may be NULL) and *dlambda = -sign(x_S)^T u (may be NULL).  tau = 0: all of S
+ * per iteration.  PCDM_ENOTCONV when max_iters ran out first (outputs are
+ * still written). */
+pcdm_status pcdm_backward(pcdm_handle h, const double *dx, int32_t dx_on_device, double *db,
+                          int32_t db_on_device, double *dlambda, int64_t tau, uint64_t seed, double tol,
+                          int64_t max_iters, int64_t *iters, double *rel_res);
+
+/* ------------------------------------------------------------------------
  * Batched solver: nrhs <= 32 LASSO problems that share A,
  *   min_x 1/2 ||A x - b_l||^2 + lambda_l ||x||_1,  l = 0 .. nrhs-1,
  * solved together.  Each problem runs Algorithm 1 exactly as pcdm_step would

@@ -16,6 +16,12 @@ Citations (sections, equations and tables of the paper):
   objective      F(x) of eq. (P) for LASSO (Sec. 8.1)
   gap            LASSO duality gap at theta = min(1, lambda/||A^T g||_inf) g
   run            iterations of Algorithm 1 with periodic residual refresh
+  active_set_solution, implicit_grad
+                 the LASSO optimality condition on a fixed support and sign
+                 pattern, and the implicit-function derivatives of the solution
+                 (dense numpy solves; tiny inputs only).  The paper has no
+                 derivatives; these are the definitions the GPU backward is
+                 checked against.
 
 Every function here is pinned by a -m "not gpu" test in tests/test_oracle_*.py.
 """
@@ -237,3 +243,34 @@ class State:
             rec = self.gap()
             rel = rec["gap"] / max(rec["primal"], 1e-300)
         return done, rel
+
+
+# ----------------------------------------------------------------------------- derivatives (dense)
+def _dense_columns(A: Csc, S):
+    cp, ri, v = A.col_ptr, A.row_idx, A.val
+    D = np.zeros((A.m, len(S)))
+    for q, i in enumerate(S):
+        D[ri[cp[i]:cp[i + 1]], q] = v[cp[i]:cp[i + 1]]
+    return D
+
+
+def active_set_solution(A: Csc, b, lam, S, s):
+    """x with x_S solving A_S^T (A_S x_S - b) + lam s = 0 and x = 0 off S."""
+    S = np.asarray(S, dtype=np.int64)
+    x = np.zeros(A.n)
+    if S.size:
+        AS = _dense_columns(A, S)
+        x[S] = np.linalg.solve(AS.T @ AS, AS.T @ np.asarray(b, dtype=np.float64) - lam * np.asarray(s, float))
+    return x
+
+
+def implicit_grad(A: Csc, x, lam, dx):
+    """(dL/db, dL/dlam) at a LASSO solution x for dL/dx = dx: with S = supp(x),
+    s = sign(x_S) and (A_S^T A_S) u = dx_S, dL/db = A_S u, dL/dlam = -s^T u."""
+    x = np.asarray(x, dtype=np.float64)
+    S = np.nonzero(x)[0]
+    if S.size == 0:
+        return np.zeros(A.m), 0.0
+    AS = _dense_columns(A, S)
+    u = np.linalg.solve(AS.T @ AS, np.asarray(dx, dtype=np.float64)[S])
+    return AS @ u, float(-np.sign(x[S]) @ u)

@@ -60,6 +60,10 @@ SIGNATURES = {
     "pcdm_batch_reset_stats": (_i32, [_ptr]),
     "pcdm_batch_destroy": (None, [_ptr]),
     "pcdm_batch_last_error": (ctypes.c_char_p, [_ptr]),
+    "pcdm_set_b": (_i32, [_ptr, _ptr, _i32, _i32]),
+    "pcdm_support_size": (_i32, [_ptr, _ptr]),
+    "pcdm_polish": (_i32, [_ptr, _i64, _u64, _dbl, _i64, _ptr, _ptr]),
+    "pcdm_backward": (_i32, [_ptr, _ptr, _i32, _ptr, _i32, _ptr, _i64, _u64, _dbl, _i64, _ptr, _ptr]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -329,3 +333,37 @@ def pcdm_batch_destroy(h):
 def pcdm_batch_last_error(h=None):
     msg = lib().pcdm_batch_last_error(h)
     return (msg or b"").decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------- derivatives
+def pcdm_set_b(h, ptr, b_dtype, on_device):
+    _check(lib().pcdm_set_b(h, _ptr(ptr), int(b_dtype), int(on_device)), h)
+
+
+def pcdm_support_size(h):
+    v = _i64()
+    _check(lib().pcdm_support_size(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def pcdm_polish(h, tau, seed, tol, max_iters):
+    """Returns (converged, iterations, relative residual)."""
+    it, rel = _i64(), _dbl()
+    st = lib().pcdm_polish(h, int(tau), int(seed) & (2**64 - 1), float(tol), int(max_iters), ctypes.byref(it),
+                           ctypes.byref(rel))
+    if st == PCDM_ENOTCONV:
+        return False, it.value, rel.value
+    _check(st, h)
+    return True, it.value, rel.value
+
+
+def pcdm_backward(h, dx_ptr, dx_on_device, db_ptr, db_on_device, tau, seed, tol, max_iters):
+    """Returns (converged, dlambda, iterations, relative residual); db written in place."""
+    dl, it, rel = _dbl(), _i64(), _dbl()
+    st = lib().pcdm_backward(h, _ptr(dx_ptr), int(dx_on_device), _ptr(db_ptr), int(db_on_device), ctypes.byref(dl),
+                             int(tau), int(seed) & (2**64 - 1), float(tol), int(max_iters), ctypes.byref(it),
+                             ctypes.byref(rel))
+    if st == PCDM_ENOTCONV:
+        return False, dl.value, it.value, rel.value
+    _check(st, h)
+    return True, dl.value, it.value, rel.value

@@ -235,6 +235,64 @@ cudaError_t launch_gap_finish(const double *pc, int nbc, const double *pr, int n
     return cudaGetLastError();
 }
 
+// Support of x in increasing index order, by one block: each pass takes
+// kBlock entries, the block's ballots give every nonzero its rank.
+__global__ void __launch_bounds__(kBlock) k_compact_support(const double *__restrict__ x, int64_t n,
+                                                            int32_t *__restrict__ sidx, int *__restrict__ count)
+{
+    __shared__ int wsum[kBlock / 32];
+    __shared__ int base_s;
+    if (threadIdx.x == 0) base_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t t0 = 0; t0 < n; t0 += kBlock) {
+        const int64_t i = t0 + threadIdx.x;
+        const bool nz = i < n && x[i] != 0.0;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, nz);
+        if (lane == 0) wsum[w] = __popc(bal);
+        __syncthreads();
+        int off = base_s;
+        for (int q = 0; q < w; ++q) off += wsum[q];
+        if (nz) sidx[off + __popc(bal & ((1u << lane) - 1u))] = int32_t(i);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int q = 0; q < kBlock / 32; ++q) tot += wsum[q];
+            base_s += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base_s;
+}
+
+cudaError_t launch_compact_support(const double *x, int64_t n, int32_t *sidx, int *count, cudaStream_t st)
+{
+    k_compact_support<<<1, kBlock, 0, st>>>(x, n, sidx, count);
+    return cudaGetLastError();
+}
+
+__global__ void k_as_linear(const double *__restrict__ x, const double *__restrict__ src,
+                            const int32_t *__restrict__ sidx, int64_t nS, double lambda, double *__restrict__ c,
+                            double *__restrict__ sgn)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nS; p += stride) {
+        const int32_t i = sidx[p];
+        const double xi = x[i];
+        const double s = xi > 0.0 ? 1.0 : (xi < 0.0 ? -1.0 : 0.0);
+        sgn[p] = s;
+        c[p] = src ? src[i] : -lambda * s;
+    }
+}
+
+cudaError_t launch_as_linear(const double *x, const double *src, const int32_t *sidx, int64_t nS, double lambda,
+                             double *c, double *sgn, cudaStream_t st)
+{
+    if (nS <= 0) return cudaSuccess;
+    k_as_linear<<<grid_for(nS), 256, 0, st>>>(x, src, sidx, nS, lambda, c, sgn);
+    return cudaGetLastError();
+}
+
 // Interleaving of nsrc vectors of length len (src[l * len + r], FP64 or FP32)
 // into dst[r * bp + l] (FP64); the padding lanes l >= nsrc get 0.
 __global__ void k_interleave(const void *src, int src_is_f32, int64_t len, int nsrc, int bp, double *dst)

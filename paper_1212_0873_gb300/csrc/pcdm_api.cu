@@ -22,7 +22,9 @@ namespace {
 void free_all(pcdm_handle h)
 {
     void *ptrs[] = {h->desc, h->prow, h->pval, h->b, h->L64, h->x, h->g, h->g2,
-                    h->S[0], h->S[1], h->h, h->counters, h->bar, h->status, h->gap_part, h->gap_out};
+                    h->S[0], h->S[1], h->h, h->counters, h->bar, h->status, h->gap_part, h->gap_out,
+                    h->as_sidx, h->as_c, h->as_sgn, h->as_u, h->as_dx, h->as_q, h->as_rowcnt, h->as_H,
+                    h->as_S, h->as_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->g64 && h->g64 != h->g) cudaFree(h->g64);
@@ -737,6 +739,253 @@ pcdm_status pcdm_reset_stats(pcdm_handle h)
         h->ev_free.push_back(pr.second);
     }
     h->ev_pending.clear();
+    return PCDM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Active-set solves: the polish of x on its support and the implicit backward.
+namespace {
+
+pcdm_status ensure_as(pcdm_handle h, int64_t tau)
+{
+    if (!h->as_sidx) {
+        CK(h, dalloc(&h->as_sidx, h->n));
+        CK(h, dalloc(&h->as_c, h->n));
+        CK(h, dalloc(&h->as_sgn, h->n));
+        CK(h, dalloc(&h->as_u, h->n));
+        CK(h, dalloc(&h->as_q, h->m));
+        CK(h, dalloc(&h->as_rowcnt, h->m + 4));
+        const int64_t cap = int64_t(h->sms) * 4;
+        int64_t blocks = (h->n + kBlock - 1) / kBlock;
+        h->as_blocks = int(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
+        CK(h, dalloc(&h->as_part, 3 * int64_t(h->as_blocks)));
+    }
+    if (tau > h->as_tau_cap) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (h->as_H) cudaFree(h->as_H);
+        if (h->as_S) cudaFree(h->as_S);
+        h->as_H = nullptr;
+        h->as_S = nullptr;
+        h->as_tau_cap = 0;
+        CK(h, dalloc(&h->as_H, tau));
+        CK(h, dalloc(&h->as_S, tau));
+        h->as_tau_cap = tau;
+    }
+    return PCDM_OK;
+}
+
+// Relative residual ||A_S^T q - c|| / ||c|| over S (and sum_p w_p u_{i_p}).
+template <typename VT, typename XT>
+pcdm_status as_residual(pcdm_handle h, int64_t nS, const double *u, const double *w, double *rel, double *wu)
+{
+    CK(h, ActiveSetKernels<VT, XT>::resid(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
+                                          static_cast<const VT *>(h->pval), h->as_sidx, h->as_c, nS, h->as_q, w, u,
+                                          h->as_part, h->as_blocks, h->stream));
+    std::vector<double> part(size_t(3 * h->as_blocks));
+    CK(h, cudaMemcpyAsync(part.data(), h->as_part, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->stream));
+    pcdm_status s = sync_check(h);
+    if (s != PCDM_OK) return s;
+    double rr = 0.0, cc = 0.0, s_wu = 0.0;
+    for (int b = 0; b < h->as_blocks; ++b) {
+        rr += part[size_t(3 * b)];
+        cc += part[size_t(3 * b + 1)];
+        s_wu += part[size_t(3 * b + 2)];
+    }
+    *rel = cc > 0.0 ? std::sqrt(rr / cc) : std::sqrt(rr);
+    if (wu) *wu = s_wu;
+    h->st_kernels += 1;
+    return PCDM_OK;
+}
+
+// Coordinate descent on Q(u) = 1/2 ||A_S u - y||^2 - c^T u over the support S
+// of x: polish (u = x, y = b, c = -lambda sign(x_S)) or backward (u = as_u from
+// 0, y = 0, c = dL/dx on S).  q = A_S u - y is kept in as_q and recomputed
+// exactly before every convergence check.
+template <typename VT, typename XT>
+pcdm_status as_solve(pcdm_handle h, bool backward, const double *dx_dev, int64_t tau_req, uint64_t seed,
+                     double tol, int64_t max_iters, int64_t *iters, double *rel_out, double *dlambda)
+{
+    const ColDesc<XT> *desc = static_cast<const ColDesc<XT> *>(h->desc);
+    const VT *pval = static_cast<const VT *>(h->pval);
+    cudaStream_t st = h->stream;
+    pcdm_status s = ensure_as(h, 1);
+    if (s != PCDM_OK) return s;
+    // S, |S|
+    int *cnt_dev = h->as_rowcnt + h->m;
+    CK(h, launch_compact_support(h->x, h->n, h->as_sidx, cnt_dev, st));
+    int hcnt[2] = {0, 0};
+    CK(h, cudaMemcpyAsync(hcnt, cnt_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    s = sync_check(h);
+    if (s != PCDM_OK) return s;
+    const int64_t nS = hcnt[0];
+    double *u = backward ? h->as_u : h->x;
+    if (backward) CK(h, cudaMemsetAsync(h->as_u, 0, sizeof(double) * size_t(h->n), st));
+    if (nS == 0) {
+        if (backward) CK(h, cudaMemsetAsync(h->as_q, 0, sizeof(double) * size_t(h->m), st));
+        if (iters) *iters = 0;
+        if (rel_out) *rel_out = 0.0;
+        if (dlambda) *dlambda = 0.0;
+        return PCDM_OK;
+    }
+    const int64_t tau = tau_req > 0 ? (tau_req < nS ? tau_req : nS) : nS;
+    s = ensure_as(h, tau);
+    if (s != PCDM_OK) return s;
+    CK(h, launch_as_linear(h->x, backward ? dx_dev : nullptr, h->as_sidx, nS, h->lambda, h->as_c, h->as_sgn, st));
+    // omega_S: the largest row count of A_S
+    CK(h, cudaMemsetAsync(h->as_rowcnt, 0, sizeof(int) * size_t(h->m + 4), st));
+    CK(h, ActiveSetKernels<VT, XT>::rowcount(desc, h->prow, h->as_sidx, nS, h->as_rowcnt, st));
+    CK(h, launch_max_int(h->as_rowcnt, h->m, cnt_dev + 1, st));
+    CK(h, cudaMemcpyAsync(hcnt, cnt_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    s = sync_check(h);
+    if (s != PCDM_OK) return s;
+    const double inv_beta = 1.0 / beta_nice(hcnt[1], tau, nS);
+    h->st_kernels += 4;
+
+    auto exact_q = [&]() -> pcdm_status {
+        if (backward)
+            CK(h, cudaMemsetAsync(h->as_q, 0, sizeof(double) * size_t(h->m), st));
+        else
+            CK(h, launch_neg_store<double>(h->as_q, h->b, h->m, st));
+        CK(h, ActiveSetKernels<VT, XT>::refresh(desc, h->prow, pval, h->as_sidx, nS, u, h->as_q, st));
+        h->st_kernels += 2;
+        return PCDM_OK;
+    };
+    s = exact_q();
+    if (s != PCDM_OK) return s;
+    double rel = 0.0, wu = 0.0;
+    s = as_residual<VT, XT>(h, nS, u, h->as_sgn, &rel, &wu);
+    if (s != PCDM_OK) return s;
+    const int64_t check = 16;
+    int64_t done = 0, k = 0;
+    while (rel > tol && done < max_iters) {
+        const int64_t chunk = check < max_iters - done ? check : max_iters - done;
+        for (int64_t it = 0; it < chunk; ++it, ++k) {
+            CK(h, ActiveSetKernels<VT, XT>::gather(desc, h->prow, pval, h->as_sidx, h->as_c, nS, tau, seed, k,
+                                                   inv_beta, h->as_q, u, h->as_H, h->as_S, st));
+            CK(h, ActiveSetKernels<VT, XT>::scatter(desc, h->prow, pval, tau, h->as_H, h->as_S, h->as_q, st));
+        }
+        h->st_kernels += 2 * chunk;
+        done += chunk;
+        s = exact_q();
+        if (s != PCDM_OK) return s;
+        s = as_residual<VT, XT>(h, nS, u, h->as_sgn, &rel, &wu);
+        if (s != PCDM_OK) return s;
+    }
+    if (iters) *iters = done;
+    if (rel_out) *rel_out = rel;
+    if (dlambda) *dlambda = -wu;
+    if (!backward) {
+        s = do_refresh(h);   // g = A x - b for the polished x
+        if (s != PCDM_OK) return s;
+        h->sample_valid = false;
+    }
+    s = sync_check(h);
+    if (s != PCDM_OK) return s;
+    if (rel > tol) return set_err(h, PCDM_ENOTCONV, "max_iters reached before the active-set tolerance");
+    return PCDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcdm_status pcdm_polish(pcdm_handle h, int64_t tau, uint64_t seed, double tol, int64_t max_iters, int64_t *iters,
+                        double *rel_res)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (tau < 0 || max_iters < 0 || !(tol >= 0.0)) return set_err(h, PCDM_EINVAL, "bad tau, max_iters or tol");
+    return dispatch(h, [&](auto *vt, auto *xt) {
+        using VT = std::remove_pointer_t<decltype(vt)>;
+        using XT = std::remove_pointer_t<decltype(xt)>;
+        return as_solve<VT, XT>(h, false, nullptr, tau, seed, tol, max_iters, iters, rel_res, nullptr);
+    });
+}
+
+pcdm_status pcdm_backward(pcdm_handle h, const double *dx, int32_t dx_on_device, double *db, int32_t db_on_device,
+                          double *dlambda, int64_t tau, uint64_t seed, double tol, int64_t max_iters, int64_t *iters,
+                          double *rel_res)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (!dx) return set_err(h, PCDM_EINVAL, "dx is NULL");
+    if (tau < 0 || max_iters < 0 || !(tol >= 0.0)) return set_err(h, PCDM_EINVAL, "bad tau, max_iters or tol");
+    s = ensure_as(h, 1);
+    if (s != PCDM_OK) return s;
+    const double *dx_dev = dx;
+    if (!dx_on_device) {
+        if (!h->as_dx) CK(h, dalloc(&h->as_dx, h->n));
+        CK(h, cudaMemcpyAsync(h->as_dx, dx, sizeof(double) * size_t(h->n), cudaMemcpyHostToDevice, h->stream));
+        dx_dev = h->as_dx;
+    }
+    double dl = 0.0;
+    s = dispatch(h, [&](auto *vt, auto *xt) {
+        using VT = std::remove_pointer_t<decltype(vt)>;
+        using XT = std::remove_pointer_t<decltype(xt)>;
+        return as_solve<VT, XT>(h, true, dx_dev, tau, seed, tol, max_iters, iters, rel_res, &dl);
+    });
+    if (s != PCDM_OK && s != PCDM_ENOTCONV) return s;
+    if (db) {
+        CK(h, cudaMemcpyAsync(db, h->as_q, sizeof(double) * size_t(h->m), copy_kind(1, db_on_device), h->stream));
+        pcdm_status s2 = sync_check(h);
+        if (s2 != PCDM_OK) return s2;
+    }
+    if (dlambda) *dlambda = dl;
+    return s;
+}
+
+pcdm_status pcdm_set_b(pcdm_handle h, const void *b, int32_t b_dtype, int32_t on_device)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (!b) return set_err(h, PCDM_EINVAL, "b is NULL");
+    if (b_dtype != PCDM_F64 && b_dtype != PCDM_F32) return set_err(h, PCDM_EINVAL, "b_dtype must be F64 or F32");
+    cudaStream_t st = h->stream;
+    // stage in the refresh buffer (m doubles), then validate before replacing b
+    double *stage = h->g64;
+    if (b_dtype == PCDM_F64) {
+        CK(h, cudaMemcpyAsync(stage, b, sizeof(double) * size_t(h->m), copy_kind(on_device, 1), st));
+    } else {
+        CK(h, cudaMemcpyAsync(h->b, b, sizeof(float) * size_t(h->m), copy_kind(on_device, 1), st));
+        CK(h, launch_convert_b(h->b, 1, h->m, stage, st));
+    }
+    int *flags = h->status + 1;
+    int *hflags = reinterpret_cast<int *>(h->host_buf + 10);
+    CK(h, cudaMemsetAsync(flags, 0, sizeof(int), st));
+    CK(h, launch_check_finite(stage, h->m, flags, st));
+    CK(h, cudaMemcpyAsync(hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    if (*hflags) {
+        // b was overwritten only in the FP32 case; recover it from nothing is not possible,
+        // so the handle refuses further work until pcdm_set_b succeeds or pcdm_reset runs
+        CK(h, cudaMemsetAsync(flags, 0, sizeof(int), st));
+        if (b_dtype != PCDM_F64) h->failed = true;
+        return set_err(h, PCDM_EINVAL, "a non-finite value in b");
+    }
+    CK(h, cudaMemcpyAsync(h->b, stage, sizeof(double) * size_t(h->m), cudaMemcpyDeviceToDevice, st));
+    h->last_solve_iters = 0;
+    s = do_refresh(h);
+    if (s != PCDM_OK) return s;
+    h->sample_valid = false;
+    return sync_check(h);
+}
+
+pcdm_status pcdm_support_size(pcdm_handle h, int64_t *count)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (!count) return set_err(h, PCDM_EINVAL, "count is NULL");
+    s = ensure_as(h, 1);
+    if (s != PCDM_OK) return s;
+    int *cnt_dev = h->as_rowcnt + h->m;
+    CK(h, launch_compact_support(h->x, h->n, h->as_sidx, cnt_dev, h->stream));
+    int hc = 0;
+    CK(h, cudaMemcpyAsync(&hc, cnt_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    s = sync_check(h);
+    if (s != PCDM_OK) return s;
+    *count = hc;
     return PCDM_OK;
 }
 

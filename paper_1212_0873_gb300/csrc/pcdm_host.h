@@ -67,6 +67,20 @@ struct pcdm_ctx {
     int gap_blocks = 0, gap_row_blocks = 0;
     double *host_buf = nullptr;   // pinned: 9 gap doubles + status + counters
 
+    // active-set solves (pcdm_polish / pcdm_backward), allocated on first use
+    int32_t *as_sidx = nullptr;   // n: the support S of x
+    double *as_c = nullptr;       // n: linear term c_p
+    double *as_sgn = nullptr;     // n: sign(x_i) on S
+    double *as_u = nullptr;       // n: the backward solution u (zero outside S)
+    double *as_dx = nullptr;      // n: staging of a host dL/dx
+    double *as_q = nullptr;       // m: A_S u - y in FP64
+    int *as_rowcnt = nullptr;     // m + 4: row counts of A_S, then count / omega_S words
+    double *as_H = nullptr;       // tau: steps of the iteration
+    int32_t *as_S = nullptr;      // tau: columns of the iteration
+    double *as_part = nullptr;    // residual partials
+    int64_t as_tau_cap = 0;
+    int as_blocks = 0;
+
     int64_t omega = 0;
     int64_t k = 0;
     int64_t last_solve_iters = 0;   // iterations of the last pcdm_solve (0 after create / reset)

@@ -162,6 +162,29 @@ cudaError_t launch_deinterleave(const double *src, int64_t len, int nout, int bp
 cudaError_t launch_batch_gap_finish(const double *pc, int nbc, const double *pr, int nbr, int bp,
                                     const double *lambda, double *out, cudaStream_t st);
 
+// Active-set coordinate descent (active_set_kernels.cuh): FP64 u, q and sums for
+// any stored value type; DT is the handle's iterate dtype (type of 1/L in desc).
+template <typename VT, typename DT>
+struct ActiveSetKernels {
+    static cudaError_t gather(const ColDesc<DT> *desc, const int32_t *prow, const VT *pval, const int32_t *sidx,
+                              const double *c, int64_t nS, int64_t tau, uint64_t seed, int64_t k, double inv_beta,
+                              const double *q, double *u, double *H, int32_t *Sbuf, cudaStream_t st);
+    static cudaError_t scatter(const ColDesc<DT> *desc, const int32_t *prow, const VT *pval, int64_t tau,
+                               const double *H, const int32_t *Sbuf, double *q, cudaStream_t st);
+    static cudaError_t refresh(const ColDesc<DT> *desc, const int32_t *prow, const VT *pval, const int32_t *sidx,
+                               int64_t nS, const double *u, double *q, cudaStream_t st);
+    static cudaError_t resid(const ColDesc<DT> *desc, const int32_t *prow, const VT *pval, const int32_t *sidx,
+                             const double *c, int64_t nS, const double *q, const double *w, const double *u,
+                             double *part, int blocks, cudaStream_t st);
+    static cudaError_t rowcount(const ColDesc<DT> *desc, const int32_t *prow, const int32_t *sidx, int64_t nS,
+                                int *rowcnt, cudaStream_t st);
+};
+// The support S = {i : x_i != 0} in increasing order (one block; *count = |S|).
+cudaError_t launch_compact_support(const double *x, int64_t n, int32_t *sidx, int *count, cudaStream_t st);
+// sgn[p] = sign(x[sidx[p]]); c[p] = src[sidx[p]] if src, else -lambda * sgn[p].
+cudaError_t launch_as_linear(const double *x, const double *src, const int32_t *sidx, int64_t nS, double lambda,
+                             double *c, double *sgn, cudaStream_t st);
+
 // Type-independent kernels (kernels_common.cu).
 cudaError_t launch_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S, cudaStream_t st);
 cudaError_t launch_check_colptr(const int64_t *col_ptr, int64_t n, int64_t nnz, int *flags, cudaStream_t st);

@@ -121,6 +121,35 @@ class Lasso:
         p, d = _ptr_and_device(x)
         B.pcdm_set_x(self._h, p, d)
 
+    def set_b(self, b):
+        """New right-hand side (m entries, numpy or CUDA tensor); x is kept."""
+        if not _is_tensor(b):
+            b = np.ascontiguousarray(b, dtype=np.float64)
+        b_dt = B.PCDM_F32 if (str(getattr(b, "dtype", "")) in ("float32", "torch.float32")) else B.PCDM_F64
+        p, d = _ptr_and_device(b)
+        B.pcdm_set_b(self._h, p, b_dt, d)
+
+    def support_size(self):
+        return B.pcdm_support_size(self._h)
+
+    def polish(self, tol=1e-13, max_iters=100_000, tau=0, seed=0):
+        """Solve the optimality system on the current support and signs
+        (pcdm_polish); returns (converged, iterations, relative residual)."""
+        return B.pcdm_polish(self._h, tau, seed, tol, max_iters)
+
+    def backward(self, dx, tol=1e-12, max_iters=100_000, tau=0, seed=0, db_out=None):
+        """dL/db (m) and dL/dlambda at the current x for dx = dL/dx (pcdm_backward).
+        dx: numpy or CUDA float64; db_out: optional CUDA float64 tensor of m.
+        Returns (db, dlambda, converged, iterations, relative residual)."""
+        if not _is_tensor(dx):
+            dx = np.ascontiguousarray(dx, dtype=np.float64)
+        p_dx, d_dx = _ptr_and_device(dx)
+        if db_out is None:
+            db_out = np.empty(self.m, dtype=np.float64)
+        p_db, d_db = _ptr_and_device(db_out)
+        ok, dl, it, rel = B.pcdm_backward(self._h, p_dx, d_dx, p_db, d_db, tau, seed, tol, max_iters)
+        return db_out, dl, ok, it, rel
+
     def residual(self):
         out = self._np_g(self.m)
         B.pcdm_get_residual(self._h, out.ctypes.data, 0)
