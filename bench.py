@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched regularisation-path measurement")
     p.add_argument("--path-len", type=int, default=32, help="lambdas on the batched regularisation path")
+    p.add_argument("--no-grad", action="store_true", help="skip the differentiation measurement")
+    p.add_argument("--no-tvr", action="store_true", help="skip the theory-versus-reality experiment")
     return p.parse_args()
 
 
@@ -329,6 +331,68 @@ def run_batched_path(a):
     }
 
 
+# ----------------------------------------------------------------------------- differentiation
+def run_grad():
+    """Forward (solve to relative gap 1e-6, then the FP64 polish on the support)
+    and backward (pcdm_backward: dL/db and dL/dlambda for L = 1/2 ||x - x*||^2)
+    on the differentiation workload: A 1e6 x 5e5, 12 FP32 nonzeros per column,
+    x* 1% dense, b = A x* + N(0, 1e-4), lambda = 0.1 ||A^T b||_inf."""
+    import numpy as np
+    import torch
+    from paper_1212_0873_gb300 import Lasso, instances
+
+    inst = instances.per_col_instance(1_000_000, 500_000, 12, density=0.01, noise=0.01, lam_frac=0.1,
+                                      val_dtype="f32", seed=1005)
+    tau = 4096
+    with Lasso.from_instance(inst, refresh_every=64) as s:
+        def forward():
+            s.reset()
+            ok, it, rel = s.solve(tau, 0, 1e-6, 10**6)
+            ok2, it2, res2 = s.polish(1e-14)
+            if not (ok and ok2):
+                raise RuntimeError("differentiation forward failed")
+            return it, it2
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            e1.synchronize()
+            return e0.elapsed_time(e1) / 1e3, out
+
+        forward()                                            # warm-up
+        t_fwd, (it, it2) = timed(forward)
+        x = s.x()
+        dx = torch.from_numpy(x - inst.x_star).cuda()
+        db = torch.empty(inst.m, dtype=torch.float64, device="cuda")
+        s.backward(dx, tol=1e-13, db_out=db)                 # warm-up
+        t_bwd, (db, dlam, ok, itb, res) = timed(lambda: s.backward(dx, tol=1e-13, db_out=db))
+        support = s.support_size()
+    return {"workload": "A 1e6 x 5e5, 12 fp32 nonzeros per column; L = 1/2 ||x(b, lambda) - x*||^2; forward "
+                        "= solve to rel. gap 1e-6 (tau=%d) + fp64 polish on the support to 1e-14; backward = "
+                        "dL/db (1e6) and dL/dlambda to relative residual 1e-13" % tau,
+            "forward_s": t_fwd, "forward_iterations": it, "polish_iterations": it2,
+            "backward_s": t_bwd, "backward_iterations": itb, "backward_rel_residual": res,
+            "support": support}
+
+
+# ----------------------------------------------------------------------------- theory vs reality
+def run_theory_vs_reality():
+    """Sec. 8.2: iteration speedup of tau-nice PCDM1 against tau / beta on least
+    squares with 3000 x 1000 equal-valued rows of omega nonzeros, eps = 1e-6."""
+    import time
+    from paper_1212_0873_gb300 import experiments
+    t0 = time.perf_counter()
+    rows = experiments.theory_vs_reality()
+    dev = max(abs(r["empirical"] / r["theory"] - 1.0) for r in rows)
+    return {"workload": "min 1/2 ||Ax - b||^2, A 3000 x 1000 with omega in {5, 10, 50, 100} equal nonzeros per row, "
+                        "tau in 1 .. 1000, iterations until F - F* <= 1e-6",
+            "max_relative_deviation_from_tau_over_beta": dev, "seconds": time.perf_counter() - t0,
+            "rows": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()} for r in rows]}
+
+
 # ----------------------------------------------------------------------------- the CUDA arm
 def run_pcdm(a, rank, local, world):
     import torch
@@ -439,6 +503,12 @@ def run_pcdm(a, rank, local, world):
     batched = None
     if rank == 0 and world == 1 and not a.no_batched:
         batched = run_batched_path(a)
+    grad = None
+    if rank == 0 and world == 1 and not a.no_grad:
+        grad = run_grad()
+    tvr = None
+    if rank == 0 and world == 1 and not a.no_tvr:
+        tvr = run_theory_vs_reality()
 
     if rank == 0:
         out = {
@@ -458,6 +528,8 @@ def run_pcdm(a, rank, local, world):
             "gpu_launches": st["kernel_launches"],
             "clocks": clk,
             "batched": batched,
+            "differentiation": grad,
+            "theory_vs_reality": tvr,
             "extras": {"nonzero_update_frac": st["nonzero_updates"] / max(st["updates"], 1),
                        "mean_col_nnz_gathered": st["gathered_nnz"] / max(st["updates"], 1),
                        "us_per_iteration_kernel": 1e3 * st["iter_kernel_ms"] / max(st["iterations"], 1),

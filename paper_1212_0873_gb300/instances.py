@@ -229,3 +229,26 @@ def batched_path_instance(m=4_000_000, n=2_000_000, per_col=15, nrhs=16, val_dty
     inst = per_col_instance(m, n, per_col, density=0.005, noise=0.01, lam_frac=0.1, val_dtype=val_dtype, seed=seed)
     B, lam_max = multi_rhs(inst, nrhs, density=0.005, noise=0.01, seed=seed + 1)
     return inst, B, lam_max
+
+
+def equal_rows_instance(m=3000, n=1000, omega=5, seed=1006):
+    """The theory-versus-reality matrix (Sec. 8.2): every row has exactly omega
+    nonzeros, all equal to 1, at distinct uniform columns (the 0-1 construction
+    for which the DSO bound is tight, Sec. 5.1); b ~ N(0, 1); lambda = 0
+    (least squares).  Returns an Instance with lam = 0 and x_star = 0."""
+    rng = np.random.default_rng(seed)
+    cols = _distinct_rows(rng, m, omega, n)
+    key = cols.reshape(-1)
+    key <<= 32
+    key |= np.repeat(np.arange(m, dtype=np.int64), omega)
+    key.sort()
+    cols_sorted = key >> 32
+    row_idx = (key & 0xFFFFFFFF).astype(np.int32)
+    counts = np.bincount(cols_sorted, minlength=n)
+    col_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=col_ptr[1:])
+    val = np.ones(row_idx.size)
+    b = rng.standard_normal(m)
+    meta = dict(kind="equal_rows", omega=omega, seed=seed)
+    return Instance(m=m, n=n, col_ptr=col_ptr, row_idx=row_idx, val=val, val_dtype="f64", val64=val.copy(),
+                    b=b, lam=0.0, x_star=np.zeros(n), meta=meta)
