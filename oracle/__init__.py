@@ -16,6 +16,9 @@ Citations (sections, equations and tables of the paper):
   objective      F(x) of eq. (P) for LASSO (Sec. 8.1)
   gap            LASSO duality gap at theta = min(1, lambda/||A^T g||_inf) g
   run            iterations of Algorithm 1 with periodic residual refresh
+  sample_independent, binomial_keep, q_independent, moments, beta_du, run_sampling
+                 the tau-independent and (tau, p_b)-binomial samplings (Sec. 4.1
+                 items 4 and 5) and beta of Theorem ESO-DU
   active_set_solution, implicit_grad
                  the LASSO optimality condition on a fixed support and sign
                  pattern, and the implicit-function derivatives of the solution
@@ -79,6 +82,19 @@ def _declare(L):
         L.pcdm_oracle_residual.restype = None
         L.pcdm_oracle_objective.argtypes = [_i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl]
         L.pcdm_oracle_objective.restype = _dbl
+        L.pcdm_oracle_sample_independent.argtypes = [_u64, _i64, _i64, _i64, _ptr, _ptr]
+        L.pcdm_oracle_sample_independent.restype = ctypes.c_int
+        L.pcdm_oracle_binomial_keep.argtypes = [_u64, _i64, _i64, _dbl, _ptr]
+        L.pcdm_oracle_binomial_keep.restype = None
+        L.pcdm_oracle_q_independent.argtypes = [_i64, _i64, _ptr]
+        L.pcdm_oracle_q_independent.restype = None
+        L.pcdm_oracle_moments.argtypes = [ctypes.c_int, _i64, _i64, _dbl, _ptr, _ptr]
+        L.pcdm_oracle_moments.restype = None
+        L.pcdm_oracle_beta_du.argtypes = [_i64, _dbl, _dbl, _i64]
+        L.pcdm_oracle_beta_du.restype = _dbl
+        L.pcdm_oracle_run_sampling.argtypes = [_i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _dbl, ctypes.c_int,
+                                               _dbl, _i64, _u64, _i64, _i64, _i64, _ptr, _ptr]
+        L.pcdm_oracle_run_sampling.restype = ctypes.c_int
         L.pcdm_oracle_gap.argtypes = [_i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _ptr]
         L.pcdm_oracle_gap.restype = None
         L.pcdm_oracle_run.argtypes = [_i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _dbl, _i64,
@@ -220,6 +236,17 @@ class State:
             raise ValueError("oracle run failed")
         self.k += int(iters)
 
+    def run_sampling(self, kind, tau, iters, seed, p_b=1.0, refresh_every=0, beta=None):
+        """run() with the sampling `kind` ("nice", "independent", "binomial") and
+        beta of Theorem ESO-DU unless given."""
+        b_ = beta_sampling(self.omega, kind, tau, self.A.n, p_b) if beta is None else float(beta)
+        rc = lib().pcdm_oracle_run_sampling(*self.A.args(), _p(self.b), _p(self.L), self.lam, b_, SAMPLINGS[kind],
+                                            float(p_b), int(tau), int(seed) & (2**64 - 1), int(self.k), int(iters),
+                                            int(refresh_every), _p(self.x), _p(self.g))
+        if rc != 0:
+            raise ValueError("oracle run failed")
+        self.k += int(iters)
+
     def refresh(self):
         self.g = residual(self.A, self.b, self.x)
 
@@ -243,6 +270,46 @@ class State:
             rec = self.gap()
             rel = rec["gap"] / max(rec["primal"], 1e-300)
         return done, rel
+
+
+# ----------------------------------------------------------------------------- other samplings
+SAMPLINGS = {"nice": 0, "independent": 1, "binomial": 2}
+
+
+def sample_independent(seed, k, n, tau):
+    """(picks, active): tau iid picks and the first-occurrence flags (Sec. 4.1 item 4)."""
+    S = np.empty(tau, dtype=np.int32)
+    act = np.empty(tau, dtype=np.uint8)
+    if lib().pcdm_oracle_sample_independent(int(seed) & (2**64 - 1), int(k), int(n), int(tau), _p(S), _p(act)):
+        raise ValueError("bad sizes")
+    return S, act.astype(bool)
+
+
+def binomial_keep(seed, k, tau, p_b):
+    act = np.empty(tau, dtype=np.uint8)
+    lib().pcdm_oracle_binomial_keep(int(seed) & (2**64 - 1), int(k), int(tau), float(p_b), _p(act))
+    return act.astype(bool)
+
+
+def q_independent(n, tau):
+    q = np.zeros(int(tau) + 1)
+    lib().pcdm_oracle_q_independent(int(n), int(tau), _p(q))
+    return q
+
+
+def moments(kind, n, tau, p_b=1.0):
+    e1, e2 = _dbl(), _dbl()
+    lib().pcdm_oracle_moments(SAMPLINGS[kind], int(n), int(tau), float(p_b), ctypes.byref(e1), ctypes.byref(e2))
+    return e1.value, e2.value
+
+
+def beta_du(omega_, e1, e2, n):
+    return float(lib().pcdm_oracle_beta_du(int(omega_), float(e1), float(e2), int(n)))
+
+
+def beta_sampling(omega_, kind, tau, n, p_b=1.0):
+    e1, e2 = moments(kind, n, tau, p_b)
+    return beta_du(omega_, e1, e2, n)
 
 
 # ----------------------------------------------------------------------------- derivatives (dense)

@@ -29,6 +29,15 @@
  *   pcdm_oracle_objective       F(x) = 1/2 ||Ax-b||^2 + lambda ||x||_1  (eq. P with LASSO, Sec. 8.1)
  *   pcdm_oracle_run             K iterations of Algorithm 1 with the residual refreshed
  *                               every refresh_every iterations
+ *   pcdm_oracle_sample_independent   tau-independent sampling (Sec. 4.1, item 4): tau iid
+ *                               uniform picks; a block picked more than once is updated
+ *                               once (the first pick), the others are idle
+ *   pcdm_oracle_binomial_keep   (tau, p_b)-binomial sampling (Sec. 4.1, item 5, case 2):
+ *                               the tau-nice positions, each kept with probability p_b
+ *   pcdm_oracle_q_independent   the paper's q_k = C(n,k) c_k recursion for item 4
+ *   pcdm_oracle_moments         E|S| and E|S|^2 of the three samplings
+ *   pcdm_oracle_beta_du         beta of Theorem ESO-DU from E|S| and E|S|^2
+ *   pcdm_oracle_run_sampling    pcdm_oracle_run with the sampling chosen by `kind`
  *
  * Sampler spec (shared in words only):
  *   w = smallest even integer >= 2 with 2^w >= n;  hb = w/2;  mask = 2^hb - 1
@@ -338,5 +347,152 @@ int pcdm_oracle_run(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t 
             pcdm_oracle_residual(m, n, col_ptr, row_idx, val, b, x, g);
     }
     free(S); free(hbuf); free(xbuf);
+    return rc;
+}
+
+
+/* ---------------------------------------------------------------------- */
+/* Other doubly uniform samplings (Sec. 4.1 items 4 and 5) and their beta  */
+/* (Theorem ESO-DU).  Sampling kinds: 0 tau-nice, 1 tau-independent,      */
+/* 2 (tau, p_b)-binomial.                                                  */
+/* Spec (shared in words only):                                            */
+/*   independent: W_j = w0 | w1 << 32 of Philox4x32-10(counter = (j, 1,    */
+/*     lo32(k), hi32(k)), key = (lo32(seed), hi32(seed))); pick_j =        */
+/*     floor(W_j * n / 2^64); position j is active iff no position j' < j  */
+/*     picked the same block.                                              */
+/*   binomial: positions j < tau of the tau-nice S_k; position j is kept   */
+/*     iff word 0 of Philox4x32-10(counter = (j, 2, lo32(k), hi32(k)),     */
+/*     same key) is below T = min(2^32, floor(p_b * 2^32)).                */
+/* ---------------------------------------------------------------------- */
+static void philox_block(uint64_t seed, uint32_t c0, uint32_t c1, uint64_t k, uint32_t out[4])
+{
+    const uint32_t ctr[4] = {c0, c1, (uint32_t)k, (uint32_t)(k >> 32)};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    pcdm_oracle_philox4x32_10(ctr, key, out);
+}
+
+int pcdm_oracle_sample_independent(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S,
+                                   uint8_t *active)
+{
+    if (n < 1 || n > 2147483647LL || tau < 0 || k < 0) return -1;
+    uint8_t *seen = (uint8_t *)calloc((size_t)n, 1);
+    if (!seen) return -1;
+    for (int64_t j = 0; j < tau; ++j) {
+        uint32_t w[4];
+        philox_block(seed, (uint32_t)j, 1u, (uint64_t)k, w);
+        const uint64_t W = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+        const int64_t pick = (int64_t)(((unsigned __int128)W * (unsigned __int128)(uint64_t)n) >> 64);
+        S[j] = (int32_t)pick;
+        active[j] = seen[pick] ? 0 : 1;
+        seen[pick] = 1;
+    }
+    free(seen);
+    return 0;
+}
+
+static uint64_t keep_threshold(double p_b)
+{
+    if (p_b >= 1.0) return (uint64_t)1 << 32;
+    if (p_b <= 0.0) return 0;
+    return (uint64_t)floor(p_b * 4294967296.0);
+}
+
+void pcdm_oracle_binomial_keep(uint64_t seed, int64_t k, int64_t tau, double p_b, uint8_t *active)
+{
+    const uint64_t T = keep_threshold(p_b);
+    for (int64_t j = 0; j < tau; ++j) {
+        uint32_t w[4];
+        philox_block(seed, (uint32_t)j, 2u, (uint64_t)k, w);
+        active[j] = (uint64_t)w[0] < T ? 1 : 0;
+    }
+}
+
+/* q_k = C(n, k) c_k, c_1 = (1/n)^tau, c_k = (k/n)^tau - sum_{i<k} C(k, i) c_i
+ * (Sec. 4.1 item 4), k = 1 .. tau, written to q[k]; q[0] = 0.  Small n and tau only. */
+void pcdm_oracle_q_independent(int64_t n, int64_t tau, double *q)
+{
+    double *c = (double *)calloc((size_t)(tau + 1), sizeof(double));
+    q[0] = 0.0;
+    for (int64_t kk = 1; kk <= tau; ++kk) {
+        double ck = pow((double)kk / (double)n, (double)tau);
+        double binom = 1.0;                       /* C(kk, i), built up over i */
+        for (int64_t i = 1; i < kk; ++i) {
+            binom = binom * (double)(kk - i + 1) / (double)i;
+            ck -= binom * c[i];
+        }
+        c[kk] = ck;
+        double cnk = 1.0;                         /* C(n, kk) */
+        for (int64_t i = 1; i <= kk; ++i) cnk = cnk * (double)(n - kk + i) / (double)i;
+        q[kk] = cnk * ck;
+    }
+    free(c);
+}
+
+/* E|S| and E|S|^2.  nice: tau, tau^2.  independent: with a = (1 - 1/n)^tau and
+ * b2 = (1 - 2/n)^tau, E|S| = n (1 - a), E|S|^2 = E|S| + n (n-1) (1 - 2a + b2)
+ * (inclusion of one block, of two blocks).  binomial: tau p_b and
+ * tau p_b (1 + tau p_b - p_b) as printed with its definition. */
+void pcdm_oracle_moments(int kind, int64_t n, int64_t tau, double p_b, double *e1, double *e2)
+{
+    const double t = (double)tau, nn = (double)n;
+    if (kind == 1) {
+        const double a = exp(t * log1p(-1.0 / nn));
+        const double b2 = n > 1 ? exp(t * log1p(-2.0 / nn)) : 0.0;
+        *e1 = nn * (1.0 - a);
+        *e2 = *e1 + nn * (nn - 1.0) * (1.0 - 2.0 * a + b2);
+    } else if (kind == 2) {
+        *e1 = t * p_b;
+        *e2 = t * p_b * (1.0 + t * p_b - p_b);
+    } else {
+        *e1 = t;
+        *e2 = t * t;
+    }
+}
+
+/* beta = 1 + (omega - 1)(E|S|^2 / E|S| - 1) / max(1, n - 1)  (Theorem ESO-DU). */
+double pcdm_oracle_beta_du(int64_t omega, double e1, double e2, int64_t n)
+{
+    const double om = (double)(omega < 1 ? 1 : omega);
+    const double denom = (double)(n - 1 > 1 ? n - 1 : 1);
+    if (!(e1 > 0.0)) return 1.0;
+    return 1.0 + (om - 1.0) * (e2 / e1 - 1.0) / denom;
+}
+
+/* Iterations of Algorithm 1 with the sampling `kind`: the positions of the
+ * drawn list that are active form S_k (inactive ones are idle); the step and
+ * update are those of pcdm_oracle_iteration, applied to the active positions
+ * in list order. */
+int pcdm_oracle_run_sampling(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx,
+                             const double *val, const double *b, const double *L, double lambda,
+                             double beta, int kind, double p_b, int64_t tau, uint64_t seed, int64_t k0,
+                             int64_t iters, int64_t refresh_every, double *x, double *g)
+{
+    if (tau < 1 || tau > n || kind < 0 || kind > 2) return -1;
+    int32_t *S = (int32_t *)malloc((size_t)tau * sizeof(int32_t));
+    int32_t *Sa = (int32_t *)malloc((size_t)tau * sizeof(int32_t));
+    uint8_t *act = (uint8_t *)malloc((size_t)tau);
+    double *hbuf = (double *)malloc((size_t)tau * sizeof(double));
+    double *xbuf = (double *)malloc((size_t)tau * sizeof(double));
+    int rc = 0;
+    if (!S || !Sa || !act || !hbuf || !xbuf) rc = -1;
+    for (int64_t it = 0; rc == 0 && it < iters; ++it) {
+        const int64_t k = k0 + it;
+        if (kind == 1) {
+            if (pcdm_oracle_sample_independent(seed, k, n, tau, S, act) != 0) { rc = -1; break; }
+        } else {
+            if (pcdm_oracle_sample(seed, k, n, tau, S) != 0) { rc = -1; break; }
+            if (kind == 2)
+                pcdm_oracle_binomial_keep(seed, k, tau, p_b, act);
+            else
+                for (int64_t j = 0; j < tau; ++j) act[j] = 1;
+        }
+        int64_t na = 0;
+        for (int64_t j = 0; j < tau; ++j)
+            if (act[j]) Sa[na++] = S[j];
+        pcdm_oracle_iteration(m, n, col_ptr, row_idx, val, L, lambda, beta, na, Sa, x, g, hbuf, xbuf);
+        if (refresh_every > 0 && (k + 1) % refresh_every == 0)
+            pcdm_oracle_residual(m, n, col_ptr, row_idx, val, b, x, g);
+    }
+    free(S); free(Sa); free(act); free(hbuf); free(xbuf);
     return rc;
 }

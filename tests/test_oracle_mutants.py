@@ -18,6 +18,7 @@ from oracle import build as oracle_build
 
 from . import test_oracle_method as M
 from . import test_oracle_sampler as Smp
+from . import test_oracle_samplings as Smv
 
 MUTANTS = {
     "beta_denominator_n": ("double denom = (double)(n - 1 > 1 ? n - 1 : 1);",
@@ -45,6 +46,12 @@ MUTANTS = {
     "philox_multiplier": ("0xCD9E8D57u", "0xCD9E8D59u"),
     "feistel_four_rounds": ("#define ORACLE_FEISTEL_ROUNDS 12", "#define ORACLE_FEISTEL_ROUNDS 4"),
     "empty_column_keeps_x": ("            x_new = 0.0;\n        }", "            x_new = x[i];\n        }"),
+    "duplicates_not_idle": ("active[j] = seen[pick] ? 0 : 1;", "active[j] = 1;"),
+    "beta_du_drops_minus_one": ("(e2 / e1 - 1.0)", "(e2 / e1)"),
+    "binomial_second_moment": ("*e2 = t * p_b * (1.0 + t * p_b - p_b);", "*e2 = t * p_b * (1.0 + t * p_b);"),
+    "independent_pick_skewed": ("(int64_t)(((unsigned __int128)W * (unsigned __int128)(uint64_t)n) >> 64)",
+                                "(int64_t)(((unsigned __int128)(W >> 1) * (unsigned __int128)(uint64_t)n) >> 64)"),
+    "q_recursion_sign": ("ck -= binom * c[i];", "ck += binom * c[i];"),
 }
 
 PINS = [
@@ -57,6 +64,11 @@ PINS = [
     M.test_objective_matches_dense,
     lambda: [Smp.test_philox_known_answers(*row) for row in Smp._kat_rows()],
     lambda: [Smp.test_every_subset_equally_likely(n, t, s) for n, t, s in [(5, 2, 2), (8, 2, 4), (10, 3, 5)]],
+    Smv.test_q_values_printed_in_the_paper, Smv.test_binomial_and_nice_moments, Smv.test_independent_sampler_law,
+    Smv.test_beta_du_reduces_to_nice,
+    lambda: [Smv.test_independent_moments_match_the_recursion(n, t) for n, t in [(5, 3), (12, 4)]],
+    lambda: [Smv.test_eso_du_holds_by_enumeration(k) for k in ("independent", "binomial")],
+    Smv.test_duplicates_are_idle_in_one_iteration,
 ]
 
 
