@@ -85,8 +85,30 @@ typedef struct {
     int64_t lanes_per_col;       /* threads that share one column: 0 (auto), 4, 8, 16 or 32     */
     uint64_t barrier_timeout_ns; /* bound on every grid-barrier wait of the fused kernel          */
     int32_t profile;             /* 1: time every iteration-kernel launch with CUDA events        */
-    int32_t reserved;
+    int32_t sampling;            /* PCDM_SAMPLING_NICE (default), _INDEPENDENT or _BINOMIAL       */
+    double p_b;                  /* binomial sampling: probability that a position is kept, (0, 1] */
 } pcdm_opts;
+
+/*
+ * Samplings (Sec. 4.1).  All three are doubly uniform; beta follows Theorem
+ * ESO-DU, 1 + (omega-1)(E|S|^2/E|S| - 1)/max(1, n-1), which for the tau-nice
+ * sampling is the beta of Theorem ESO-nice.
+ *  NICE         tau distinct blocks, uniform over tau-subsets (see pcdm_step).
+ *  INDEPENDENT  tau picks, each uniform over [0, n) and independent: pick j is
+ *               floor(W_j n / 2^64), W_j the low 64 bits (words 0, 1) of the
+ *               Philox4x32-10 block with counter (j, 1, lo32 k, hi32 k) and key
+ *               (lo32 seed, hi32 seed); a block picked more than once is updated
+ *               once, by its first pick (the others are idle).
+ *               E|S| = n(1 - a), E|S|^2 = E|S| + n(n-1)(1 - 2a + (1-2/n)^tau),
+ *               a = (1-1/n)^tau.
+ *  BINOMIAL     the tau-nice positions, each kept independently with
+ *               probability p_b (the paper's unreliable-processor model, case 2):
+ *               position j is kept iff word 0 of the Philox block with counter
+ *               (j, 2, lo32 k, hi32 k) is below min(2^32, floor(p_b 2^32)).
+ *               E|S| = tau p_b, E|S|^2 = tau p_b (1 + tau p_b - p_b).
+ * INDEPENDENT and BINOMIAL run the two-kernel form (opts.fused is ignored).
+ */
+enum { PCDM_SAMPLING_NICE = 0, PCDM_SAMPLING_INDEPENDENT = 1, PCDM_SAMPLING_BINOMIAL = 2 };
 
 /* Counters since pcdm_create or pcdm_reset_stats. */
 typedef struct {
@@ -105,7 +127,7 @@ typedef struct {
 } pcdm_stats;
 
 /* Default options: xg_dtype F64, fused 1, refresh_every 0, check_every 0,
- * lanes_per_col 0, barrier_timeout_ns 2e9, profile 0. */
+ * lanes_per_col 0, barrier_timeout_ns 2e9, profile 0, sampling NICE, p_b 1. */
 void pcdm_default_opts(pcdm_opts *opts);
 
 /*
@@ -200,7 +222,8 @@ pcdm_status pcdm_set_lambda(pcdm_handle h, double lambda);
 /* omega, the degree of partial separability of f (largest row count of A). */
 pcdm_status pcdm_omega(pcdm_handle h, int64_t *omega);
 
-/* beta = 1 + (omega-1)(tau-1)/max(1, n-1) (Theorem ESO-nice); omega taken as >= 1. */
+/* beta of the handle's sampling for tau (Theorem ESO-DU; for the tau-nice
+ * sampling 1 + (omega-1)(tau-1)/max(1, n-1), Theorem ESO-nice); omega taken as >= 1. */
 pcdm_status pcdm_beta(pcdm_handle h, int64_t tau, double *beta);
 
 /* The iteration counter k (iterations run since create or reset), and its setter
@@ -222,6 +245,16 @@ pcdm_status pcdm_reset_stats(pcdm_handle h);
  * 1 <= n < 2^31, 0 <= tau <= n, k >= 0.  No handle needed.
  */
 pcdm_status pcdm_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S_device, void *cuda_stream);
+
+/*
+ * The list of iteration k of sampling `kind` on its own (no handle): for NICE
+ * and BINOMIAL the tau-nice positions S_device[j] = pi_k(j), for INDEPENDENT
+ * the tau picks (repeats included; which of them are idle is decided inside
+ * the solver).  keep_device (tau bytes, may be NULL) receives 1 for the kept
+ * positions of BINOMIAL (all 1 for NICE; not written for INDEPENDENT).
+ */
+pcdm_status pcdm_sample_kind(int32_t kind, uint64_t seed, int64_t k, int64_t n, int64_t tau, double p_b,
+                             int32_t *S_device, uint8_t *keep_device, void *cuda_stream);
 
 /*
  * Self-test of the bounded grid barrier used by the fused kernel: launches a
@@ -327,7 +360,7 @@ typedef struct pcdm_batch_ctx *pcdm_batch_handle;
  *             copied and kept in FP64
  * lambdas     nrhs host doubles, finite and >= 0
  * opts        as for pcdm_create (xg_dtype, refresh_every, check_every,
- *             barrier_timeout_ns, profile are used)
+ *             barrier_timeout_ns, profile are used; sampling must be NICE)
  * Errors: those of pcdm_create, EINVAL for nrhs out of range, a bad lambda or a
  * non-finite value in B.
  */

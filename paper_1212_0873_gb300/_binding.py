@@ -25,7 +25,8 @@ class pcdm_csc(ctypes.Structure):
 
 class pcdm_opts(ctypes.Structure):
     _fields_ = [("xg_dtype", _i32), ("fused", _i32), ("refresh_every", _i64), ("check_every", _i64),
-                ("lanes_per_col", _i64), ("barrier_timeout_ns", _u64), ("profile", _i32), ("reserved", _i32)]
+                ("lanes_per_col", _i64), ("barrier_timeout_ns", _u64), ("profile", _i32), ("sampling", _i32),
+                ("p_b", _dbl)]
 
 
 class pcdm_stats(ctypes.Structure):
@@ -64,6 +65,7 @@ SIGNATURES = {
     "pcdm_support_size": (_i32, [_ptr, _ptr]),
     "pcdm_polish": (_i32, [_ptr, _i64, _u64, _dbl, _i64, _ptr, _ptr]),
     "pcdm_backward": (_i32, [_ptr, _ptr, _i32, _ptr, _i32, _ptr, _i64, _u64, _dbl, _i64, _ptr, _ptr]),
+    "pcdm_sample_kind": (_i32, [_i32, _u64, _i64, _i64, _i64, _dbl, _ptr, _ptr, _ptr]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -367,3 +369,12 @@ def pcdm_backward(h, dx_ptr, dx_on_device, db_ptr, db_on_device, tau, seed, tol,
         return False, dl.value, it.value, rel.value
     _check(st, h)
     return True, dl.value, it.value, rel.value
+
+
+PCDM_SAMPLING_NICE, PCDM_SAMPLING_INDEPENDENT, PCDM_SAMPLING_BINOMIAL = 0, 1, 2
+SAMPLING_CODES = {"nice": 0, "independent": 1, "binomial": 2}
+
+
+def pcdm_sample_kind(kind, seed, k, n, tau, p_b, S_device_ptr, keep_device_ptr=None, stream=0):
+    _check(lib().pcdm_sample_kind(int(kind), int(seed) & (2**64 - 1), int(k), int(n), int(tau), float(p_b),
+                                  _ptr(S_device_ptr), _ptr(keep_device_ptr), _stream(stream)), None)

@@ -47,6 +47,35 @@ __global__ void k_check_colptr(const int64_t *col_ptr, int64_t n, int64_t nnz, i
     if (f) atomicOr(flags, f);
 }
 
+// S_k of the other samplings (see launch_sample_kind in pcdm_internal.h).
+__global__ void k_sample_kind(int kind, uint64_t seed, int64_t k, int64_t n, int64_t tau, uint64_t keep_T,
+                              int32_t *S, unsigned long long *win, uint8_t *keep)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (kind == 1) {
+        for (; j < tau; j += stride) {
+            const int32_t i = independent_pick(seed, k, uint32_t(j), n);
+            S[j] = i;
+            if (win) atomicMax(win + i, independent_key(k, uint32_t(j)));
+        }
+        return;
+    }
+    const SampleKey key = warp_sample_key(seed, k, n);
+    for (; j < tau; j += stride) {
+        S[j] = sample_index(uint32_t(j), key);
+        if (keep) keep[j] = (kind == 2 && !binomial_keep(seed, k, uint32_t(j), keep_T)) ? 0 : 1;
+    }
+}
+
+cudaError_t launch_sample_kind(int kind, uint64_t seed, int64_t k, int64_t n, int64_t tau, uint64_t keep_T,
+                               int32_t *S, unsigned long long *win, uint8_t *keep, cudaStream_t st)
+{
+    if (tau <= 0) return cudaSuccess;
+    k_sample_kind<<<grid_for(tau), 256, 0, st>>>(kind, seed, k, n, tau, keep_T, S, win, keep);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check_colptr(const int64_t *col_ptr, int64_t n, int64_t nnz, int *flags, cudaStream_t st)
 {
     k_check_colptr<<<grid_for(n + 1), 256, 0, st>>>(col_ptr, n, nnz, flags);

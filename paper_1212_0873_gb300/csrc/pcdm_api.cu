@@ -24,7 +24,7 @@ void free_all(pcdm_handle h)
     void *ptrs[] = {h->desc, h->prow, h->pval, h->b, h->L64, h->x, h->g, h->g2,
                     h->S[0], h->S[1], h->h, h->counters, h->bar, h->status, h->gap_part, h->gap_out,
                     h->as_sidx, h->as_c, h->as_sgn, h->as_u, h->as_dx, h->as_q, h->as_rowcnt, h->as_H,
-                    h->as_S, h->as_part};
+                    h->as_S, h->as_part, h->win};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->g64 && h->g64 != h->g) cudaFree(h->g64);
@@ -38,6 +38,15 @@ void free_all(pcdm_handle h)
 
 // Lanes per column: enough lanes of kLaneRun entries each to cover a column
 // of average length in one chunk.
+// beta of the handle's sampling (Theorem ESO-DU; ESO-nice for the tau-nice sampling).
+double beta_for(pcdm_handle h, int64_t tau)
+{
+    if (h->opts.sampling == PCDM_SAMPLING_NICE) return beta_nice(h->omega, tau, h->n);
+    double e1 = 0.0, e2 = 0.0;
+    sampling_moments(h->opts.sampling, h->n, tau, h->opts.p_b, &e1, &e2);
+    return beta_du(h->omega, e1, e2, h->n);
+}
+
 int auto_lanes(int64_t nnz, int64_t n)
 {
     const double mean = n > 0 ? double(nnz) / double(n) : 0.0;
@@ -78,7 +87,10 @@ IterArgs<VT, XT> iter_args(pcdm_handle h, int64_t tau, uint64_t seed)
     a.h = static_cast<XT *>(h->h);
     a.S[0] = h->S[0];
     a.S[1] = h->S[1];
-    a.inv_beta = 1.0 / beta_nice(h->omega, tau, h->n);
+    a.inv_beta = 1.0 / beta_for(h, tau);
+    a.sampling = h->opts.sampling;
+    a.keep_T = binomial_threshold(h->opts.p_b);
+    a.win = h->win;
     a.lambda = h->lambda;
     a.n = h->n;
     a.tau = tau;
@@ -145,7 +157,29 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         CK(h, take_event(h, &e1));
         CK(h, cudaEventRecord(e0, h->stream));
     }
-    if (h->opts.fused) {
+    if (h->opts.sampling != PCDM_SAMPLING_NICE) {
+        // the other samplings: draw, gather, scatter per iteration
+        if (h->opts.sampling == PCDM_SAMPLING_INDEPENDENT) {
+            if (!h->win) {
+                CK(h, cudaStreamSynchronize(h->stream));
+                CK(h, dalloc(&h->win, h->n));
+                a.win = h->win;
+            }
+            // keys of a later iteration than k would shadow this run's (after set_iteration)
+            CK(h, cudaMemsetAsync(h->win, 0, sizeof(unsigned long long) * size_t(h->n), h->stream));
+        }
+        for (int64_t it = 0; it < iters; ++it) {
+            const int64_t kk = h->k + it;
+            CK(h, launch_sample_kind(h->opts.sampling, seed, kk, h->n, tau, a.keep_T, a.S[kk & 1],
+                                     h->opts.sampling == PCDM_SAMPLING_INDEPENDENT ? h->win : nullptr, nullptr,
+                                     h->stream));
+            CK(h, Kernels<VT, XT>::gather(a, h->W, kk, h->stream));
+            CK(h, Kernels<VT, XT>::scatter(a, h->W, kk, false, h->stream));
+        }
+        h->g2_valid = false;
+        h->st_launches += iters;
+        h->st_kernels += 3 * iters;
+    } else if (h->opts.fused) {
         FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
         if (pipe_shape<VT, XT>(h, tau, &sh)) {
@@ -276,6 +310,8 @@ void pcdm_default_opts(pcdm_opts *o)
     o->lanes_per_col = 0;
     o->barrier_timeout_ns = kDefaultTimeoutNs;
     o->profile = 0;
+    o->sampling = PCDM_SAMPLING_NICE;
+    o->p_b = 1.0;
 }
 
 const char *pcdm_status_string(pcdm_status s)
@@ -317,6 +353,10 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         o.lanes_per_col != 32)
         return set_err(nullptr, PCDM_EINVAL, "lanes_per_col must be 0, 4, 8, 16 or 32");
     if (o.refresh_every < 0 || o.check_every < 0) return set_err(nullptr, PCDM_EINVAL, "negative period");
+    if (o.sampling < PCDM_SAMPLING_NICE || o.sampling > PCDM_SAMPLING_BINOMIAL)
+        return set_err(nullptr, PCDM_EINVAL, "unknown sampling");
+    if (o.sampling == PCDM_SAMPLING_BINOMIAL && !(o.p_b > 0.0 && o.p_b <= 1.0))
+        return set_err(nullptr, PCDM_EINVAL, "p_b must be in (0, 1]");
 
     pcdm_ctx *h = new (std::nothrow) pcdm_ctx();
     if (!h) return set_err(nullptr, PCDM_ENOMEM, "host allocation failed");
@@ -664,7 +704,7 @@ pcdm_status pcdm_beta(pcdm_handle h, int64_t tau, double *beta)
 {
     if (!h || !beta) return set_err(h, PCDM_EINVAL, "NULL argument");
     if (tau < 1 || tau > h->n) return set_err(h, PCDM_EINVAL, "tau must be in [1, n]");
-    *beta = beta_nice(h->omega, tau, h->n);
+    *beta = beta_for(h, tau);
     return PCDM_OK;
 }
 
@@ -1029,6 +1069,23 @@ pcdm_status pcdm_omega_noalloc(const pcdm_csc *A, int64_t *omega, void *cuda_str
     if (host[0] & FLAG_ROW_RANGE) return set_err(nullptr, PCDM_EINVAL, "a row index outside [0, m)");
     if (host[0] & FLAG_ROW_ORDER) return set_err(nullptr, PCDM_EINVAL, "rows of a column not strictly increasing");
     *omega = host[1];
+    return PCDM_OK;
+}
+
+pcdm_status pcdm_sample_kind(int32_t kind, uint64_t seed, int64_t k, int64_t n, int64_t tau, double p_b,
+                             int32_t *S_device, uint8_t *keep_device, void *cuda_stream)
+{
+    if (kind < PCDM_SAMPLING_NICE || kind > PCDM_SAMPLING_BINOMIAL)
+        return set_err(nullptr, PCDM_EINVAL, "unknown sampling");
+    if (n < 1 || n > 2147483647LL || tau < 0 || tau > n || k < 0)
+        return set_err(nullptr, PCDM_EINVAL, "need 1 <= n < 2^31, 0 <= tau <= n, k >= 0");
+    if (kind == PCDM_SAMPLING_BINOMIAL && !(p_b > 0.0 && p_b <= 1.0))
+        return set_err(nullptr, PCDM_EINVAL, "p_b must be in (0, 1]");
+    if (tau > 0 && !S_device) return set_err(nullptr, PCDM_EINVAL, "S_device is NULL");
+    cudaError_t e = launch_sample_kind(kind, seed, k, n, tau, binomial_threshold(p_b), S_device, nullptr,
+                                       kind == PCDM_SAMPLING_INDEPENDENT ? nullptr : keep_device,
+                                       static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "launch_sample_kind");
     return PCDM_OK;
 }
 

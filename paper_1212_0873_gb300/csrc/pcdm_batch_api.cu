@@ -341,6 +341,8 @@ pcdm_status pcdm_batch_create(const pcdm_csc *A, int64_t nrhs, const void *B, in
         if (!(lambdas[l] >= 0.0) || !std::isfinite(lambdas[l]))
             return berr(nullptr, PCDM_EINVAL, "every lambda must be finite and >= 0");
     if (b_dtype != PCDM_F64 && b_dtype != PCDM_F32) return berr(nullptr, PCDM_EINVAL, "b_dtype must be F64 or F32");
+    if (opts && opts->sampling != PCDM_SAMPLING_NICE)
+        return berr(nullptr, PCDM_EINVAL, "the batched solver runs the tau-nice sampling only");
     pcdm_handle base = nullptr;
     // A's validation and layout, with the first right-hand side
     pcdm_status s = pcdm_create(A, B, b_dtype, lambdas[0], opts, cuda_stream, &base);

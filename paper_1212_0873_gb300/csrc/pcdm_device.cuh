@@ -53,6 +53,33 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t
     out[3] = c3;
 }
 
+// The other doubly uniform samplings (Sec. 4.1 items 4 and 5).
+// tau-independent: pick j = floor(W * n / 2^64), W the low 64 bits of the Philox
+// block with counter (j, 1, lo32(k), hi32(k)); a block picked more than once is
+// updated by its first pick only, decided through the key below (larger for
+// earlier picks of the same iteration, and for later iterations).
+__device__ __forceinline__ int32_t independent_pick(uint64_t seed, int64_t k, uint32_t j, int64_t n)
+{
+    uint32_t w[4];
+    philox4x32_10(j, 1u, uint32_t(uint64_t(k)), uint32_t(uint64_t(k) >> 32), uint32_t(seed), uint32_t(seed >> 32), w);
+    const uint64_t W = uint64_t(w[0]) | (uint64_t(w[1]) << 32);
+    return int32_t(__umul64hi(W, uint64_t(n)));
+}
+
+__device__ __forceinline__ unsigned long long independent_key(int64_t k, uint32_t j)
+{
+    return ((unsigned long long)(k + 1) << 32) | (unsigned long long)(0xFFFFFFFFu - j);
+}
+
+// (tau, p_b)-binomial: position j of the tau-nice sample is kept iff word 0 of
+// the Philox block with counter (j, 2, lo32(k), hi32(k)) is below T.
+__device__ __forceinline__ bool binomial_keep(uint64_t seed, int64_t k, uint32_t j, uint64_t T)
+{
+    uint32_t w[4];
+    philox4x32_10(j, 2u, uint32_t(uint64_t(k)), uint32_t(uint64_t(k) >> 32), uint32_t(seed), uint32_t(seed >> 32), w);
+    return uint64_t(w[0]) < T;
+}
+
 constexpr int kFeistelRounds = 12;
 
 // Permutation key of iteration k: 12 round keys (three Philox blocks with

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <utility>
@@ -80,6 +81,7 @@ struct pcdm_ctx {
     double *as_part = nullptr;    // residual partials
     int64_t as_tau_cap = 0;
     int as_blocks = 0;
+    unsigned long long *win = nullptr;   // n: first-pick keys of the tau-independent sampling
 
     int64_t omega = 0;
     int64_t k = 0;
@@ -138,6 +140,38 @@ inline cudaError_t dalloc_bytes(void **p, int64_t bytes)
     *p = nullptr;
     if (bytes <= 0) bytes = 16;
     return cudaMalloc(p, size_t(bytes));
+}
+
+// Moments E|S|, E|S|^2 of the samplings (see pcdm.h) and beta of Theorem ESO-DU.
+inline void sampling_moments(int kind, int64_t n, int64_t tau, double p_b, double *e1, double *e2)
+{
+    const double t = double(tau), nn = double(n);
+    if (kind == PCDM_SAMPLING_INDEPENDENT) {
+        const double a = std::exp(t * std::log1p(-1.0 / nn));
+        const double a2 = n > 1 ? std::exp(t * std::log1p(-2.0 / nn)) : 0.0;
+        *e1 = nn * (1.0 - a);
+        *e2 = *e1 + nn * (nn - 1.0) * (1.0 - 2.0 * a + a2);
+    } else if (kind == PCDM_SAMPLING_BINOMIAL) {
+        *e1 = t * p_b;
+        *e2 = t * p_b * (1.0 + t * p_b - p_b);
+    } else {
+        *e1 = t;
+        *e2 = t * t;
+    }
+}
+
+inline double beta_du(int64_t omega, double e1, double e2, int64_t n)
+{
+    const double om = double(omega < 1 ? 1 : omega);
+    const double denom = double(n - 1 > 1 ? n - 1 : 1);
+    return e1 > 0.0 ? 1.0 + (om - 1.0) * (e2 / e1 - 1.0) / denom : 1.0;
+}
+
+inline uint64_t binomial_threshold(double p_b)
+{
+    if (p_b >= 1.0) return uint64_t(1) << 32;
+    if (p_b <= 0.0) return 0;
+    return uint64_t(std::floor(p_b * 4294967296.0));
 }
 
 inline double beta_nice(int64_t omega, int64_t tau, int64_t n)

@@ -74,6 +74,12 @@ struct IterArgs {
     unsigned long long *bar;        // grid-barrier counter of the fused kernel (0 at launch)
     int *status;                    // DEV_OK or DEV_TIMEOUT
     uint64_t timeout_ns;
+    // Sampling (two-kernel form only for the non-nice kinds): 0 tau-nice,
+    // 1 tau-independent (win[i] holds the key of the first pick of block i),
+    // 2 (tau, p_b)-binomial (position kept iff its coin is below keep_T).
+    int sampling;
+    uint64_t keep_T;
+    const unsigned long long *win;
 };
 
 // Launch shape of the fused kernel.
@@ -187,6 +193,11 @@ cudaError_t launch_as_linear(const double *x, const double *src, const int32_t *
 
 // Type-independent kernels (kernels_common.cu).
 cudaError_t launch_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S, cudaStream_t st);
+// S_k of sampling `kind` (0, 2: tau-nice positions; 1: tau-independent picks,
+// claiming win[pick] when win is not NULL); keep (may be NULL) receives the
+// binomial keep flags for kind 2.
+cudaError_t launch_sample_kind(int kind, uint64_t seed, int64_t k, int64_t n, int64_t tau, uint64_t keep_T,
+                               int32_t *S, unsigned long long *win, uint8_t *keep, cudaStream_t st);
 cudaError_t launch_check_colptr(const int64_t *col_ptr, int64_t n, int64_t nnz, int *flags, cudaStream_t st);
 cudaError_t launch_check_finite(const double *v, int64_t count, int *flags, cudaStream_t st);
 cudaError_t launch_max_int(const int *a, int64_t count, int *out, cudaStream_t st);

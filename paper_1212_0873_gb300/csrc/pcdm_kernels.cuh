@@ -312,9 +312,19 @@ __device__ __forceinline__ double prox_step(double xi, double grad, double invL,
 // Phase 1 for sampled position j, columns read from memory (no prefetch).
 template <int W, typename VT, typename XT>
 __device__ __forceinline__ void gather_generic(const IterArgs<VT, XT> &a, const int32_t *S, int64_t j, int lane,
-                                               unsigned gmask, Counters &cnt)
+                                               unsigned gmask, Counters &cnt, int64_t k = -1)
 {
     const int32_t i = ldcg(S + j);
+    // positions idle under the tau-independent (a repeated pick) or binomial
+    // (a dropped position) samplings take no step
+    if (k >= 0 && a.sampling != 0) {
+        const bool idle = a.sampling == 1 ? (ldcg(a.win + i) != independent_key(k, uint32_t(j)))
+                                          : !binomial_keep(a.seed, k, uint32_t(j), a.keep_T);
+        if (idle) {
+            if (lane == 0) a.h[j] = XT(0);
+            return;
+        }
+    }
     const Col<XT> c = load_col(a.desc, i);
     const double xi = ldcg(a.x + i);
     const XT grad = column_dot<W>(a, c, lane, gmask);
@@ -350,7 +360,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(const IterArgs<VT, XT> a, int
     const unsigned gmask = group_mask<W>(threadIdx.x & 31);
     const int64_t grp = (int64_t(blockIdx.x) * kBlock + threadIdx.x) / W;
     Counters cnt;
-    if (grp < a.tau) gather_generic<W>(a, sample_buf(a, k), grp, lane, gmask, cnt);
+    if (grp < a.tau) gather_generic<W>(a, sample_buf(a, k), grp, lane, gmask, cnt, k);
     flush_counters(cnt, a.counters);
 }
 

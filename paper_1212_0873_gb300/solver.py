@@ -55,7 +55,8 @@ class Lasso:
     """min 1/2 ||A x - b||^2 + lam ||x||_1 with A in CSC form, on one GPU."""
 
     def __init__(self, m, n, col_ptr, row_idx, val, b, lam, *, xg_dtype=None, fused=True, refresh_every=0,
-                 check_every=0, lanes_per_col=0, profile=False, barrier_timeout_ns=None, stream=None):
+                 check_every=0, lanes_per_col=0, profile=False, barrier_timeout_ns=None, stream=None,
+                 sampling="nice", p_b=1.0):
         val_dtype = _val_code(val)
         if xg_dtype is None:
             xg_dtype = "f64" if val_dtype == "f64" else "f32"
@@ -64,7 +65,7 @@ class Lasso:
         p_cp, d_cp = _ptr_and_device(col_ptr)
         p_ri, d_ri = _ptr_and_device(row_idx)
         p_v, d_v = _ptr_and_device(val)
-        p_b, d_b = _ptr_and_device(b)
+        p_b_ptr, d_b = _ptr_and_device(b)
         if len({d_cp, d_ri, d_v, d_b}) != 1:
             raise ValueError("A and b must all be host arrays or all be device tensors")
         nnz = int(col_ptr[-1]) if not _is_tensor(col_ptr) else int(col_ptr[-1].item())
@@ -76,11 +77,13 @@ class Lasso:
         opts.check_every = int(check_every)
         opts.lanes_per_col = int(lanes_per_col)
         opts.profile = 1 if profile else 0
+        opts.sampling = B.SAMPLING_CODES[sampling]
+        opts.p_b = float(p_b)
         if barrier_timeout_ns is not None:
             opts.barrier_timeout_ns = int(barrier_timeout_ns)
         b_dt = B.PCDM_F32 if (str(getattr(b, "dtype", "")) in ("float32", "torch.float32")) else B.PCDM_F64
         self.stream = current_stream() if stream is None else stream
-        self._h = B.pcdm_create(A, p_b, b_dt, lam, opts, self.stream)
+        self._h = B.pcdm_create(A, p_b_ptr, b_dt, lam, opts, self.stream)
         self.lam = float(lam)
 
     @classmethod
