@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--path-len", type=int, default=32, help="lambdas on the batched regularisation path")
     p.add_argument("--no-grad", action="store_true", help="skip the differentiation measurement")
     p.add_argument("--no-tvr", action="store_true", help="skip the theory-versus-reality experiment")
+    p.add_argument("--no-async", action="store_true", help="skip the asynchronous-mode measurement")
     return p.parse_args()
 
 
@@ -378,6 +379,36 @@ def run_grad():
             "support": support}
 
 
+# ----------------------------------------------------------------------------- asynchronous mode
+def run_async(a, inst):
+    """The asynchronous mode (pcdm_solve_async: every GPU thread applies
+    updates with atomics, no barrier) on the bench workload, to the same
+    relative gap; device-timed solves after one warm-up."""
+    import torch
+    from paper_1212_0873_gb300 import Lasso
+
+    out = {}
+    with Lasso.from_instance(inst, profile=False) as s:
+        def once():
+            s.reset()
+            ok, upd, rel = s.solve_async(seed=0, tol=a.tol, max_updates=10**12)
+            if not ok:
+                raise RuntimeError("asynchronous solve did not converge")
+            return upd, rel
+        once()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        upd, rel = once()
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+    out.update({"workload": "the bench workload, asynchronous updates (all resident GPU threads, atomics on x and "
+                            "g, no barrier), from x = 0 to the same relative gap",
+                "time_to_gap_s": t, "updates": upd, "updates_per_s": upd / t, "rel_gap": rel})
+    return out
+
+
 # ----------------------------------------------------------------------------- theory vs reality
 def run_theory_vs_reality():
     """Sec. 8.2: iteration speedup of tau-nice PCDM1 against tau / beta on least
@@ -500,6 +531,9 @@ def run_pcdm(a, rank, local, world):
                "sample": "first %d iterations (tau=%d, %d updates) of the same solve from x=0, single-threaded "
                          "FP64 oracle, %.1f s" % (done, a.tau, done * a.tau, used)}
 
+    asyn = None
+    if rank == 0 and world == 1 and not a.no_async:
+        asyn = run_async(a, inst)
     batched = None
     if rank == 0 and world == 1 and not a.no_batched:
         batched = run_batched_path(a)
@@ -528,6 +562,7 @@ def run_pcdm(a, rank, local, world):
             "gpu_launches": st["kernel_launches"],
             "clocks": clk,
             "batched": batched,
+            "asynchronous": asyn,
             "differentiation": grad,
             "theory_vs_reality": tvr,
             "extras": {"nonzero_update_frac": st["nonzero_updates"] / max(st["updates"], 1),

@@ -164,6 +164,27 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
  */
 pcdm_status pcdm_step(pcdm_handle h, int64_t tau, int64_t iters, uint64_t seed);
 
+/*
+ * Asynchronous mode (the shared-memory implementation of Sec. 8.1, not
+ * Algorithm 1's synchronous iteration): `threads` GPU threads (0: as many as
+ * the device holds at once, at most n) take updates u = 0, 1, 2, ... of a
+ * global sequence without any barrier.  Update u picks block i_u uniformly
+ * (the INDEPENDENT pick with k = u, position 0), reads x_i and g as they are,
+ * computes the step of eq. (h(x)) and applies it with atomic additions to x_i
+ * and g.  beta is that of the tau-independent sampling with tau = threads
+ * (Theorem ESO-DU).  With threads = 1 this is the serial method with iid
+ * blocks: it equals `updates` iterations of the INDEPENDENT sampling with
+ * tau = 1.  Results are not deterministic for threads > 1.  The update counter
+ * continues across calls (pcdm_reset sets it to 0).
+ */
+pcdm_status pcdm_step_async(pcdm_handle h, int64_t updates, uint64_t seed, int32_t threads);
+
+/* pcdm_step_async in chunks (first one epoch = n updates, then the adaptive
+ * schedule of pcdm_next_check_interval) until gap / primal <= rel_gap_tol; the
+ * gap check refreshes g.  PCDM_ENOTCONV when max_updates ran out first. */
+pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, int64_t max_updates,
+                             int32_t threads, int64_t *updates_done, double *rel_gap);
+
 /* Recompute g = A x - b in FP64 (stored in g's dtype). */
 pcdm_status pcdm_refresh(pcdm_handle h);
 

@@ -66,6 +66,8 @@ SIGNATURES = {
     "pcdm_polish": (_i32, [_ptr, _i64, _u64, _dbl, _i64, _ptr, _ptr]),
     "pcdm_backward": (_i32, [_ptr, _ptr, _i32, _ptr, _i32, _ptr, _i64, _u64, _dbl, _i64, _ptr, _ptr]),
     "pcdm_sample_kind": (_i32, [_i32, _u64, _i64, _i64, _i64, _dbl, _ptr, _ptr, _ptr]),
+    "pcdm_step_async": (_i32, [_ptr, _i64, _u64, _i32]),
+    "pcdm_solve_async": (_i32, [_ptr, _u64, _dbl, _i64, _i32, _ptr, _ptr]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -378,3 +380,18 @@ SAMPLING_CODES = {"nice": 0, "independent": 1, "binomial": 2}
 def pcdm_sample_kind(kind, seed, k, n, tau, p_b, S_device_ptr, keep_device_ptr=None, stream=0):
     _check(lib().pcdm_sample_kind(int(kind), int(seed) & (2**64 - 1), int(k), int(n), int(tau), float(p_b),
                                   _ptr(S_device_ptr), _ptr(keep_device_ptr), _stream(stream)), None)
+
+
+def pcdm_step_async(h, updates, seed, threads=0):
+    _check(lib().pcdm_step_async(h, int(updates), int(seed) & (2**64 - 1), int(threads)), h)
+
+
+def pcdm_solve_async(h, seed, rel_gap_tol, max_updates, threads=0):
+    """Returns (converged, updates_done, rel_gap)."""
+    u, rel = _i64(), _dbl()
+    st = lib().pcdm_solve_async(h, int(seed) & (2**64 - 1), float(rel_gap_tol), int(max_updates), int(threads),
+                                ctypes.byref(u), ctypes.byref(rel))
+    if st == PCDM_ENOTCONV:
+        return False, u.value, rel.value
+    _check(st, h)
+    return True, u.value, rel.value

@@ -737,6 +737,7 @@ pcdm_status pcdm_reset(pcdm_handle h)
     }
     h->ev_pending.clear();
     h->last_solve_iters = 0;
+    h->async_u = 0;
     pcdm_status s = reset_state(h);
     if (s != PCDM_OK) return s;
     CK(h, cudaStreamSynchronize(h->stream));
@@ -1069,6 +1070,98 @@ pcdm_status pcdm_omega_noalloc(const pcdm_csc *A, int64_t *omega, void *cuda_str
     if (host[0] & FLAG_ROW_RANGE) return set_err(nullptr, PCDM_EINVAL, "a row index outside [0, m)");
     if (host[0] & FLAG_ROW_ORDER) return set_err(nullptr, PCDM_EINVAL, "rows of a column not strictly increasing");
     *omega = host[1];
+    return PCDM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous mode.
+}  // extern "C"
+namespace {
+
+template <typename VT, typename XT>
+pcdm_status async_t(pcdm_handle h, int64_t updates, uint64_t seed, int32_t threads, int64_t *used_threads)
+{
+    IterArgs<VT, XT> a = iter_args<VT, XT>(h, 1, seed);
+    const int cap = Kernels<VT, XT>::async_max_blocks();
+    if (cap <= 0) return set_err(h, PCDM_ECUDA, "occupancy query failed");
+    int64_t T = threads > 0 ? threads : int64_t(cap) * kBlock;
+    if (T > h->n) T = h->n;
+    if (T < 1) T = 1;
+    const int64_t blocks = (T + kBlock - 1) / kBlock;
+    double e1 = 0.0, e2 = 0.0;
+    sampling_moments(PCDM_SAMPLING_INDEPENDENT, h->n, T, 1.0, &e1, &e2);
+    a.inv_beta = 1.0 / beta_du(h->omega, e1, e2, h->n);
+    cudaEvent_t e0 = nullptr, ev1 = nullptr;
+    if (h->opts.profile) {
+        CK(h, take_event(h, &e0));
+        CK(h, take_event(h, &ev1));
+        CK(h, cudaEventRecord(e0, h->stream));
+    }
+    CK(h, Kernels<VT, XT>::async(a, int(blocks), uint64_t(T), h->async_u, uint64_t(updates), h->stream));
+    if (h->opts.profile) {
+        CK(h, cudaEventRecord(ev1, h->stream));
+        h->ev_pending.emplace_back(e0, ev1);
+    }
+    h->async_u += uint64_t(updates);
+    h->g2_valid = false;
+    h->sample_valid = false;
+    h->st_updates += updates;
+    h->st_launches += 1;
+    h->st_kernels += 1;
+    if (used_threads) *used_threads = T;
+    return PCDM_OK;
+}
+
+}  // namespace
+extern "C" {
+
+pcdm_status pcdm_step_async(pcdm_handle h, int64_t updates, uint64_t seed, int32_t threads)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (updates < 0 || threads < 0) return set_err(h, PCDM_EINVAL, "updates and threads must be >= 0");
+    if (updates == 0) return PCDM_OK;
+    s = dispatch(h, [&](auto *vt, auto *xt) {
+        using VT = std::remove_pointer_t<decltype(vt)>;
+        using XT = std::remove_pointer_t<decltype(xt)>;
+        return async_t<VT, XT>(h, updates, seed, threads, nullptr);
+    });
+    if (s != PCDM_OK) return s;
+    return sync_check(h);
+}
+
+pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, int64_t max_updates, int32_t threads,
+                             int64_t *updates_done, double *rel_gap)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (max_updates < 0 || threads < 0 || !(rel_gap_tol >= 0.0))
+        return set_err(h, PCDM_EINVAL, "bad max_updates, threads or tolerance");
+    const int64_t epoch = h->n;   // updates between the first checks
+    int64_t every = epoch, done = 0, prev = 0;
+    double rec[9];
+    s = do_gap(h, rec);
+    if (s != PCDM_OK) return s;
+    double rel = rec[2] / (rec[0] > 1e-300 ? rec[0] : 1e-300), rel_prev = rel;
+    while (rel > rel_gap_tol && done < max_updates) {
+        const int64_t chunk = every < max_updates - done ? every : max_updates - done;
+        s = dispatch(h, [&](auto *vt, auto *xt) {
+            using VT = std::remove_pointer_t<decltype(vt)>;
+            using XT = std::remove_pointer_t<decltype(xt)>;
+            return async_t<VT, XT>(h, chunk, seed, threads, nullptr);
+        });
+        if (s != PCDM_OK) return s;
+        prev = done;
+        done += chunk;
+        rel_prev = rel;
+        s = do_gap(h, rec);   // refreshes g exactly
+        if (s != PCDM_OK) return s;
+        rel = rec[2] / (rec[0] > 1e-300 ? rec[0] : 1e-300);
+        every = pcdm_next_check_interval(epoch, prev, rel_prev, done, rel, rel_gap_tol);
+    }
+    if (updates_done) *updates_done = done;
+    if (rel_gap) *rel_gap = rel;
+    if (rel > rel_gap_tol) return set_err(h, PCDM_ENOTCONV, "max_updates reached before the gap tolerance");
     return PCDM_OK;
 }
 

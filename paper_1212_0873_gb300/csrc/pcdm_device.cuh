@@ -383,6 +383,7 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsig
 }
 
 __device__ __forceinline__ int ld_volatile_int(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+__device__ __forceinline__ double ld_volatile_f64(const double *p) { return *reinterpret_cast<const volatile double *>(p); }
 __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
 {
     return *reinterpret_cast<const volatile unsigned *>(p);

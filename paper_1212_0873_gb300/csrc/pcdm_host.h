@@ -86,6 +86,7 @@ struct pcdm_ctx {
     int64_t omega = 0;
     int64_t k = 0;
     int64_t last_solve_iters = 0;   // iterations of the last pcdm_solve (0 after create / reset)
+    uint64_t async_u = 0;           // next update number of the asynchronous mode
     bool sample_valid = false;
     uint64_t sample_seed = 0;
     int64_t sample_tau = 0, sample_k = -1;

@@ -105,6 +105,10 @@ struct Kernels {
     static cudaError_t fused_pipe(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
                                   cudaStream_t st);
     static int pipe_max_blocks(int threads);
+    // Asynchronous updates u0 .. u0+count-1 (no barrier; atomics on x and g).
+    static cudaError_t async(const IterArgs<VT, XT> &a, int blocks, uint64_t nthreads, uint64_t u0, uint64_t count,
+                             cudaStream_t st);
+    static int async_max_blocks();
     // L_i = sum a_ri^2 (FP64), row counts and validation, on the caller's CSC layout.
     static cudaError_t setup_cols(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, int64_t m,
                                   int64_t n, double *L, int *rowcnt, int *flags, cudaStream_t st);

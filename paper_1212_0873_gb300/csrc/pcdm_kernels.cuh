@@ -751,6 +751,50 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous PCDM (the shared-memory implementation mode of Sec. 8.1): every
+// thread repeatedly takes the next update u of a global sequence, picks block
+// i_u (the tau-independent pick with k = u, position 0, so that one thread
+// reproduces the serial method with iid blocks), reads x_i and the residual as
+// they are, computes the step of eq. (h(x)) with the given beta and applies it
+// with atomic additions to x_i and to g.  No barrier: reads may see other
+// threads' updates partially.  Updates u0 .. u0 + count - 1.
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_async(const IterArgs<VT, XT> a, uint64_t u0, uint64_t count,
+                                                  uint64_t nthreads)
+{
+    const uint64_t T = nthreads;   // threads taking part (the rest of the grid idles)
+    Counters cnt;
+    const uint64_t tid = uint64_t(blockIdx.x) * kBlock + threadIdx.x;
+    for (uint64_t t = tid; tid < T && t < count; t += T) {
+        const uint64_t u = u0 + t;
+        const int32_t i = independent_pick(a.seed, int64_t(u), 0u, a.n);
+        const Col<XT> c = load_col(a.desc, i);
+        const double xi = ld_volatile_f64(a.x + i);
+        XT acc = XT(0);
+        for (int cs = 0; cs < c.cnt; cs += kE) {
+            Chunk<kE, XT> ch;
+            ld_chunk<kE>(ch, a.prow, a.pval, c.pbeg + cs);
+            acc += chunk_dot<kE, XT, XT, XT>(ch, a.g, c.cnt - cs);
+        }
+        const double xn = prox_step(xi, double(acc), double(c.invL), a.inv_beta, a.lambda);
+        const double h64 = xn - xi;
+        cnt.gathered += (unsigned long long)c.cnt;
+        if (h64 != 0.0) {
+            atomicAdd(a.x + i, h64);
+            const XT h = XT(h64);
+            for (int cs = 0; cs < c.cnt; cs += kE) {
+                Chunk<kE, XT> ch;
+                ld_chunk<kE>(ch, a.prow, a.pval, c.pbeg + cs);
+                chunk_scatter<kE>(ch, a.g, h, c.cnt - cs);
+            }
+            cnt.nonzero += 1;
+            cnt.scattered += (unsigned long long)c.cnt;
+        }
+    }
+    flush_counters(cnt, a.counters);
+}
+
+// ---------------------------------------------------------------------------
 // Set-up on the caller's layout: one thread per column (runs once per matrix).
 template <typename VT>
 __device__ __forceinline__ double ld_orig(const VT *p);
@@ -1015,6 +1059,25 @@ cudaError_t Kernels<VT, XT>::build_layout(const int64_t *col_ptr, const int32_t 
     k_build_layout<VT, XT><<<blocks_for_threads(n, 152 * 64), kBlock, 0, st>>>(col_ptr, row_idx, val, pbeg, L, n,
                                                                                 desc, prow, pval);
     return cudaGetLastError();
+}
+
+template <typename VT, typename XT>
+cudaError_t Kernels<VT, XT>::async(const IterArgs<VT, XT> &a, int blocks, uint64_t nthreads, uint64_t u0,
+                                   uint64_t count, cudaStream_t st)
+{
+    k_async<VT, XT><<<dim3(unsigned(blocks)), kBlock, 0, st>>>(a, u0, count, nthreads);
+    return cudaGetLastError();
+}
+
+template <typename VT, typename XT>
+int Kernels<VT, XT>::async_max_blocks()
+{
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_async<VT, XT>, kBlock, 0) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
 }
 
 template <typename VT, typename XT>

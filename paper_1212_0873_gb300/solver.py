@@ -124,6 +124,14 @@ class Lasso:
         p, d = _ptr_and_device(x)
         B.pcdm_set_x(self._h, p, d)
 
+    def step_async(self, updates, seed=0, threads=0):
+        """Asynchronous updates (pcdm_step_async); threads = 1 is the serial method."""
+        B.pcdm_step_async(self._h, updates, seed, threads)
+
+    def solve_async(self, seed=0, tol=1e-6, max_updates=10**12, threads=0):
+        """Returns (converged, updates, relative gap)."""
+        return B.pcdm_solve_async(self._h, seed, tol, max_updates, threads)
+
     def set_b(self, b):
         """New right-hand side (m entries, numpy or CUDA tensor); x is kept."""
         if not _is_tensor(b):
