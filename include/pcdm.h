@@ -434,6 +434,48 @@ void pcdm_batch_destroy(pcdm_batch_handle h);
  * on this thread. */
 const char *pcdm_batch_last_error(pcdm_batch_handle h);
 
+/* ------------------------------------------------------------------------
+ * Many independent problems: count LASSO problems, each with its own A_p, b_p
+ * and lambda_p, all of the same dtype pair.  One thread block runs Algorithm 1
+ * (tau-nice sampling with tau_p = min(tau, n_p), beta of Theorem ESO-nice for
+ * (omega_p, tau_p, n_p)) for one problem with block barriers only, so small
+ * problems of uneven size run side by side.  A check period (copy of the
+ * active flags, iters_per_check iterations, FP64 refresh and duality gap of
+ * every running problem, copy of the gap records) is captured once as a CUDA
+ * graph and replayed; a problem stops at its first check with
+ * gap / primal <= rel_gap_tol.  Meant for problems that fit one block's reach
+ * (n up to about 1e5); each problem p follows a single-problem handle stepped
+ * with the same seed and tau_p (with an FP64 refresh at every check).
+ * ------------------------------------------------------------------------ */
+typedef struct pcdm_multi_ctx *pcdm_multi_handle;
+
+/* As[p], bs[p] (m_p entries of b_dtype), lambdas[p] for p < count (1 .. 65535),
+ * host or device as As[p].on_device says; validated and copied as by
+ * pcdm_create (opts likewise; sampling must be NICE).  The solves run on an
+ * internal stream; cuda_stream is used for the copies of the set-up only. */
+pcdm_status pcdm_multi_create(int64_t count, const pcdm_csc *As, const void *const *bs, int32_t b_dtype,
+                              const double *lambdas, const pcdm_opts *opts, void *cuda_stream,
+                              pcdm_multi_handle *out);
+
+/* Iterate every problem from its current x until its relative gap is at most
+ * rel_gap_tol (checks every iters_per_check iterations; 1 <= tau <= 256).
+ * iters_done, rel_gaps: count entries each (may be NULL).  PCDM_ENOTCONV when a
+ * problem ran max_iters iterations first. */
+pcdm_status pcdm_multi_solve(pcdm_multi_handle h, int64_t tau, uint64_t seed, double rel_gap_tol,
+                             int64_t max_iters, int64_t iters_per_check, int64_t *iters_done, double *rel_gaps);
+
+/* x of problem p (n_p doubles, host memory). */
+pcdm_status pcdm_multi_get_x(pcdm_multi_handle h, int64_t p, double *x_out);
+
+/* x = 0 and g = -b for every problem, iteration counters to 0. */
+pcdm_status pcdm_multi_reset(pcdm_multi_handle h);
+
+/* Counters (updates = sum over problems of tau_p per iteration run). */
+pcdm_status pcdm_multi_get_stats(pcdm_multi_handle h, pcdm_stats *out);
+
+void pcdm_multi_destroy(pcdm_multi_handle h);
+const char *pcdm_multi_last_error(pcdm_multi_handle h);
+
 /* Free everything the handle owns.  NULL is ignored. */
 void pcdm_destroy(pcdm_handle h);
 

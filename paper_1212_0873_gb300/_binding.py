@@ -68,6 +68,13 @@ SIGNATURES = {
     "pcdm_sample_kind": (_i32, [_i32, _u64, _i64, _i64, _i64, _dbl, _ptr, _ptr, _ptr]),
     "pcdm_step_async": (_i32, [_ptr, _i64, _u64, _i32]),
     "pcdm_solve_async": (_i32, [_ptr, _u64, _dbl, _i64, _i32, _ptr, _ptr]),
+    "pcdm_multi_create": (_i32, [_i64, _ptr, _ptr, _i32, _ptr, ctypes.POINTER(pcdm_opts), _ptr, _ptr]),
+    "pcdm_multi_solve": (_i32, [_ptr, _i64, _u64, _dbl, _i64, _i64, _ptr, _ptr]),
+    "pcdm_multi_get_x": (_i32, [_ptr, _i64, _ptr]),
+    "pcdm_multi_reset": (_i32, [_ptr]),
+    "pcdm_multi_get_stats": (_i32, [_ptr, ctypes.POINTER(pcdm_stats)]),
+    "pcdm_multi_destroy": (None, [_ptr]),
+    "pcdm_multi_last_error": (ctypes.c_char_p, [_ptr]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -395,3 +402,53 @@ def pcdm_solve_async(h, seed, rel_gap_tol, max_updates, threads=0):
         return False, u.value, rel.value
     _check(st, h)
     return True, u.value, rel.value
+
+
+# ---------------------------------------------------------------------------- many problems
+def _mcheck(status, handle=None):
+    if status != PCDM_OK:
+        msg = lib().pcdm_multi_last_error(handle)
+        raise PcdmError(status, (msg or b"").decode(errors="replace"))
+
+
+def pcdm_multi_create(cscs, b_ptrs, b_dtype, lambdas, opts=None, stream=0):
+    count = len(cscs)
+    arr = (pcdm_csc * count)(*cscs)
+    bp = (ctypes.c_void_p * count)(*[int(p) for p in b_ptrs])
+    lam = (ctypes.c_double * count)(*[float(v) for v in lambdas])
+    h = _ptr()
+    st = lib().pcdm_multi_create(count, ctypes.cast(arr, _ptr), ctypes.cast(bp, _ptr), int(b_dtype),
+                                 ctypes.cast(lam, _ptr), ctypes.byref(opts) if opts is not None else None,
+                                 _stream(stream), ctypes.byref(h))
+    _mcheck(st, None)
+    return h
+
+
+def pcdm_multi_solve(h, count, tau, seed, tol, max_iters, iters_per_check):
+    """Returns (all converged, [iterations], [relative gap])."""
+    it = (ctypes.c_int64 * count)()
+    rel = (ctypes.c_double * count)()
+    st = lib().pcdm_multi_solve(h, int(tau), int(seed) & (2**64 - 1), float(tol), int(max_iters),
+                                int(iters_per_check), ctypes.cast(it, _ptr), ctypes.cast(rel, _ptr))
+    if st == PCDM_ENOTCONV:
+        return False, list(it), list(rel)
+    _mcheck(st, h)
+    return True, list(it), list(rel)
+
+
+def pcdm_multi_get_x(h, p, ptr):
+    _mcheck(lib().pcdm_multi_get_x(h, int(p), _ptr(ptr)), h)
+
+
+def pcdm_multi_reset(h):
+    _mcheck(lib().pcdm_multi_reset(h), h)
+
+
+def pcdm_multi_get_stats(h):
+    s = pcdm_stats()
+    _mcheck(lib().pcdm_multi_get_stats(h, ctypes.byref(s)), h)
+    return {name: getattr(s, name) for name, _ in pcdm_stats._fields_}
+
+
+def pcdm_multi_destroy(h):
+    lib().pcdm_multi_destroy(h)

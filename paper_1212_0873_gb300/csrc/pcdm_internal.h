@@ -172,6 +172,30 @@ cudaError_t launch_deinterleave(const double *src, int64_t len, int nout, int bp
 cudaError_t launch_batch_gap_finish(const double *pc, int nbc, const double *pr, int nbr, int bp,
                                     const double *lambda, double *out, cudaStream_t st);
 
+// Many independent problems, one thread block each (multi_kernels.cuh).
+constexpr int kMultiBlock = 256;   // threads per problem; tau <= kMultiBlock
+template <typename VT, typename XT>
+struct MultiInst {
+    const ColDesc<XT> *desc;
+    const int32_t *prow;
+    const VT *pval;
+    double *x;
+    XT *g;
+    double *g64;                // FP64 refresh target (aliases g in the FP64 form)
+    const double *b;
+    int64_t m, n, tau;
+    double inv_beta, lambda;
+};
+template <typename VT, typename XT>
+struct MultiKernels {
+    // iters iterations of every active problem p, from its counter kcount[p]
+    static cudaError_t iter(const MultiInst<VT, XT> *inst, const int *active, int64_t *kcount, int count,
+                            int64_t iters, uint64_t seed, unsigned long long *counters, cudaStream_t st);
+    // refresh and gap record (9 doubles) of every active problem
+    static cudaError_t gap(const MultiInst<VT, XT> *inst, const int *active, int count, double *rec,
+                           cudaStream_t st);
+};
+
 // Active-set coordinate descent (active_set_kernels.cuh): FP64 u, q and sums for
 // any stored value type; DT is the handle's iterate dtype (type of 1/L in desc).
 template <typename VT, typename DT>

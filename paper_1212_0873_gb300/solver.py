@@ -313,3 +313,68 @@ class BatchLasso:
             self.close()
         except Exception:
             pass
+
+
+class MultiLasso:
+    """Many independent LASSO problems (each its own A, b, lambda; numpy host
+    arrays), one GPU thread block per problem (pcdm_multi_*)."""
+
+    def __init__(self, problems, *, xg_dtype=None, stream=None):
+        """problems: sequence of (m, n, col_ptr, row_idx, val, b, lam)."""
+        vals = {_val_code(pr[4]) for pr in problems}
+        if len(vals) != 1:
+            raise ValueError("every problem must store its values in the same dtype")
+        val_dtype = vals.pop()
+        if xg_dtype is None:
+            xg_dtype = "f64" if val_dtype == "f64" else "f32"
+        self._keep = []
+        cscs, bps, lams, self.ns = [], [], [], []
+        for m, n, col_ptr, row_idx, val, b, lam in problems:
+            col_ptr = np.ascontiguousarray(col_ptr, dtype=np.int64)
+            row_idx = np.ascontiguousarray(row_idx, dtype=np.int32)
+            val = np.ascontiguousarray(val)
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            self._keep += [col_ptr, row_idx, val, b]
+            cscs.append(B.pcdm_csc(int(m), int(n), int(col_ptr[-1]), col_ptr.ctypes.data, row_idx.ctypes.data,
+                                   val.ctypes.data, B.DTYPE_CODES[val_dtype], 0))
+            bps.append(b.ctypes.data)
+            lams.append(float(lam))
+            self.ns.append(int(n))
+        opts = B.pcdm_default_opts()
+        opts.xg_dtype = B.DTYPE_CODES[xg_dtype]
+        self.count = len(cscs)
+        self.stream = current_stream() if stream is None else stream
+        self._h = B.pcdm_multi_create(cscs, bps, B.PCDM_F64, lams, opts, self.stream)
+        self._keep = None
+
+    def solve(self, tau=256, seed=0, tol=1e-6, max_iters=10**7, iters_per_check=64):
+        ok, it, rel = B.pcdm_multi_solve(self._h, self.count, tau, seed, tol, max_iters, iters_per_check)
+        return ok, np.array(it), np.array(rel)
+
+    def x(self, p):
+        out = np.empty(self.ns[p], dtype=np.float64)
+        B.pcdm_multi_get_x(self._h, p, out.ctypes.data)
+        return out
+
+    def reset(self):
+        B.pcdm_multi_reset(self._h)
+
+    def stats(self):
+        return B.pcdm_multi_get_stats(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            B.pcdm_multi_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
