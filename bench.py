@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--no-grad", action="store_true", help="skip the differentiation measurement")
     p.add_argument("--no-tvr", action="store_true", help="skip the theory-versus-reality experiment")
     p.add_argument("--no-async", action="store_true", help="skip the asynchronous-mode measurement")
+    p.add_argument("--no-multi", action="store_true", help="skip the many-small-problems measurement")
     return p.parse_args()
 
 
@@ -332,6 +333,66 @@ def run_batched_path(a):
     }
 
 
+# ----------------------------------------------------------------------------- many small problems
+def run_multi():
+    """256 independent problems (n log-uniform in [1e3, 1e5], m = 2n, 8 nonzeros
+    per column, bf16 values, fp32 residuals, fp64 refresh + gap every 64
+    iterations, tau = min(256, n)), one thread block each, to relative gap 1e-6;
+    against the plain FP64 form solving them one after another."""
+    import torch
+    from paper_1212_0873_gb300 import Lasso, MultiLasso, instances
+
+    insts = instances.small_instances()
+    tol = 1e-6
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        out = fn()
+        torch.cuda.synchronize()
+        e1.record(torch.cuda.current_stream())
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    with MultiLasso([(i.m, i.n, i.col_ptr, i.row_idx, i.val, i.b, i.lam) for i in insts]) as ml:
+        def once():
+            ml.reset()
+            ok, it, rel = ml.solve(tau=256, seed=0, tol=tol, max_iters=10**7, iters_per_check=64)
+            if not ok:
+                raise RuntimeError("multi-problem solve did not converge")
+            return it
+        once()
+        ml_stats0 = ml.stats()
+        t_multi, iters = timed(once)
+        st = ml.stats()
+    plain = [Lasso(i.m, i.n, i.col_ptr, i.row_idx, i.val64, i.b, i.lam) for i in insts]
+    try:
+        def seq():
+            its = 0
+            for s_, i in zip(plain, insts):
+                s_.reset()
+                ok, it, rel = s_.solve(min(256, i.n), 0, tol, 10**7)
+                if not ok:
+                    raise RuntimeError("plain solve did not converge")
+                its += it
+            return its
+        seq()
+        t_plain, plain_iters = timed(seq)
+    finally:
+        for s_ in plain:
+            s_.close()
+    updates = st["updates"] - ml_stats0["updates"]
+    return {"workload": "256 independent problems, n log-uniform in [1e3, 1e5], m = 2n, 8 nonzeros per column, "
+                        "bf16 values, fp32 residuals, fp64 refresh and gap every 64 iterations, tau = min(256, n), "
+                        "each to rel. duality gap 1e-6",
+            "time_s": t_multi, "problem_updates_per_s": updates / t_multi, "max_iterations": int(iters.max()),
+            "total_n": int(sum(i.n for i in insts)),
+            "plain_f64_time_s": t_plain, "plain_f64_iterations": plain_iters,
+            "plain": "the same problems solved one after another by the plain FP64 form (pcdm_solve, same tau)",
+            "speedup_vs_plain_f64": t_plain / t_multi}
+
+
 # ----------------------------------------------------------------------------- differentiation
 def run_grad():
     """Forward (solve to relative gap 1e-6, then the FP64 polish on the support)
@@ -537,6 +598,9 @@ def run_pcdm(a, rank, local, world):
     batched = None
     if rank == 0 and world == 1 and not a.no_batched:
         batched = run_batched_path(a)
+    multi = None
+    if rank == 0 and world == 1 and not a.no_multi:
+        multi = run_multi()
     grad = None
     if rank == 0 and world == 1 and not a.no_grad:
         grad = run_grad()
@@ -563,6 +627,7 @@ def run_pcdm(a, rank, local, world):
             "clocks": clk,
             "batched": batched,
             "asynchronous": asyn,
+            "many_small_problems": multi,
             "differentiation": grad,
             "theory_vs_reality": tvr,
             "extras": {"nonzero_update_frac": st["nonzero_updates"] / max(st["updates"], 1),

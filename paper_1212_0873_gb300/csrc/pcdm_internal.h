@@ -174,6 +174,7 @@ cudaError_t launch_batch_gap_finish(const double *pc, int nbc, const double *pr,
 
 // Many independent problems, one thread block each (multi_kernels.cuh).
 constexpr int kMultiBlock = 256;   // threads per problem; tau <= kMultiBlock
+constexpr int kMultiSplit = 16;    // blocks per problem in the refresh and gap kernels
 template <typename VT, typename XT>
 struct MultiInst {
     const ColDesc<XT> *desc;
@@ -191,8 +192,8 @@ struct MultiKernels {
     // iters iterations of every active problem p, from its counter kcount[p]
     static cudaError_t iter(const MultiInst<VT, XT> *inst, const int *active, int64_t *kcount, int count,
                             int64_t iters, uint64_t seed, unsigned long long *counters, cudaStream_t st);
-    // refresh and gap record (9 doubles) of every active problem
-    static cudaError_t gap(const MultiInst<VT, XT> *inst, const int *active, int count, double *rec,
+    // refresh and gap record (9 doubles) of every active problem; part: count x kMultiSplit x 5 doubles
+    static cudaError_t gap(const MultiInst<VT, XT> *inst, const int *active, int count, double *part, double *rec,
                            cudaStream_t st);
 };
 

@@ -25,6 +25,7 @@ struct pcdm_multi_ctx {
     int *active = nullptr;             // device flags
     int64_t *kcount = nullptr;         // device iteration counters
     double *rec = nullptr;             // device gap records, count x 9
+    double *part = nullptr;            // device gap partials, count x kMultiSplit x 5
     unsigned long long *counters = nullptr;
     int *h_active = nullptr;           // pinned
     double *h_rec = nullptr;           // pinned
@@ -69,7 +70,7 @@ void mfree_all(pcdm_multi_handle h)
 {
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    void *ptrs[] = {h->inst, h->active, h->kcount, h->rec, h->counters};
+    void *ptrs[] = {h->inst, h->active, h->kcount, h->rec, h->part, h->counters};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_active) cudaFreeHost(h->h_active);
@@ -132,7 +133,7 @@ pcdm_status build_graph(pcdm_multi_handle h, int64_t iters, uint64_t seed)
                                     h->stream);
     if (e == cudaSuccess)
         e = MultiKernels<VT, XT>::iter(inst, h->active, h->kcount, h->count, iters, seed, h->counters, h->stream);
-    if (e == cudaSuccess) e = MultiKernels<VT, XT>::gap(inst, h->active, h->count, h->rec, h->stream);
+    if (e == cudaSuccess) e = MultiKernels<VT, XT>::gap(inst, h->active, h->count, h->part, h->rec, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->h_rec, h->rec, sizeof(double) * 9 * size_t(h->count), cudaMemcpyDeviceToHost,
                             h->stream);
@@ -170,7 +171,7 @@ pcdm_status multi_solve_t(pcdm_multi_handle h, int64_t tau, uint64_t seed, doubl
     for (int p = 0; p < h->count; ++p) h->h_active[p] = 1;
     MCK(h, cudaMemcpyAsync(h->active, h->h_active, sizeof(int) * size_t(h->count), cudaMemcpyHostToDevice,
                            h->stream));
-    MCK(h, MultiKernels<VT, XT>::gap(inst, h->active, h->count, h->rec, h->stream));
+    MCK(h, MultiKernels<VT, XT>::gap(inst, h->active, h->count, h->part, h->rec, h->stream));
     MCK(h, cudaMemcpyAsync(h->h_rec, h->rec, sizeof(double) * 9 * size_t(h->count), cudaMemcpyDeviceToHost,
                            h->stream));
     MCK(h, cudaStreamSynchronize(h->stream));
@@ -265,6 +266,7 @@ pcdm_status pcdm_multi_create(int64_t count, const pcdm_csc *As, const void *con
     MCKC(dalloc(&h->active, count));
     MCKC(dalloc(&h->kcount, count));
     MCKC(dalloc(&h->rec, 9 * count));
+    MCKC(dalloc(&h->part, int64_t(kMultiSplit) * 5 * count));
     MCKC(dalloc(&h->counters, 3));
     MCKC(cudaMallocHost(reinterpret_cast<void **>(&h->h_active), sizeof(int) * size_t(count)));
     MCKC(cudaMallocHost(reinterpret_cast<void **>(&h->h_rec), sizeof(double) * 9 * size_t(count)));
@@ -329,7 +331,7 @@ pcdm_status pcdm_multi_get_stats(pcdm_multi_handle h, pcdm_stats *out)
     out->gaps = h->st_gaps;
     out->val_bytes = dtype_bytes(h->val_dtype);
     out->xg_bytes = dtype_bytes(h->xg_dtype);
-    out->kernel_launches = 2 * h->st_launches;
+    out->kernel_launches = 5 * h->st_launches;
     return PCDM_OK;
 }
 

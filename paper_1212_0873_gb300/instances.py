@@ -252,3 +252,13 @@ def equal_rows_instance(m=3000, n=1000, omega=5, seed=1006):
     meta = dict(kind="equal_rows", omega=omega, seed=seed)
     return Instance(m=m, n=n, col_ptr=col_ptr, row_idx=row_idx, val=val, val_dtype="f64", val64=val.copy(),
                     b=b, lam=0.0, x_star=np.zeros(n), meta=meta)
+
+
+def small_instances(count=256, lo=1_000, hi=100_000, per_col=8, val_dtype="bf16", seed=1007):
+    """The batch of independent small problems: n log-uniform in [lo, hi], m = 2n,
+    `per_col` N(0,1) nonzeros per column, x* 1% dense, noise variance 1e-4,
+    lambda = 0.1 ||A^T b||_inf (one per_col_instance per problem)."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
+    return [per_col_instance(2 * int(n), int(n), per_col, density=0.01, noise=0.01, lam_frac=0.1,
+                             val_dtype=val_dtype, seed=seed + 1 + q) for q, n in enumerate(ns)]
