@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-tvr", action="store_true", help="skip the theory-versus-reality experiment")
     p.add_argument("--no-async", action="store_true", help="skip the asynchronous-mode measurement")
     p.add_argument("--no-multi", action="store_true", help="skip the many-small-problems measurement")
+    p.add_argument("--no-tune", action="store_true", help="keep the built-in kernel choice (no pcdm_autotune)")
     return p.parse_args()
 
 
@@ -499,6 +500,7 @@ def run_pcdm(a, rank, local, world):
     seed = rank
     solver = Lasso.from_instance(inst, profile=True, **kw)
     omega = solver.omega
+    tuning = solver.autotune(a.tau, 30) if (not a.unfused and not a.no_tune) else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
     def one_solve():
@@ -549,7 +551,10 @@ def run_pcdm(a, rank, local, world):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (tpu * st["updates"] / launches) if tpu is not None else None,
-                "kernel": ("k_gather + k_scatter (two-kernel PCDM1 iterations)" if a.unfused else
+                "kernel": ("k_gather + k_scatter (two-kernel PCDM1 iterations)" if a.unfused or
+                           (tuning and tuning["kernel"] == 2) else
+                           "k_fused (persistent PCDM1 iterations, %d lanes per column)" % tuning["lanes_per_col"]
+                           if tuning and tuning["kernel"] == 1 else
                            "k_fused_pipe (persistent PCDM1 iterations)"), "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes / launches, "avg_launch_ms": avg_launch_s * 1e3,
                 "launches": st["iter_launches"]}
@@ -620,6 +625,7 @@ def run_pcdm(a, rank, local, world):
                        "l2": "256 MB buffer written between timed steps (outside the events); A is %.2f GB"
                              % ((inst.col_ptr.nbytes + inst.row_idx.nbytes + inst.val.nbytes) / 1e9)},
             "time_to_gap_s": max_seconds / a.steps,
+            "tuning": tuning,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -185,6 +185,27 @@ pcdm_status pcdm_step_async(pcdm_handle h, int64_t updates, uint64_t seed, int32
 pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, int64_t max_updates,
                              int32_t threads, int64_t *updates_done, double *rel_gap);
 
+/*
+ * Autotuner: choose the iteration kernel for tau by timing trial_iters
+ * iterations of each candidate on this handle's matrix, from its current
+ * state (which is restored afterwards; the counters of pcdm_get_stats are not
+ * changed).  Candidates: the pipelined one-lane-per-column kernel with blocks
+ * of 128 .. 448 threads (the tau positions per block), the fused kernel with
+ * 1 .. 32 lanes per column (its scatter reloads the column), and the two-kernel
+ * form with 1, 4 or 16 lanes.  The fastest is kept for later pcdm_step /
+ * pcdm_solve calls (for any tau; tune again for a very different one).
+ * Needs the tau-nice sampling and opts.fused = 1.
+ */
+typedef struct {
+    int32_t kernel;             /* 0 pipelined, 1 fused with lanes_per_col lanes, 2 two-kernel form */
+    int32_t lanes_per_col;
+    int32_t threads_per_block;  /* pipelined kernel only */
+    int32_t reserved;
+    double us_per_iteration;    /* measured */
+} pcdm_tuning;
+
+pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_tuning *best);
+
 /* Recompute g = A x - b in FP64 (stored in g's dtype). */
 pcdm_status pcdm_refresh(pcdm_handle h);
 

@@ -23,6 +23,11 @@ class pcdm_csc(ctypes.Structure):
                 ("val_dtype", _i32), ("on_device", _i32)]
 
 
+class pcdm_tuning(ctypes.Structure):
+    _fields_ = [("kernel", _i32), ("lanes_per_col", _i32), ("threads_per_block", _i32), ("reserved", _i32),
+                ("us_per_iteration", _dbl)]
+
+
 class pcdm_opts(ctypes.Structure):
     _fields_ = [("xg_dtype", _i32), ("fused", _i32), ("refresh_every", _i64), ("check_every", _i64),
                 ("lanes_per_col", _i64), ("barrier_timeout_ns", _u64), ("profile", _i32), ("sampling", _i32),
@@ -75,6 +80,7 @@ SIGNATURES = {
     "pcdm_multi_get_stats": (_i32, [_ptr, ctypes.POINTER(pcdm_stats)]),
     "pcdm_multi_destroy": (None, [_ptr]),
     "pcdm_multi_last_error": (ctypes.c_char_p, [_ptr]),
+    "pcdm_autotune": (_i32, [_ptr, _i64, _i64, ctypes.POINTER(pcdm_tuning)]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -452,3 +458,9 @@ def pcdm_multi_get_stats(h):
 
 def pcdm_multi_destroy(h):
     lib().pcdm_multi_destroy(h)
+
+
+def pcdm_autotune(h, tau, trial_iters):
+    t = pcdm_tuning()
+    _check(lib().pcdm_autotune(h, int(tau), int(trial_iters), ctypes.byref(t)), h)
+    return {name: getattr(t, name) for name, _ in pcdm_tuning._fields_ if name != "reserved"}

@@ -106,20 +106,20 @@ IterArgs<VT, XT> iter_args(pcdm_handle h, int64_t tau, uint64_t seed)
 // column when the grid can hold them (spread over all SMs, one block each),
 // otherwise full blocks at the co-residency limit.
 template <typename VT, typename XT>
-pcdm_status fused_shape(pcdm_handle h, int64_t tau, FusedShape *sh)
+pcdm_status fused_shape(pcdm_handle h, int64_t tau, int W, FusedShape *sh)
 {
-    sh->W = h->W;
-    const int64_t need = tau * h->W;
+    sh->W = W;
+    const int64_t need = tau * W;
     int64_t blocks = (need + 63) / 64;
     if (blocks > h->sms) blocks = h->sms;
     if (blocks < 1) blocks = 1;
     int64_t threads = (need + blocks - 1) / blocks;
     threads = (threads + 31) / 32 * 32;
-    if (threads > fused_max_block(h->W)) {
-        threads = fused_max_block(h->W);
+    if (threads > fused_max_block(W)) {
+        threads = fused_max_block(W);
         blocks = (need + threads - 1) / threads;
     }
-    const int cap = Kernels<VT, XT>::fused_max_blocks(h->W, int(threads));
+    const int cap = Kernels<VT, XT>::fused_max_blocks(W, int(threads));
     if (cap <= 0) return set_err(h, PCDM_ECUDA, "cooperative occupancy query failed");
     if (blocks > cap) blocks = cap;
     sh->blocks = int(blocks);
@@ -130,10 +130,10 @@ pcdm_status fused_shape(pcdm_handle h, int64_t tau, FusedShape *sh)
 // Shape of the pipelined kernel for tau, if it applies: one lane per column,
 // every position owned by one thread of a co-resident grid.
 template <typename VT, typename XT>
-bool pipe_shape(pcdm_handle h, int64_t tau, FusedShape *sh)
+bool pipe_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads = 0)
 {
-    if (h->W != 1) return false;
-    int64_t threads = (tau + h->sms - 1) / h->sms;
+    if (h->W != 1 && want_threads == 0) return false;
+    int64_t threads = want_threads > 0 ? want_threads : (tau + h->sms - 1) / h->sms;
     threads = (threads + 31) / 32 * 32;
     if (threads < 32) threads = 32;
     if (threads > kPipeMaxBlock) return false;
@@ -179,10 +179,12 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         h->g2_valid = false;
         h->st_launches += iters;
         h->st_kernels += 3 * iters;
-    } else if (h->opts.fused) {
+    } else if (h->opts.fused && h->tune_kernel != 2) {
         FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
-        if (pipe_shape<VT, XT>(h, tau, &sh)) {
+        const bool pipe = h->tune_kernel == 1 ? false
+                                              : pipe_shape<VT, XT>(h, tau, &sh, h->tune_kernel == 0 ? h->tune_threads : 0);
+        if (pipe) {
             const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
             if (!h->g2) {
                 CK(h, cudaStreamSynchronize(h->stream));
@@ -194,7 +196,7 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
             CK(h, Kernels<VT, XT>::fused_pipe(a, sh, h->k, iters, h->stream));
             h->g2_valid = true;
         } else {
-            pcdm_status s = fused_shape<VT, XT>(h, tau, &sh);
+            pcdm_status s = fused_shape<VT, XT>(h, tau, h->tune_kernel == 1 ? h->tune_W : h->W, &sh);
             if (s != PCDM_OK) return s;
             CK(h, Kernels<VT, XT>::fused(a, sh, h->k, iters, h->stream));
             h->g2_valid = false;
@@ -202,10 +204,11 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         h->st_launches += 1;
         h->st_kernels += 1;
     } else {
+        const int W2 = h->tune_kernel == 2 && h->tune_W > 0 ? h->tune_W : h->W;
         for (int64_t it = 0; it < iters; ++it) {
             const int64_t kk = h->k + it;
-            CK(h, Kernels<VT, XT>::gather(a, h->W, kk, h->stream));
-            CK(h, Kernels<VT, XT>::scatter(a, h->W, kk, true, h->stream));
+            CK(h, Kernels<VT, XT>::gather(a, W2, kk, h->stream));
+            CK(h, Kernels<VT, XT>::scatter(a, W2, kk, true, h->stream));
         }
         h->g2_valid = false;
         h->st_launches += iters;
@@ -1162,6 +1165,122 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
     if (updates_done) *updates_done = done;
     if (rel_gap) *rel_gap = rel;
     if (rel > rel_gap_tol) return set_err(h, PCDM_ENOTCONV, "max_updates reached before the gap tolerance");
+    return PCDM_OK;
+}
+
+pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_tuning *best)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (tau < 1 || tau > h->n || trial_iters < 1) return set_err(h, PCDM_EINVAL, "bad tau or trial_iters");
+    if (h->opts.sampling != PCDM_SAMPLING_NICE || !h->opts.fused)
+        return set_err(h, PCDM_EINVAL, "autotuning applies to the fused tau-nice iteration kernels");
+    s = ensure_tau(h, tau);
+    if (s != PCDM_OK) return s;
+    // the state the trials start from, restored after each one and at the end
+    const size_t xbytes = sizeof(double) * size_t(h->n), gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
+    double *x0 = nullptr;
+    void *g0 = nullptr;
+    CK(h, dalloc(&x0, h->n));
+    cudaError_t e = dalloc_bytes(&g0, int64_t(gbytes));
+    if (e != cudaSuccess) {
+        cudaFree(x0);
+        return cuda_fail(h, e, "autotune state copy");
+    }
+    const int64_t k0 = h->k;
+    const int64_t st_it = h->st_iterations, st_up = h->st_updates, st_la = h->st_launches, st_ke = h->st_kernels;
+    const double st_ms = h->st_kernel_ms;
+    const int keep[3] = {h->tune_kernel, h->tune_W, h->tune_threads};
+    auto restore = [&]() -> pcdm_status {
+        CK(h, cudaMemcpyAsync(h->x, x0, xbytes, cudaMemcpyDeviceToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->g, g0, gbytes, cudaMemcpyDeviceToDevice, h->stream));
+        h->k = k0;
+        h->g2_valid = false;
+        h->sample_valid = false;
+        return PCDM_OK;
+    };
+    CK(h, cudaMemcpyAsync(x0, h->x, xbytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(g0, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
+    struct Cand {
+        int kernel, W, threads;
+    };
+    std::vector<Cand> cands;
+    for (int t : {128, 192, 256, 320, 384, 448}) cands.push_back({0, 1, t});
+    for (int W : {1, 2, 4, 8, 16, 32}) cands.push_back({1, W, 0});
+    for (int W : {1, 4, 16}) cands.push_back({2, W, 0});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    Cand bestc{-1, 0, 0};
+    double best_us = 0.0;
+    pcdm_status rs = PCDM_OK;
+    for (const Cand &c : cands) {
+        if (c.kernel == 0) {
+            // the pipelined kernel must hold tau positions at this block size
+            FusedShape sh;
+            bool ok = false;
+            dispatch(h, [&](auto *vt, auto *xt) {
+                using VT = std::remove_pointer_t<decltype(vt)>;
+                using XT = std::remove_pointer_t<decltype(xt)>;
+                const int save_W = h->W;
+                h->W = 1;
+                ok = pipe_shape<VT, XT>(h, tau, &sh, c.threads);
+                h->W = save_W;
+                return PCDM_OK;
+            });
+            if (!ok) continue;
+        }
+        h->tune_kernel = c.kernel;
+        h->tune_W = c.W;
+        h->tune_threads = c.threads;
+        if ((rs = restore()) != PCDM_OK) break;
+        if ((rs = pcdm_step(h, tau, 2, 0x5eedULL)) != PCDM_OK) break;   // warm-up (first launch of a shape)
+        if ((rs = restore()) != PCDM_OK) break;
+        if ((e = cudaEventRecord(e0, h->stream)) != cudaSuccess) break;
+        if ((rs = pcdm_step(h, tau, trial_iters, 0x5eedULL)) != PCDM_OK) break;
+        if ((e = cudaEventRecord(e1, h->stream)) != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+        const double us = 1e3 * double(ms) / double(trial_iters);
+        if (bestc.kernel < 0 || us < best_us) {
+            bestc = c;
+            best_us = us;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs == PCDM_OK && e == cudaSuccess) rs = restore();
+    if (rs == PCDM_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(x0);
+    cudaFree(g0);
+    h->st_iterations = st_it;
+    h->st_updates = st_up;
+    h->st_launches = st_la;
+    h->st_kernels = st_ke;
+    h->st_kernel_ms = st_ms;
+    for (auto &pr : h->ev_pending) {   // timings of the trials are not kept
+        h->ev_free.push_back(pr.first);
+        h->ev_free.push_back(pr.second);
+    }
+    h->ev_pending.clear();
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotune");
+    if (rs != PCDM_OK) {
+        h->tune_kernel = keep[0];
+        h->tune_W = keep[1];
+        h->tune_threads = keep[2];
+        return rs;
+    }
+    h->tune_kernel = bestc.kernel;
+    h->tune_W = bestc.W;
+    h->tune_threads = bestc.threads;
+    if (best) {
+        best->kernel = bestc.kernel;
+        best->lanes_per_col = bestc.W;
+        best->threads_per_block = bestc.threads;
+        best->reserved = 0;
+        best->us_per_iteration = best_us;
+    }
     return PCDM_OK;
 }
 

@@ -124,6 +124,10 @@ class Lasso:
         p, d = _ptr_and_device(x)
         B.pcdm_set_x(self._h, p, d)
 
+    def autotune(self, tau, trial_iters=50):
+        """Pick the fastest iteration kernel for tau on this matrix (pcdm_autotune)."""
+        return B.pcdm_autotune(self._h, tau, trial_iters)
+
     def step_async(self, updates, seed=0, threads=0):
         """Asynchronous updates (pcdm_step_async); threads = 1 is the serial method."""
         B.pcdm_step_async(self._h, updates, seed, threads)
