@@ -66,6 +66,7 @@ def parse():
     p.add_argument("--no-async", action="store_true", help="skip the asynchronous-mode measurement")
     p.add_argument("--no-multi", action="store_true", help="skip the many-small-problems measurement")
     p.add_argument("--no-tune", action="store_true", help="keep the built-in kernel choice (no pcdm_autotune)")
+    p.add_argument("--sweep", action="store_true", help="print the omega x tau x dtype table of the scale workload")
     return p.parse_args()
 
 
@@ -647,8 +648,51 @@ def run_pcdm(a, rank, local, world):
     return 0
 
 
+def run_sweep(a):
+    """The scale configurations (m = n = 4e6, omega in {2, 16, 128}, tau in {1,
+    256, 4096, 65536}, FP64 and FP32): time to relative gap 1e-6 where it takes
+    less than about a minute (tau >= 256), updates/s otherwise; one JSON line per
+    point.  Not part of the default run."""
+    import torch
+    from paper_1212_0873_gb300 import Lasso, instances
+    torch.cuda.set_device(0)
+    for omega in (2, 16, 128):
+        for dtype in ("f64", "f32"):
+            inst = instances.row_omega_instance(a.n, a.n, omega, density=0.01, noise=0.01, lam_frac=0.05,
+                                                val_dtype=dtype, seed=1002)
+            for tau in (1, 256, 4096, 65536):
+                with Lasso.from_instance(inst, profile=True, refresh_every=0 if dtype == "f64" else 64) as s:
+                    tuning = s.autotune(tau, 20)
+                    rec = {"omega": omega, "dtype": dtype, "tau": tau, "tuning": tuning, "beta": s.beta(tau)}
+                    if tau == 1:
+                        s.step(tau, 2000, 0)
+                        s.reset_stats()
+                        s.step(tau, 20000, 0)
+                        st = s.stats()
+                        rec["updates_per_s"] = st["updates"] / (st["iter_kernel_ms"] / 1e3)
+                        rec["us_per_iteration"] = 1e3 * st["iter_kernel_ms"] / st["iterations"]
+                    else:
+                        s.reset()
+                        torch.cuda.synchronize()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        ok, it, rel = s.solve(tau, 0, a.tol, 10**7)
+                        e1.record()
+                        e1.synchronize()
+                        t = e0.elapsed_time(e1) / 1e3
+                        st = s.stats()
+                        rec.update({"converged": ok, "iterations": it, "rel_gap": rel, "time_to_gap_s": t,
+                                    "updates_per_s": it * tau / t,
+                                    "us_per_iteration": 1e3 * st["iter_kernel_ms"] / max(st["iterations"], 1)})
+                    print(json.dumps(rec), flush=True)
+            del inst
+    return 0
+
+
 def main():
     a = parse()
+    if a.sweep:
+        return run_sweep(a)
     rank, local, world = dist_setup()
     if a.impl == "reference":
         rc = run_reference(a, rank, world)
