@@ -51,8 +51,28 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+GEN_SRC = os.path.join(HERE, "gen", "gen_kernels.cu")
+GEN_LIB = os.path.join(LIBDIR, "libpcdm_gen.so")
+
+
+def build_gen(force=False):
+    """The device instance generator (include/pcdm_gen.h), a library of its own."""
+    deps = [GEN_SRC, os.path.join(INCLUDE, "pcdm_gen.h"), os.path.abspath(__file__)]
+    if not force and not _stale(GEN_LIB, deps):
+        return GEN_LIB
+    os.makedirs(LIBDIR, exist_ok=True)
+    tmp = GEN_LIB + ".tmp%d" % os.getpid()
+    cmd = [nvcc(), *ARCH, *FLAGS, "-shared", "-cudart", "static", GEN_SRC, "-o", tmp]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (GEN_SRC, " ".join(cmd), res.stderr))
+    os.replace(tmp, GEN_LIB)
+    return GEN_LIB
+
+
 def build(force=False, verbose=False, extra_flags=()):
-    """Compile (when stale) and return the path of libpcdm.so."""
+    """Compile (when stale) and return the path of libpcdm.so (and build libpcdm_gen.so)."""
+    build_gen(force)
     deps = _deps()
     if not force and not _stale(LIB, deps):
         return LIB

@@ -209,3 +209,13 @@ def test_batch_create_host_checks(B):
     assert L.pcdm_batch_step(None, 1, 1, 0) == B.PCDM_EINVAL
     assert L.pcdm_batch_gap(None, None, None, None) == B.PCDM_EINVAL
     L.pcdm_batch_destroy(None)
+
+
+def test_generator_library_exports_its_header():
+    from paper_1212_0873_gb300 import build
+    build.build_gen()
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "pcdm_gen.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(pcdm_[A-Za-z_0-9]+)\s*\(", text)))
+    assert names == ["pcdm_gen_per_col"]
+    lib = ctypes.CDLL(build.GEN_LIB)
+    assert all(hasattr(lib, n) for n in names)
