@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--no-multi", action="store_true", help="skip the many-small-problems measurement")
     p.add_argument("--no-tune", action="store_true", help="keep the built-in kernel choice (no pcdm_autotune)")
     p.add_argument("--sweep", action="store_true", help="print the omega x tau x dtype table of the scale workload")
+    p.add_argument("--huge", action="store_true", help="time the 4e9-nonzero configuration (about 140 GB of HBM)")
     return p.parse_args()
 
 
@@ -648,6 +649,54 @@ def run_pcdm(a, rank, local, world):
     return 0
 
 
+def run_huge(a):
+    """The huge mixed-precision configuration: A 1e9 x 5e8 with 8 BF16 nonzeros
+    per column (4e9 nonzeros, generated on the device by libpcdm_gen), b FP32,
+    x* 1e-4 dense, lambda = 0.1 ||A^T b||_inf, tau = 2^20, FP32 residuals with an
+    FP64 refresh every 32 iterations, solved from x = 0 to relative gap 1e-5.
+    One JSON line.  Not part of the default run (about 140 GB of HBM)."""
+    import time
+    import torch
+    from paper_1212_0873_gb300 import Lasso, device_instances
+    torch.cuda.set_device(0)
+    m, n, per_col, tau, tol = 1_000_000_000, 500_000_000, 8, 1 << 20, 1e-5
+    t0 = time.perf_counter()
+    gen = device_instances.per_col_on_device(m, n, per_col, seed=1008, val_dtype="bf16", x_density=1e-4,
+                                             noise_sd=1e-2, b_dtype="f32")
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    lam = 0.1 * gen["lambda_max"]
+    t0 = time.perf_counter()
+    s = Lasso(m, n, gen["col_ptr"], gen["row_idx"], gen["val"], gen["b"], lam, refresh_every=32, profile=True)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    del gen
+    torch.cuda.empty_cache()
+    tuning = s.autotune(tau, 10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.reset_stats()
+    e0.record()
+    ok, it, rel = s.solve(tau, 0, tol, 10**6)
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    st = s.stats()
+    sv, sg, sx = st["val_bytes"], st["xg_bytes"], 8
+    alg = (st["gathered_nnz"] * (sv + 4 + sg) + st["updates"] * (2 * sx + sg + 8)
+           + st["scattered_nnz"] * (sv + 4 + 2 * sg))
+    peak, kind = measured_peaks()
+    ach = alg / (st["iter_kernel_ms"] / 1e3) / 1e9
+    s.close()
+    print(json.dumps({"workload": "huge: A 1e9 x 5e8, 8 bf16 nonzeros per column (4e9 nonzeros), b fp32, tau = 2^20, "
+                                  "fp32 residuals, fp64 refresh every 32, from x = 0 to rel. gap 1e-5",
+                      "converged": ok, "iterations": it, "rel_gap": rel, "time_to_gap_s": t,
+                      "updates_per_s": it * tau / t, "us_per_iteration": 1e3 * st["iter_kernel_ms"] / it,
+                      "tuning": tuning, "generate_s": t_gen, "create_s": t_create,
+                      "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                   "peak_source": kind}}), flush=True)
+    return 0
+
+
 def run_sweep(a):
     """The scale configurations (m = n = 4e6, omega in {2, 16, 128}, tau in {1,
     256, 4096, 65536}, FP64 and FP32): time to relative gap 1e-6 where it takes
@@ -693,6 +742,8 @@ def main():
     a = parse()
     if a.sweep:
         return run_sweep(a)
+    if a.huge:
+        return run_huge(a)
     rank, local, world = dist_setup()
     if a.impl == "reference":
         rc = run_reference(a, rank, world)
