@@ -190,14 +190,17 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
  * iterations of each candidate on this handle's matrix, from its current
  * state (which is restored afterwards; the counters of pcdm_get_stats are not
  * changed).  Candidates: the pipelined one-lane-per-column kernel with blocks
- * of 128 .. 448 threads (the tau positions per block), the fused kernel with
- * 1 .. 32 lanes per column (its scatter reloads the column), and the two-kernel
- * form with 1, 4 or 16 lanes.  The fastest is kept for later pcdm_step /
+ * of 128 .. 448 threads (the tau positions per block; when tau fits one pass of
+ * the grid), its rounds form with blocks of 128 or 256 threads (several
+ * positions per thread and iteration), the fused kernel with 1 .. 32 lanes per
+ * column (its scatter reloads the column), and the two-kernel form with 1, 4 or
+ * 16 lanes.  The fastest is kept for later pcdm_step /
  * pcdm_solve calls (for any tau; tune again for a very different one).
  * Needs the tau-nice sampling and opts.fused = 1.
  */
 typedef struct {
-    int32_t kernel;             /* 0 pipelined, 1 fused with lanes_per_col lanes, 2 two-kernel form */
+    int32_t kernel;             /* 0 pipelined, 1 fused with lanes_per_col lanes, 2 two-kernel form,
+                                   3 pipelined rounds */
     int32_t lanes_per_col;
     int32_t threads_per_block;  /* pipelined kernel only */
     int32_t reserved;
@@ -205,6 +208,12 @@ typedef struct {
 } pcdm_tuning;
 
 pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_tuning *best);
+
+/* Choose the iteration kernel by hand (the fields of pcdm_tuning; us_per_iteration
+ * is ignored; threads_per_block a multiple of 32, up to 448 for kernel 0 and
+ * 256 for kernel 3), or return to the built-in rule with t = NULL.  A pipelined
+ * kernel that cannot hold tau at that block size falls back to the fused one. */
+pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t);
 
 /* Recompute g = A x - b in FP64 (stored in g's dtype). */
 pcdm_status pcdm_refresh(pcdm_handle h);

@@ -81,6 +81,7 @@ SIGNATURES = {
     "pcdm_multi_destroy": (None, [_ptr]),
     "pcdm_multi_last_error": (ctypes.c_char_p, [_ptr]),
     "pcdm_autotune": (_i32, [_ptr, _i64, _i64, ctypes.POINTER(pcdm_tuning)]),
+    "pcdm_set_tuning": (_i32, [_ptr, ctypes.POINTER(pcdm_tuning)]),
     "pcdm_get_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_set_x": (_i32, [_ptr, _ptr, _i32]),
     "pcdm_get_residual": (_i32, [_ptr, _ptr, _i32]),
@@ -464,3 +465,12 @@ def pcdm_autotune(h, tau, trial_iters):
     t = pcdm_tuning()
     _check(lib().pcdm_autotune(h, int(tau), int(trial_iters), ctypes.byref(t)), h)
     return {name: getattr(t, name) for name, _ in pcdm_tuning._fields_ if name != "reserved"}
+
+
+def pcdm_set_tuning(h, kernel=None, lanes_per_col=1, threads_per_block=0):
+    """kernel None: back to the built-in rule."""
+    if kernel is None:
+        _check(lib().pcdm_set_tuning(h, None), h)
+        return
+    t = pcdm_tuning(int(kernel), int(lanes_per_col), int(threads_per_block), 0, 0.0)
+    _check(lib().pcdm_set_tuning(h, ctypes.byref(t)), h)

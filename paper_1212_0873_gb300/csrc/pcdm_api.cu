@@ -151,6 +151,7 @@ template <typename VT, typename XT>
 pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters)
 {
     IterArgs<VT, XT> a = iter_args<VT, XT>(h, tau, seed);
+    h->rounds_last = false;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->opts.profile) {
         CK(h, take_event(h, &e0));
@@ -182,9 +183,36 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
     } else if (h->opts.fused && h->tune_kernel != 2) {
         FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
-        const bool pipe = h->tune_kernel == 1 ? false
-                                              : pipe_shape<VT, XT>(h, tau, &sh, h->tune_kernel == 0 ? h->tune_threads : 0);
-        if (pipe) {
+        const bool pipe = (h->tune_kernel == 1 || h->tune_kernel == 3)
+                              ? false
+                              : pipe_shape<VT, XT>(h, tau, &sh, h->tune_kernel == 0 ? h->tune_threads : 0);
+        // rounds: when chosen (pcdm_autotune / pcdm_set_tuning); on the workloads measured so far
+        // it did not beat the fused kernel where the one-pass grid cannot hold tau
+        bool rounds = false;
+        if (!pipe && h->tune_kernel == 3) {
+            const int thr = h->tune_kernel == 3 && h->tune_threads > 0 ? h->tune_threads : kPipeRoundsMaxBlock;
+            const int cap = Kernels<VT, XT>::pipe_rounds_max_blocks(thr);
+            if (cap > 0) {
+                sh.W = 1;
+                sh.threads = thr;
+                const int64_t need = (tau + thr - 1) / thr;
+                sh.blocks = int(need < cap ? need : cap);
+                rounds = true;
+            }
+        }
+        h->rounds_last = rounds;
+        if (rounds) {
+            const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
+            if (!h->g2) {
+                CK(h, cudaStreamSynchronize(h->stream));
+                CK(h, dalloc_bytes(&h->g2, int64_t(gbytes)));
+                a.g2 = static_cast<XT *>(h->g2);
+                h->g2_valid = false;
+            }
+            if (!h->g2_valid) CK(h, cudaMemcpyAsync(h->g2, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
+            CK(h, Kernels<VT, XT>::fused_pipe_rounds(a, sh, h->k, iters, h->stream));
+            h->g2_valid = true;
+        } else if (pipe) {
             const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
             if (!h->g2) {
                 CK(h, cudaStreamSynchronize(h->stream));
@@ -219,7 +247,7 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         h->ev_pending.emplace_back(e0, e1);
     }
     h->k += iters;
-    h->sample_valid = true;
+    h->sample_valid = !h->rounds_last;
     h->sample_seed = seed;
     h->sample_tau = tau;
     h->sample_k = h->k;
@@ -1168,6 +1196,30 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
     return PCDM_OK;
 }
 
+pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (!t) {
+        h->tune_kernel = -1;
+        h->tune_W = 0;
+        h->tune_threads = 0;
+        return PCDM_OK;
+    }
+    const bool lanes_ok = t->lanes_per_col == 1 || t->lanes_per_col == 2 || t->lanes_per_col == 4 ||
+                          t->lanes_per_col == 8 || t->lanes_per_col == 16 || t->lanes_per_col == 32;
+    if (t->kernel < 0 || t->kernel > 3 || !lanes_ok)
+        return set_err(h, PCDM_EINVAL, "kernel must be 0..3 and lanes_per_col a power of two up to 32");
+    if ((t->kernel == 0 && (t->threads_per_block < 32 || t->threads_per_block > kPipeMaxBlock)) ||
+        (t->kernel == 3 && (t->threads_per_block < 32 || t->threads_per_block > kPipeRoundsMaxBlock)) ||
+        t->threads_per_block % 32 != 0)
+        return set_err(h, PCDM_EINVAL, "threads_per_block must be a multiple of 32 within the kernel's limit");
+    h->tune_kernel = t->kernel;
+    h->tune_W = t->lanes_per_col;
+    h->tune_threads = t->threads_per_block;
+    return PCDM_OK;
+}
+
 pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_tuning *best)
 {
     pcdm_status s = usable(h);
@@ -1208,6 +1260,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     for (int t : {128, 192, 256, 320, 384, 448}) cands.push_back({0, 1, t});
     for (int W : {1, 2, 4, 8, 16, 32}) cands.push_back({1, W, 0});
     for (int W : {1, 4, 16}) cands.push_back({2, W, 0});
+    for (int t : {128, 256}) cands.push_back({3, 1, t});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));

@@ -88,9 +88,10 @@ struct pcdm_ctx {
     int64_t last_solve_iters = 0;   // iterations of the last pcdm_solve (0 after create / reset)
     uint64_t async_u = 0;           // next update number of the asynchronous mode
     // iteration kernel chosen by pcdm_autotune (-1: the built-in rule)
-    int tune_kernel = -1;           // 0 pipelined, 1 fused with tune_W lanes per column, 2 two-kernel form
+    int tune_kernel = -1;           // 0 pipelined, 1 fused with tune_W lanes, 2 two-kernel form, 3 pipelined rounds
     int tune_W = 0;
     int tune_threads = 0;           // block size of the pipelined kernel (0: built-in rule)
+    bool rounds_last = false;       // the last segment ran the pipelined rounds kernel (S_{k} not left drawn)
     bool sample_valid = false;
     uint64_t sample_seed = 0;
     int64_t sample_tau = 0, sample_k = -1;

@@ -28,6 +28,7 @@ constexpr int kFinishBlock = 256;    // threads of the single-block gap reductio
 // column, 256 (up to 255 registers) for wider groups, whose chunk loops need more.
 __host__ __device__ constexpr int fused_max_block(int W) { return W == 1 ? 448 : 256; }
 constexpr int kPipeMaxBlock = 448;   // block limit of the pipelined kernel (its chunk buffers fill shared memory)
+constexpr int kPipeRoundsMaxBlock = 256;   // block limit of the pipelined rounds kernel (up to 255 registers)
 constexpr int64_t kSlack = 1024;     // trailing entries of prow / pval
 constexpr int kLaneRun = 16;         // entries a lane reads per chunk (16-byte vector loads)
 
@@ -105,6 +106,10 @@ struct Kernels {
     static cudaError_t fused_pipe(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
                                   cudaStream_t st);
     static int pipe_max_blocks(int threads);
+    // Pipelined kernel for tau beyond the grid (several positions per thread per iteration).
+    static cudaError_t fused_pipe_rounds(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
+                                         cudaStream_t st);
+    static int pipe_rounds_max_blocks(int threads);
     // Asynchronous updates u0 .. u0+count-1 (no barrier; atomics on x and g).
     static cudaError_t async(const IterArgs<VT, XT> &a, int blocks, uint64_t nthreads, uint64_t u0, uint64_t count,
                              cudaStream_t st);

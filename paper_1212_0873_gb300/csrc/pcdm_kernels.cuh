@@ -750,6 +750,212 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     flush_counters(cnt, a.counters);
 }
 
+// Scatter of a whole column read from memory (A evict-first, g evict-last).
+template <typename VT, typename XT>
+__device__ __forceinline__ void mem_scatter(const IterArgs<VT, XT> &a, const Col<XT> &d, XT h, XT *g, uint64_t pf,
+                                            uint64_t pl)
+{
+    for (int cs = 0; cs < d.cnt; cs += kE) {
+        Chunk<kE, XT> t;
+        ld_chunk_hint<kE>(t, a.prow, a.pval, d.pbeg + cs, pf);
+        chunk_scatter_hint<kE>(t, g, h, d.cnt - cs, pl);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined kernel for tau larger than the grid: thread t of T owns positions
+// t, t + T, ..., t + (R-1) T of every iteration ("rounds").  Its work items
+// (k, r) form one stream: while item q is computed, the first chunk of item
+// q+1 arrives in the other shared-memory slot (TMA bulk copies, as in
+// k_fused_pipe) and the sample of item q+2 is drawn.  The residual is double
+// buffered (iteration k gathers from buffer k & 1, scatters into the other),
+// so the only grid barrier is at the end of an iteration.  The step of
+// position j in iteration k-1, still owed to the other buffer, is kept in
+// H[j] with its column in S[(k-1) & 1][j] and re-scattered from memory when
+// item (k, r) passes position j (most steps are zero).
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(kPipeRoundsMaxBlock, 1) k_fused_pipe_rounds(const IterArgs<VT, XT> a, int64_t k0,
+                                                                        int64_t iters, int64_t R)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int VW = pipe_value_words<VT>();
+    constexpr int SB = pipe_slot_bytes<VT>();
+    constexpr int G = pad_granule<VT>();
+    const int nt = blockDim.x, t = threadIdx.x;
+    const int64_t T = int64_t(gridDim.x) * nt;
+    const int64_t tg = int64_t(blockIdx.x) * nt + t;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + size_t(2) * nt * SB);
+    unsigned long long target = 0;
+    uint32_t phase = 0;
+    Counters cnt;
+    const uint64_t pf = l2_evict_first();
+    const uint64_t pl = l2_evict_last();
+    auto slot = [&](int b) { return smem + (size_t(b) * nt + t) * SB; };
+    auto gbuf = [&](int64_t kk) { return (kk & 1) ? a.g2 : a.g; };
+    auto fill = [&](int b, const Col<XT> &d, bool mine) {
+        if (mine && d.cnt > 0) {
+            const int64_t pc = (int64_t(d.cnt) + G - 1) / G * G;
+            const uint32_t e = uint32_t(pc < kE ? pc : kE);
+            const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
+            mbar_arrive_expect_tx(&mbar[b], br + bv);
+            bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b], pf);
+            bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b], pf);
+        } else {
+            mbar_arrive(&mbar[b]);
+        }
+    };
+    auto wait_buf = [&](int b) {
+        const bool ok = mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, a.status, a.timeout_ns);
+        phase ^= 1u << b;
+        return ok;
+    };
+    if (t == 0) {
+        mbar_init(&mbar[0], uint32_t(nt));
+        mbar_init(&mbar[1], uint32_t(nt));
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+
+    const int64_t items = iters * R;
+    // position and iteration of item q
+    auto pos_of = [&](int64_t q) { return tg + (q % R) * T; };
+    auto k_of = [&](int64_t q) { return k0 + q / R; };
+    // sample of item q (key cached per iteration)
+    SampleKey key = make_sample_key(a.seed, k0, a.n);
+    int64_t key_k = k0;
+    auto draw = [&](int64_t q, int32_t &i, Col<XT> &d) {
+        const int64_t j = pos_of(q);
+        const int64_t kq = k_of(q);
+        if (q >= items || j >= a.tau) {
+            i = 0;
+            d.pbeg = 0;
+            d.cnt = 0;
+            d.invL = XT(0);
+            return false;
+        }
+        if (kq != key_k) {
+            key = make_sample_key(a.seed, kq, a.n);
+            key_k = kq;
+        }
+        i = sample_index(uint32_t(j), key);
+        d = load_col(a.desc, i, pf);
+        return true;
+    };
+
+    int32_t i_cur = 0, i_nxt = 0;
+    Col<XT> d_cur, d_nxt;
+    bool own_cur = draw(0, i_cur, d_cur);
+    bool own_nxt = draw(1, i_nxt, d_nxt);
+    fill(0, d_cur, own_cur);
+
+    constexpr int kT = kE / 2;
+    for (int64_t q = 0; q < items; ++q) {
+        const int64_t k = k_of(q);
+        const int64_t r = q % R;
+        const int64_t j = pos_of(q);
+        const int b = int(q & 1);
+        if (!wait_buf(b)) return;
+        const unsigned char *my = slot(b);
+        const XT *gk = gbuf(k);
+        XT *gn = gbuf(k + 1);
+        int32_t i_nn = 0;
+        Col<XT> d_nn;
+        bool own_nn = false;
+        if (own_cur) {
+            const double xi = ldcg_hint(a.x + i_cur, pf);
+            const int valid = d_cur.cnt;
+            int32_t row[kE];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint4 r4 = reinterpret_cast<const uint4 *>(my)[w];
+                row[4 * w + 0] = int32_t(r4.x);
+                row[4 * w + 1] = int32_t(r4.y);
+                row[4 * w + 2] = int32_t(r4.z);
+                row[4 * w + 3] = int32_t(r4.w);
+            }
+            XT gv[kE];
+#pragma unroll
+            for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
+            Chunk<kT, XT> tl;
+            if (valid > kE) ld_chunk_hint<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE, pf);
+            own_nn = draw(q + 2, i_nn, d_nn);
+            XT gt[kT];
+#pragma unroll
+            for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg_hint(gk + tl.row[e], pl) : XT(0);
+            constexpr int EPW = 16 / int(sizeof(VT));
+            XT acc = XT(0);
+#pragma unroll
+            for (int w = 0; w < VW; ++w) {
+                XT vw[EPW];
+                decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
+#pragma unroll
+                for (int e = 0; e < EPW; ++e)
+                    if (w * EPW + e < valid) acc = fma(vw[e], gv[w * EPW + e], acc);
+            }
+#pragma unroll
+            for (int e = 0; e < kT; ++e)
+                if (kE + e < valid) acc = fma(tl.val[e], gt[e], acc);
+            for (int cs = kE + kT; cs < valid; cs += kE) {
+                Chunk<kE, XT> tc;
+                ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
+                acc += chunk_dot_hint<kE, XT>(tc, gk, valid - cs, pl);
+            }
+            const double xn = prox_step(xi, double(acc), double(d_cur.invL), a.inv_beta, a.lambda);
+            const double h64 = xn - xi;
+            const XT h = XT(h64);
+            if (h64 != 0.0) st_hint(a.x + i_cur, xn, pf);
+            cnt.gathered += (unsigned long long)valid;
+            if (h64 != 0.0) {
+                cnt.nonzero += 1;
+                cnt.scattered += (unsigned long long)valid;
+            }
+            // the step of iteration k-1 at this position, owed to the other buffer
+            if (k > k0) {
+                const XT hp = a.h[j];
+                if (hp != XT(0)) mem_scatter<VT, XT>(a, load_col(a.desc, sample_buf(a, k - 1)[j], pf), hp, gn, pf, pl);
+            }
+            if (h != XT(0)) slot_scatter<VT, XT>(a, my, d_cur, h, gn, pf, pl);
+            a.h[j] = h;
+            sample_buf(a, k)[j] = i_cur;
+        } else {
+            own_nn = draw(q + 2, i_nn, d_nn);
+        }
+        if (r == R - 1) {
+            // ---------------- end of iteration k: the only grid barrier
+            target += gridDim.x;
+            grid_arrive(a.bar);
+            fence_proxy_async_shared();
+            fill(b ^ 1, d_nxt, own_nxt);
+            if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) {
+                wait_buf(b ^ 1);
+                return;
+            }
+        } else {
+            fence_proxy_async_shared();
+            fill(b ^ 1, d_nxt, own_nxt);
+        }
+        i_cur = i_nxt;
+        d_cur = d_nxt;
+        own_cur = own_nxt;
+        i_nxt = i_nn;
+        d_nxt = d_nn;
+        own_nxt = own_nn;
+    }
+    // Both buffers equal again: the last iteration's steps go into the buffer
+    // that holds g_{k0+iters-1}.
+    if (iters > 0) {
+        const int64_t kl = k0 + iters - 1;
+        for (int64_t r = 0; r < R; ++r) {
+            const int64_t j = tg + r * T;
+            if (j >= a.tau) break;
+            const XT hp = a.h[j];
+            if (hp != XT(0)) mem_scatter<VT, XT>(a, load_col(a.desc, sample_buf(a, kl)[j], pf), hp, gbuf(kl), pf, pl);
+        }
+    }
+    wait_buf(int(items & 1));
+    flush_counters(cnt, a.counters);
+}
+
 // ---------------------------------------------------------------------------
 // Asynchronous PCDM (the shared-memory implementation mode of Sec. 8.1): every
 // thread repeatedly takes the next update u of a global sequence, picks block
@@ -1037,6 +1243,35 @@ cudaError_t Kernels<VT, XT>::fused_pipe(const IterArgs<VT, XT> &a, const FusedSh
     IterArgs<VT, XT> args = a;
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
     return cudaLaunchCooperativeKernel((const void *)k_fused_pipe<VT, XT>, dim3(unsigned(sh.blocks)),
+                                       dim3(unsigned(sh.threads)), params, pipe_smem_bytes<VT>(sh.threads), st);
+}
+
+template <typename VT, typename XT>
+int Kernels<VT, XT>::pipe_rounds_max_blocks(int threads)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const size_t bytes = pipe_smem_bytes<VT>(threads);
+    if (cudaFuncSetAttribute(k_fused_pipe_rounds<VT, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) !=
+        cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_pipe_rounds<VT, XT>, threads, bytes) !=
+        cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+template <typename VT, typename XT>
+cudaError_t Kernels<VT, XT>::fused_pipe_rounds(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0,
+                                               int64_t iters, cudaStream_t st)
+{
+    if (iters <= 0 || a.tau <= 0) return cudaSuccess;
+    IterArgs<VT, XT> args = a;
+    const int64_t T = int64_t(sh.blocks) * sh.threads;
+    int64_t R = (a.tau + T - 1) / T;
+    void *params[] = {(void *)&args, (void *)&k0, (void *)&iters, (void *)&R};
+    return cudaLaunchCooperativeKernel((const void *)k_fused_pipe_rounds<VT, XT>, dim3(unsigned(sh.blocks)),
                                        dim3(unsigned(sh.threads)), params, pipe_smem_bytes<VT>(sh.threads), st);
 }
 

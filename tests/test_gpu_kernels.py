@@ -1,0 +1,65 @@
+"""Every iteration kernel (pipelined, fused with several lane widths, two-kernel,
+pipelined rounds) selected by hand through pcdm_set_tuning follows the oracle;
+the rounds kernel also with several positions per thread (tau beyond the grid)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1212_0873_gb300 import Lasso, instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1212_0873_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b))) / max(float(np.max(np.abs(b))), 1e-300)
+
+
+CHOICES = [(0, 1, 64), (0, 1, 448), (1, 1, 0), (1, 4, 0), (1, 32, 0), (2, 1, 0), (2, 16, 0), (3, 1, 128),
+           (3, 1, 256)]
+
+
+@pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])
+@pytest.mark.parametrize("choice", CHOICES)
+def test_each_kernel_follows_the_oracle(val_dtype, tol, choice):
+    inst = instances.per_col_instance(2000, 1000, 20, nnz_star=50, val_dtype=val_dtype, seed=1001)
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    with Lasso.from_instance(inst) as s:
+        s.set_tuning(*choice)
+        for upto in (1, 9, 40):
+            s.step(96, upto - s.iteration, 2)
+            ref.run(96, upto - ref.k, 2)
+            assert _rel(s.x(), ref.x) <= tol, (choice, upto)
+            assert _rel(s.residual(), ref.g) <= tol, (choice, upto)
+
+
+@pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("bf16", 1e-5)])
+def test_rounds_kernel_with_several_positions_per_thread(val_dtype, tol):
+    # tau = 2^17 is beyond one pass of the grid: two or more positions per thread
+    inst = instances.per_col_instance(400_000, 200_000, 10, nnz_star=2000, val_dtype=val_dtype, seed=91)
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    tau = 1 << 17
+    with Lasso.from_instance(inst) as s:
+        s.set_tuning(3, 1, 256)
+        for upto in (1, 4, 12):
+            s.step(tau, upto - s.iteration, 8)
+            ref.run(tau, upto - ref.k, 8)
+            assert _rel(s.x(), ref.x) <= tol, upto
+            assert _rel(s.residual(), ref.g) <= tol, upto
+        s.set_tuning(3, 1, 128)                       # more rounds per iteration
+        s.step(tau, 5, 8)
+        ref.run(tau, 5, 8)
+        assert _rel(s.x(), ref.x) <= tol
+        ok, it, rel = s.solve(tau, 8, 1e-8 if val_dtype == "f64" else 1e-6, 100_000)
+        assert ok
