@@ -191,7 +191,7 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
  * state (which is restored afterwards; the counters of pcdm_get_stats are not
  * changed).  Candidates: the pipelined one-lane-per-column kernel with blocks
  * of 128 .. 448 threads (the tau positions per block; when tau fits one pass of
- * the grid), its rounds form with blocks of 128 or 256 threads (several
+ * the grid), each with and without the column heads, its rounds form with blocks of 128 or 256 threads (several
  * positions per thread and iteration), the fused kernel with 1 .. 32 lanes per
  * column (its scatter reloads the column), and the two-kernel form with 1, 4 or
  * 16 lanes.  The fastest is kept for later pcdm_step /
@@ -203,14 +203,18 @@ typedef struct {
                                    3 pipelined rounds */
     int32_t lanes_per_col;
     int32_t threads_per_block;  /* pipelined kernel only */
-    int32_t reserved;
+    int32_t heads;              /* pipelined kernels: 1 = fetch each sampled column's first chunk
+                                   (16 row indices, then 16 values) with one bulk copy from a
+                                   per-column head array, n * (64 + 16 sizeof(value)) bytes built
+                                   on first use when free device memory holds four times that;
+                                   0 = two copies from the padded CSC arrays */
     double us_per_iteration;    /* measured */
 } pcdm_tuning;
 
 pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_tuning *best);
 
 /* Choose the iteration kernel by hand (the fields of pcdm_tuning; us_per_iteration
- * is ignored; threads_per_block a multiple of 32, up to 448 for kernel 0 and
+ * is ignored; heads 0 or 1; threads_per_block a multiple of 32, up to 448 for kernel 0 and
  * 256 for kernel 3), or return to the built-in rule with t = NULL.  A pipelined
  * kernel that cannot hold tau at that block size falls back to the fused one. */
 pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t);

@@ -24,7 +24,7 @@ class pcdm_csc(ctypes.Structure):
 
 
 class pcdm_tuning(ctypes.Structure):
-    _fields_ = [("kernel", _i32), ("lanes_per_col", _i32), ("threads_per_block", _i32), ("reserved", _i32),
+    _fields_ = [("kernel", _i32), ("lanes_per_col", _i32), ("threads_per_block", _i32), ("heads", _i32),
                 ("us_per_iteration", _dbl)]
 
 
@@ -464,13 +464,13 @@ def pcdm_multi_destroy(h):
 def pcdm_autotune(h, tau, trial_iters):
     t = pcdm_tuning()
     _check(lib().pcdm_autotune(h, int(tau), int(trial_iters), ctypes.byref(t)), h)
-    return {name: getattr(t, name) for name, _ in pcdm_tuning._fields_ if name != "reserved"}
+    return {name: getattr(t, name) for name, _ in pcdm_tuning._fields_}
 
 
-def pcdm_set_tuning(h, kernel=None, lanes_per_col=1, threads_per_block=0):
+def pcdm_set_tuning(h, kernel=None, lanes_per_col=1, threads_per_block=0, heads=1):
     """kernel None: back to the built-in rule."""
     if kernel is None:
         _check(lib().pcdm_set_tuning(h, None), h)
         return
-    t = pcdm_tuning(int(kernel), int(lanes_per_col), int(threads_per_block), 0, 0.0)
+    t = pcdm_tuning(int(kernel), int(lanes_per_col), int(threads_per_block), int(heads), 0.0)
     _check(lib().pcdm_set_tuning(h, ctypes.byref(t)), h)

@@ -24,7 +24,7 @@ void free_all(pcdm_handle h)
     void *ptrs[] = {h->desc, h->prow, h->pval, h->b, h->L64, h->x, h->g, h->g2,
                     h->S[0], h->S[1], h->h, h->counters, h->bar, h->status, h->gap_part, h->gap_out,
                     h->as_sidx, h->as_c, h->as_sgn, h->as_u, h->as_dx, h->as_q, h->as_rowcnt, h->as_H,
-                    h->as_S, h->as_part, h->win};
+                    h->as_S, h->as_part, h->win, h->head};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->g64 && h->g64 != h->g) cudaFree(h->g64);
@@ -91,6 +91,7 @@ IterArgs<VT, XT> iter_args(pcdm_handle h, int64_t tau, uint64_t seed)
     a.sampling = h->opts.sampling;
     a.keep_T = binomial_threshold(h->opts.p_b);
     a.win = h->win;
+    a.head = h->head;
     a.lambda = h->lambda;
     a.n = h->n;
     a.tau = tau;
@@ -144,6 +145,32 @@ bool pipe_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads = 0
     sh->blocks = int(blocks);
     sh->threads = int(threads);
     return true;
+}
+
+// The per-column heads of the pipelined kernels, built on their first use.
+template <typename VT, typename XT>
+pcdm_status ensure_heads(pcdm_handle h, IterArgs<VT, XT> &a)
+{
+    a.head = nullptr;
+    if (!h->tune_heads || h->head_off) return PCDM_OK;
+    if (!h->head) {
+        const int64_t need = h->n * head_stride<VT>();
+        size_t free_b = 0, total_b = 0;
+        CK(h, cudaMemGetInfo(&free_b, &total_b));
+        if (int64_t(free_b / 4) < need) {
+            h->head_off = true;
+            return PCDM_OK;
+        }
+        CK(h, cudaStreamSynchronize(h->stream));
+        void *p = nullptr;
+        CK(h, dalloc_bytes(&p, need));
+        h->head = static_cast<unsigned char *>(p);
+        CK(h, Kernels<VT, XT>::build_heads(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
+                                           static_cast<const VT *>(h->pval), h->n, h->head, h->stream));
+        h->st_kernels += 1;
+    }
+    a.head = h->head;
+    return PCDM_OK;
 }
 
 // Run `iters` iterations starting at h->k with S_k already drawn.
@@ -201,6 +228,10 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
             }
         }
         h->rounds_last = rounds;
+        if (rounds || pipe) {
+            pcdm_status hs = ensure_heads<VT, XT>(h, a);
+            if (hs != PCDM_OK) return hs;
+        }
         if (rounds) {
             const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
             if (!h->g2) {
@@ -1204,8 +1235,10 @@ pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
         h->tune_kernel = -1;
         h->tune_W = 0;
         h->tune_threads = 0;
+        h->tune_heads = 1;
         return PCDM_OK;
     }
+    if (t->heads != 0 && t->heads != 1) return set_err(h, PCDM_EINVAL, "heads must be 0 or 1");
     const bool lanes_ok = t->lanes_per_col == 1 || t->lanes_per_col == 2 || t->lanes_per_col == 4 ||
                           t->lanes_per_col == 8 || t->lanes_per_col == 16 || t->lanes_per_col == 32;
     if (t->kernel < 0 || t->kernel > 3 || !lanes_ok)
@@ -1217,6 +1250,7 @@ pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
     h->tune_kernel = t->kernel;
     h->tune_W = t->lanes_per_col;
     h->tune_threads = t->threads_per_block;
+    h->tune_heads = t->heads;
     return PCDM_OK;
 }
 
@@ -1242,7 +1276,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     const int64_t k0 = h->k;
     const int64_t st_it = h->st_iterations, st_up = h->st_updates, st_la = h->st_launches, st_ke = h->st_kernels;
     const double st_ms = h->st_kernel_ms;
-    const int keep[3] = {h->tune_kernel, h->tune_W, h->tune_threads};
+    const int keep[4] = {h->tune_kernel, h->tune_W, h->tune_threads, h->tune_heads};
     auto restore = [&]() -> pcdm_status {
         CK(h, cudaMemcpyAsync(h->x, x0, xbytes, cudaMemcpyDeviceToDevice, h->stream));
         CK(h, cudaMemcpyAsync(h->g, g0, gbytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -1254,17 +1288,18 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     CK(h, cudaMemcpyAsync(x0, h->x, xbytes, cudaMemcpyDeviceToDevice, h->stream));
     CK(h, cudaMemcpyAsync(g0, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
     struct Cand {
-        int kernel, W, threads;
+        int kernel, W, threads, heads;
     };
     std::vector<Cand> cands;
-    for (int t : {128, 192, 256, 320, 384, 448}) cands.push_back({0, 1, t});
-    for (int W : {1, 2, 4, 8, 16, 32}) cands.push_back({1, W, 0});
-    for (int W : {1, 4, 16}) cands.push_back({2, W, 0});
-    for (int t : {128, 256}) cands.push_back({3, 1, t});
+    for (int hd : {1, 0})
+        for (int t : {128, 192, 256, 320, 384, 448}) cands.push_back({0, 1, t, hd});
+    for (int W : {1, 2, 4, 8, 16, 32}) cands.push_back({1, W, 0, 1});
+    for (int W : {1, 4, 16}) cands.push_back({2, W, 0, 1});
+    for (int t : {128, 256}) cands.push_back({3, 1, t, 1});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
-    Cand bestc{-1, 0, 0};
+    Cand bestc{-1, 0, 0, 1};
     double best_us = 0.0;
     pcdm_status rs = PCDM_OK;
     for (const Cand &c : cands) {
@@ -1283,9 +1318,11 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
             });
             if (!ok) continue;
         }
+        if (c.kernel == 0 && c.heads && h->head_off) continue;   // the heads do not fit
         h->tune_kernel = c.kernel;
         h->tune_W = c.W;
         h->tune_threads = c.threads;
+        h->tune_heads = c.heads;
         if ((rs = restore()) != PCDM_OK) break;
         if ((rs = pcdm_step(h, tau, 2, 0x5eedULL)) != PCDM_OK) break;   // warm-up (first launch of a shape)
         if ((rs = restore()) != PCDM_OK) break;
@@ -1322,16 +1359,18 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
         h->tune_kernel = keep[0];
         h->tune_W = keep[1];
         h->tune_threads = keep[2];
+        h->tune_heads = keep[3];
         return rs;
     }
     h->tune_kernel = bestc.kernel;
     h->tune_W = bestc.W;
     h->tune_threads = bestc.threads;
+    h->tune_heads = bestc.heads;
     if (best) {
         best->kernel = bestc.kernel;
         best->lanes_per_col = bestc.W;
         best->threads_per_block = bestc.threads;
-        best->reserved = 0;
+        best->heads = bestc.heads && !h->head_off ? 1 : 0;
         best->us_per_iteration = best_us;
     }
     return PCDM_OK;

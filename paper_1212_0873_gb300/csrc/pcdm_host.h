@@ -55,6 +55,7 @@ struct pcdm_ctx {
     double *x = nullptr;          // n FP64 entries
     void *g = nullptr;            // m entries of xg dtype
     void *g2 = nullptr;           // second residual buffer of the pipelined kernel
+    unsigned char *head = nullptr;  // per-column heads of the pipelined kernels (built on first use)
     bool g2_valid = false;        // g2 holds the same residual as g
     double *g64 = nullptr;        // FP64 residual of the refresh (aliases g in the FP64 form)
     int32_t *S[2] = {nullptr, nullptr};
@@ -91,6 +92,8 @@ struct pcdm_ctx {
     int tune_kernel = -1;           // 0 pipelined, 1 fused with tune_W lanes, 2 two-kernel form, 3 pipelined rounds
     int tune_W = 0;
     int tune_threads = 0;           // block size of the pipelined kernel (0: built-in rule)
+    int tune_heads = 1;             // pipelined kernels read the column heads (when they fit)
+    bool head_off = false;          // the column heads did not fit in device memory
     bool rounds_last = false;       // the last segment ran the pipelined rounds kernel (S_{k} not left drawn)
     bool sample_valid = false;
     uint64_t sample_seed = 0;

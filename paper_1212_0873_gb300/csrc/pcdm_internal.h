@@ -81,7 +81,18 @@ struct IterArgs {
     int sampling;
     uint64_t keep_T;
     const unsigned long long *win;
+    // Per-column heads for the pipelined kernels (NULL: copy rows and values
+    // separately): column i's first kLaneRun row indices at head + i * stride,
+    // its first kLaneRun values 64 bytes further.
+    const unsigned char *head;
 };
+
+// Bytes of one column head: kLaneRun row indices, then kLaneRun values.
+template <typename VT>
+__host__ __device__ constexpr int64_t head_stride()
+{
+    return 4 * kLaneRun + kLaneRun * int64_t(sizeof(VT));
+}
 
 // Launch shape of the fused kernel.
 struct FusedShape {
@@ -118,6 +129,9 @@ struct Kernels {
     static cudaError_t setup_cols(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, int64_t m,
                                   int64_t n, double *L, int *rowcnt, int *flags, cudaStream_t st);
     // Padded layout: copy the columns into prow/pval at pbeg (entries) and write desc.
+    // head + i * head_stride<VT>(): the first chunk of column i (rows, then values), zero-padded.
+    static cudaError_t build_heads(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, int64_t n,
+                                   unsigned char *head, cudaStream_t st);
     static cudaError_t build_layout(const int64_t *col_ptr, const int32_t *row_idx, const VT *val,
                                     const int64_t *pbeg, const double *L, int64_t n, ColDesc<XT> *desc,
                                     int32_t *prow, VT *pval, cudaStream_t st);

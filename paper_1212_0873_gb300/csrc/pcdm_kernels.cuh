@@ -599,15 +599,21 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     // the residual buffer that holds g_k at iteration k
     auto gbuf = [&](int64_t kk) { return (kk & 1) ? a.g2 : a.g; };
     // This thread's share of filling buffer b: arrive on mbar[b] and, for a
-    // non-empty column, bulk-copy its first chunk (rows, then values).
-    auto fill = [&](int b, const Col<XT> &d, bool mine) {
+    // non-empty column, bulk-copy its first chunk (rows, then values): one copy
+    // from the column's head when the heads exist, else two.
+    auto fill = [&](int b, const Col<XT> &d, int32_t ci, bool mine) {
         if (mine && d.cnt > 0) {
             const int64_t pc = (int64_t(d.cnt) + G - 1) / G * G;
             const uint32_t e = uint32_t(pc < kE ? pc : kE);
             const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
-            mbar_arrive_expect_tx(&mbar[b], br + bv);
-            bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b], pf);
-            bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b], pf);
+            if (a.head) {
+                mbar_arrive_expect_tx(&mbar[b], 64u + bv);
+                bulk_copy_g2s(slot(b), a.head + int64_t(ci) * head_stride<VT>(), 64u + bv, &mbar[b], pf);
+            } else {
+                mbar_arrive_expect_tx(&mbar[b], br + bv);
+                bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b], pf);
+                bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b], pf);
+            }
         } else {
             mbar_arrive(&mbar[b]);
         }
@@ -638,7 +644,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         i_nxt = sample_index(uint32_t(j0), make_sample_key(a.seed, k0 + 1, a.n));
         d_nxt = load_col(a.desc, i_nxt, pf);
     }
-    fill(0, d_cur, own);
+    fill(0, d_cur, i_cur, own);
 
     constexpr int kT = kE / 2;   // tail entries [kE, kE + kT) fetched early into registers
     for (int64_t it = 0; it < iters; ++it) {
@@ -729,7 +735,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         target += gridDim.x;
         grid_arrive(a.bar);
         fence_proxy_async_shared();
-        fill(b ^ 1, d_nxt, own);
+        fill(b ^ 1, d_nxt, i_nxt, own);
         if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) {
             wait_buf(b ^ 1);   // the copies just issued land before the block leaves
             return;
@@ -792,14 +798,19 @@ __global__ void __launch_bounds__(kPipeRoundsMaxBlock, 1) k_fused_pipe_rounds(co
     const uint64_t pl = l2_evict_last();
     auto slot = [&](int b) { return smem + (size_t(b) * nt + t) * SB; };
     auto gbuf = [&](int64_t kk) { return (kk & 1) ? a.g2 : a.g; };
-    auto fill = [&](int b, const Col<XT> &d, bool mine) {
+    auto fill = [&](int b, const Col<XT> &d, int32_t ci, bool mine) {
         if (mine && d.cnt > 0) {
             const int64_t pc = (int64_t(d.cnt) + G - 1) / G * G;
             const uint32_t e = uint32_t(pc < kE ? pc : kE);
             const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
-            mbar_arrive_expect_tx(&mbar[b], br + bv);
-            bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b], pf);
-            bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b], pf);
+            if (a.head) {
+                mbar_arrive_expect_tx(&mbar[b], 64u + bv);
+                bulk_copy_g2s(slot(b), a.head + int64_t(ci) * head_stride<VT>(), 64u + bv, &mbar[b], pf);
+            } else {
+                mbar_arrive_expect_tx(&mbar[b], br + bv);
+                bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b], pf);
+                bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b], pf);
+            }
         } else {
             mbar_arrive(&mbar[b]);
         }
@@ -846,7 +857,7 @@ __global__ void __launch_bounds__(kPipeRoundsMaxBlock, 1) k_fused_pipe_rounds(co
     Col<XT> d_cur, d_nxt;
     bool own_cur = draw(0, i_cur, d_cur);
     bool own_nxt = draw(1, i_nxt, d_nxt);
-    fill(0, d_cur, own_cur);
+    fill(0, d_cur, i_cur, own_cur);
 
     constexpr int kT = kE / 2;
     for (int64_t q = 0; q < items; ++q) {
@@ -925,14 +936,14 @@ __global__ void __launch_bounds__(kPipeRoundsMaxBlock, 1) k_fused_pipe_rounds(co
             target += gridDim.x;
             grid_arrive(a.bar);
             fence_proxy_async_shared();
-            fill(b ^ 1, d_nxt, own_nxt);
+            fill(b ^ 1, d_nxt, i_nxt, own_nxt);
             if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) {
                 wait_buf(b ^ 1);
                 return;
             }
         } else {
             fence_proxy_async_shared();
-            fill(b ^ 1, d_nxt, own_nxt);
+            fill(b ^ 1, d_nxt, i_nxt, own_nxt);
         }
         i_cur = i_nxt;
         d_cur = d_nxt;
@@ -1062,6 +1073,26 @@ __global__ void k_build_layout(const int64_t *__restrict__ col_ptr, const int32_
         d.invL = L[i] > 0.0 ? XT(1.0 / L[i]) : XT(0);
         if constexpr (sizeof(XT) == 4) d.unused = 0.f;
         desc[i] = d;
+    }
+}
+
+// Column heads: the first kE row indices (zero-padded) and values of every column.
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_build_heads(const ColDesc<XT> *__restrict__ desc,
+                                                        const int32_t *__restrict__ prow, const VT *__restrict__ pval,
+                                                        int64_t n, unsigned char *__restrict__ head)
+{
+    const int64_t stride = int64_t(gridDim.x) * kBlock;
+    for (int64_t i = int64_t(blockIdx.x) * kBlock + threadIdx.x; i < n; i += stride) {
+        const Col<XT> c = load_col(desc, int32_t(i));
+        unsigned char *h = head + i * head_stride<VT>();
+        int32_t *hr = reinterpret_cast<int32_t *>(h);
+        VT *hv = reinterpret_cast<VT *>(h + 4 * kE);
+        for (int e = 0; e < kE; ++e) {
+            const bool in = e < c.cnt;
+            hr[e] = in ? prow[c.pbeg + e] : 0;
+            hv[e] = in ? pval[c.pbeg + e] : VT{};
+        }
     }
 }
 
@@ -1273,6 +1304,15 @@ cudaError_t Kernels<VT, XT>::fused_pipe_rounds(const IterArgs<VT, XT> &a, const 
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters, (void *)&R};
     return cudaLaunchCooperativeKernel((const void *)k_fused_pipe_rounds<VT, XT>, dim3(unsigned(sh.blocks)),
                                        dim3(unsigned(sh.threads)), params, pipe_smem_bytes<VT>(sh.threads), st);
+}
+
+template <typename VT, typename XT>
+cudaError_t Kernels<VT, XT>::build_heads(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, int64_t n,
+                                         unsigned char *head, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_build_heads<VT, XT><<<blocks_for_threads(n, 152 * 64), kBlock, 0, st>>>(desc, prow, pval, n, head);
+    return cudaGetLastError();
 }
 
 template <typename VT, typename XT>

@@ -1,5 +1,6 @@
 """Every iteration kernel (pipelined, fused with several lane widths, two-kernel,
-pipelined rounds) selected by hand through pcdm_set_tuning follows the oracle;
+pipelined rounds; the pipelined ones with and without the column heads)
+selected by hand through pcdm_set_tuning follows the oracle;
 the rounds kernel also with several positions per thread (tau beyond the grid)."""
 import numpy as np
 import pytest
@@ -24,8 +25,9 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b))) / max(float(np.max(np.abs(b))), 1e-300)
 
 
-CHOICES = [(0, 1, 64), (0, 1, 448), (1, 1, 0), (1, 4, 0), (1, 32, 0), (2, 1, 0), (2, 16, 0), (3, 1, 128),
-           (3, 1, 256)]
+# (kernel, lanes per column, threads per block, column heads)
+CHOICES = [(0, 1, 64, 1), (0, 1, 448, 1), (0, 1, 128, 0), (1, 1, 0, 1), (1, 4, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1),
+           (2, 16, 0, 1), (3, 1, 128, 1), (3, 1, 256, 0)]
 
 
 @pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])
@@ -57,7 +59,7 @@ def test_rounds_kernel_with_several_positions_per_thread(val_dtype, tol):
             ref.run(tau, upto - ref.k, 8)
             assert _rel(s.x(), ref.x) <= tol, upto
             assert _rel(s.residual(), ref.g) <= tol, upto
-        s.set_tuning(3, 1, 128)                       # more rounds per iteration
+        s.set_tuning(3, 1, 128, 0)                    # more rounds per iteration, no heads
         s.step(tau, 5, 8)
         ref.run(tau, 5, 8)
         assert _rel(s.x(), ref.x) <= tol
