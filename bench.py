@@ -66,6 +66,9 @@ def parse():
     p.add_argument("--no-async", action="store_true", help="skip the asynchronous-mode measurement")
     p.add_argument("--no-multi", action="store_true", help="skip the many-small-problems measurement")
     p.add_argument("--no-tune", action="store_true", help="keep the built-in kernel choice (no pcdm_autotune)")
+    p.add_argument("--tuning", default=None,
+                   help="kernel,lanes_per_col,threads_per_block,heads set by hand (pcdm_set_tuning) instead of "
+                        "pcdm_autotune, e.g. 0,1,448,1 for the pipelined kernel with 448-thread blocks")
     p.add_argument("--sweep", action="store_true", help="print the omega x tau x dtype table of the scale workload")
     p.add_argument("--huge", action="store_true", help="time the 4e9-nonzero configuration (about 140 GB of HBM)")
     return p.parse_args()
@@ -136,20 +139,26 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_update(a):
-    """DRAM bytes per coordinate update of the fused kernel from the committed ncu
-    summary, when it was taken on the current kernel sources and this workload."""
+def traffic_per_update(a, tuning):
+    """(DRAM bytes per coordinate update, the tuning they were taken at) of the
+    iteration kernel from the committed ncu summary, when it was taken on the
+    current kernel sources, this workload and this kernel (same kernel, lanes per
+    column and column-head choice; the block size may differ), else (None, None)."""
     path = os.path.join(ROOT, "profiles", "fused_kernel_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
-        return None
+        return None, None
     if d.get("src_hash") != kernel_source_hash():
-        return None
+        return None, None
     key = "%s/omega%d/tau%d" % (a.dtype, a.omega, a.tau)
     ent = d.get("workloads", {}).get(key)
-    return None if ent is None else float(ent["dram_bytes_per_update"])
+    if ent is None or tuning is None:
+        return None, None
+    if any(ent.get("tuning", {}).get(f) != tuning.get(f) for f in ("kernel", "lanes_per_col", "heads")):
+        return None, None
+    return float(ent["dram_bytes_per_update"]), ent["tuning"]
 
 
 class ClockSampler:
@@ -502,7 +511,12 @@ def run_pcdm(a, rank, local, world):
     seed = rank
     solver = Lasso.from_instance(inst, profile=True, **kw)
     omega = solver.omega
-    tuning = solver.autotune(a.tau, 30) if (not a.unfused and not a.no_tune) else None
+    if a.tuning:
+        k, w, t, hd = (int(v) for v in a.tuning.split(","))
+        solver.set_tuning(k, w, t, hd)
+        tuning = {"kernel": k, "lanes_per_col": w, "threads_per_block": t, "heads": hd, "set_by_hand": True}
+    else:
+        tuning = solver.autotune(a.tau, 30) if (not a.unfused and not a.no_tune) else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
     def one_solve():
@@ -549,7 +563,7 @@ def run_pcdm(a, rank, local, world):
     avg_launch_s = st["iter_kernel_ms"] / launches / 1e3
     achieved = alg_bytes / launches / avg_launch_s / 1e9 if avg_launch_s > 0 else None
     peak, peak_kind = measured_peaks()
-    tpu = traffic_per_update(a)
+    tpu, tpu_tuning = traffic_per_update(a, tuning)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (tpu * st["updates"] / launches) if tpu is not None else None,
@@ -557,9 +571,11 @@ def run_pcdm(a, rank, local, world):
                            (tuning and tuning["kernel"] == 2) else
                            "k_fused (persistent PCDM1 iterations, %d lanes per column)" % tuning["lanes_per_col"]
                            if tuning and tuning["kernel"] == 1 else
+                           "k_fused_pipe_rounds (persistent PCDM1 iterations, several positions per thread)"
+                           if tuning and tuning["kernel"] == 3 else
                            "k_fused_pipe (persistent PCDM1 iterations)"), "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes / launches, "avg_launch_ms": avg_launch_s * 1e3,
-                "launches": st["iter_launches"]}
+                "launches": st["iter_launches"], "traffic_taken_at": tpu_tuning}
 
     # end to end through the public API from pinned host memory
     e2e = None
@@ -575,22 +591,29 @@ def run_pcdm(a, rank, local, world):
             pin[name] = t.numpy().view(arr.dtype)
         h2d = sum(v.nbytes for v in pin.values())
         e2e_s, e2e_updates, d2h = [], 0, 0
+        phases = [0.0, 0.0, 0.0]
         for q in range(a.warmup + a.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s2 = Lasso(inst.m, inst.n, pin["col_ptr"], pin["row_idx"], pin["val"], pin["b"], inst.lam, **kw)
+            t1 = time.perf_counter()
             ok, it, rel = s2.solve(a.tau, seed, a.tol, a.max_iters)
+            t2 = time.perf_counter()
             x = s2.x()
             gaps = s2.stats()["gaps"]
             s2.close()
             torch.cuda.synchronize()
             if q >= a.warmup:
-                e2e_s.append(time.perf_counter() - t0)
+                t3 = time.perf_counter()
+                e2e_s.append(t3 - t0)
+                for j, d in enumerate((t1 - t0, t2 - t1, t3 - t2)):
+                    phases[j] += d
                 e2e_updates += it * a.tau
                 d2h = x.nbytes + gaps * 9 * 8
         e2e_value, _, _ = aggregate(e2e_updates, sum(e2e_s), world)
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": 1e3 * sum(e2e_s) / len(e2e_s)}
+               "ms_per_step": 1e3 * sum(e2e_s) / len(e2e_s),
+               "ms_create_solve_finish": [round(1e3 * p / len(e2e_s), 2) for p in phases]}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

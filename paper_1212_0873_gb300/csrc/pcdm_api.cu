@@ -161,7 +161,6 @@ pcdm_status ensure_heads(pcdm_handle h, IterArgs<VT, XT> &a)
             h->head_off = true;
             return PCDM_OK;
         }
-        CK(h, cudaStreamSynchronize(h->stream));
         void *p = nullptr;
         CK(h, dalloc_bytes(&p, need));
         h->head = static_cast<unsigned char *>(p);

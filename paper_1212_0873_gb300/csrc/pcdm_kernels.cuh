@@ -1076,23 +1076,23 @@ __global__ void k_build_layout(const int64_t *__restrict__ col_ptr, const int32_
     }
 }
 
-// Column heads: the first kE row indices (zero-padded) and values of every column.
+// Column heads: the first kE row indices (zero-padded) and values of every
+// column.  Thread t fills entry t mod kE of column t / kE, so that a column's
+// reads and writes are contiguous across kE neighbouring lanes.
 template <typename VT, typename XT>
 __global__ void __launch_bounds__(kBlock) k_build_heads(const ColDesc<XT> *__restrict__ desc,
                                                         const int32_t *__restrict__ prow, const VT *__restrict__ pval,
                                                         int64_t n, unsigned char *__restrict__ head)
 {
     const int64_t stride = int64_t(gridDim.x) * kBlock;
-    for (int64_t i = int64_t(blockIdx.x) * kBlock + threadIdx.x; i < n; i += stride) {
+    for (int64_t t = int64_t(blockIdx.x) * kBlock + threadIdx.x; t < n * kE; t += stride) {
+        const int64_t i = t / kE;
+        const int e = int(t % kE);
         const Col<XT> c = load_col(desc, int32_t(i));
         unsigned char *h = head + i * head_stride<VT>();
-        int32_t *hr = reinterpret_cast<int32_t *>(h);
-        VT *hv = reinterpret_cast<VT *>(h + 4 * kE);
-        for (int e = 0; e < kE; ++e) {
-            const bool in = e < c.cnt;
-            hr[e] = in ? prow[c.pbeg + e] : 0;
-            hv[e] = in ? pval[c.pbeg + e] : VT{};
-        }
+        const bool in = e < c.cnt;
+        reinterpret_cast<int32_t *>(h)[e] = in ? prow[c.pbeg + e] : 0;
+        reinterpret_cast<VT *>(h + 4 * kE)[e] = in ? pval[c.pbeg + e] : VT{};
     }
 }
 
@@ -1311,7 +1311,7 @@ cudaError_t Kernels<VT, XT>::build_heads(const ColDesc<XT> *desc, const int32_t 
                                          unsigned char *head, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_build_heads<VT, XT><<<blocks_for_threads(n, 152 * 64), kBlock, 0, st>>>(desc, prow, pval, n, head);
+    k_build_heads<VT, XT><<<blocks_for_threads(n * kE, 152 * 64), kBlock, 0, st>>>(desc, prow, pval, n, head);
     return cudaGetLastError();
 }
 
