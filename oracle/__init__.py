@@ -1,4 +1,5 @@
-"""Plain FP64 CPU oracle for PCDM1 on LASSO (arXiv:1212.0873).
+"""Plain FP64 CPU oracle for PCDM1 (arXiv:1212.0873) on LASSO, the SVM dual and
+L2-regularised logistic regression.
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by
 the CPU-baseline leg of bench.py, never by the product package.  The arithmetic
@@ -19,6 +20,11 @@ Citations (sections, equations and tables of the paper):
   sample_independent, binomial_keep, q_independent, moments, beta_du, run_sampling
                  the tau-independent and (tau, p_b)-binomial samplings (Sec. 4.1
                  items 4 and 5) and beta of Theorem ESO-DU
+  glm_*, GlmState
+                 PCDM1 on the SVM dual (Sec. 8.3) and on L2-regularised logistic
+                 regression (Sec. 8.4): L_i, the kept vector (u or A x), the
+                 gradient, objective, duality gap, iteration and run
+                 (pcdm_oracle_glm.c)
   active_set_solution, implicit_grad
                  the LASSO optimality condition on a fixed support and sign
                  pattern, and the implicit-function derivatives of the solution
@@ -100,6 +106,23 @@ def _declare(L):
         L.pcdm_oracle_run.argtypes = [_i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _dbl, _i64,
                                       _u64, _i64, _i64, _i64, _ptr, _ptr]
         L.pcdm_oracle_run.restype = ctypes.c_int
+        _ci = ctypes.c_int
+        L.pcdm_oracle_glm_lipschitz.argtypes = [_ci, _i64, _ptr, _ptr, _dbl, _ptr]
+        L.pcdm_oracle_glm_lipschitz.restype = None
+        L.pcdm_oracle_glm_residual.argtypes = [_ci, _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _ptr]
+        L.pcdm_oracle_glm_residual.restype = None
+        L.pcdm_oracle_glm_gradient.argtypes = [_ci, _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _ptr]
+        L.pcdm_oracle_glm_gradient.restype = None
+        L.pcdm_oracle_glm_objective.argtypes = [_ci, _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl]
+        L.pcdm_oracle_glm_objective.restype = _dbl
+        L.pcdm_oracle_glm_gap.argtypes = [_ci, _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _ptr]
+        L.pcdm_oracle_glm_gap.restype = None
+        L.pcdm_oracle_glm_iteration.argtypes = [_ci, _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _dbl, _i64,
+                                                _ptr, _ptr, _ptr, _ptr, _ptr]
+        L.pcdm_oracle_glm_iteration.restype = None
+        L.pcdm_oracle_glm_run.argtypes = [_ci, _i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _dbl, _i64, _u64,
+                                          _i64, _i64, _i64, _ptr, _ptr]
+        L.pcdm_oracle_glm_run.restype = ctypes.c_int
     return L
 
 
@@ -341,3 +364,100 @@ def implicit_grad(A: Csc, x, lam, dx):
     AS = _dense_columns(A, S)
     u = np.linalg.solve(AS.T @ AS, np.asarray(dx, dtype=np.float64)[S])
     return AS @ u, float(-np.sign(x[S]) @ u)
+
+
+# ----------------------------------------------------------------------------- SVM dual and logistic
+# problem codes: 1 = dual of the L2-regularised hinge-loss SVM (Sec. 8.3),
+# 2 = L2-regularised logistic regression (Sec. 8.4); see pcdm_oracle_glm.c.
+SVM_DUAL = 1
+LOGISTIC = 2
+
+
+def glm_lipschitz(problem, A: Csc, lam):
+    L = np.zeros(max(A.n, 1))
+    lib().pcdm_oracle_glm_lipschitz(int(problem), A.n, _p(A.col_ptr), _p(A.val), float(lam), _p(L))
+    return L[: A.n]
+
+
+def glm_residual(problem, A: Csc, y, x):
+    """SVM: u = sum_i y_i x_i A_i.  Logistic: z = A x."""
+    y = _c(y, np.float64)
+    x = _c(x, np.float64)
+    v = np.zeros(max(A.m, 1))
+    lib().pcdm_oracle_glm_residual(int(problem), *A.args(), _p(y), _p(x), _p(v))
+    return v[: A.m]
+
+
+def glm_gradient(problem, A: Csc, y, v, lam):
+    y = _c(y, np.float64)
+    v = _c(v, np.float64)
+    gr = np.zeros(max(A.n, 1))
+    lib().pcdm_oracle_glm_gradient(int(problem), *A.args(), _p(y), _p(v), float(lam), _p(gr))
+    return gr[: A.n]
+
+
+def glm_objective(problem, A: Csc, y, x, lam):
+    y = _c(y, np.float64)
+    x = _c(x, np.float64)
+    return float(lib().pcdm_oracle_glm_objective(int(problem), *A.args(), _p(y), _p(x), float(lam)))
+
+
+def glm_gap(problem, A: Csc, y, x, lam):
+    """{primal, dual, gap} at x, from scratch."""
+    y = _c(y, np.float64)
+    x = _c(x, np.float64)
+    out = np.zeros(3)
+    lib().pcdm_oracle_glm_gap(int(problem), *A.args(), _p(y), _p(x), float(lam), _p(out))
+    return {"primal": float(out[0]), "dual": float(out[1]), "gap": float(out[2])}
+
+
+def glm_iteration(problem, A: Csc, y, L, lam, beta, S, x, v):
+    """One Jacobi iteration on the explicit set S (in place on x, v)."""
+    y = _c(y, np.float64)
+    L = _c(L, np.float64)
+    S = _c(S, np.int32)
+    assert x.dtype == np.float64 and x.flags.c_contiguous and v.dtype == np.float64 and v.flags.c_contiguous
+    tau = S.shape[0]
+    hb = np.zeros(max(tau, 1))
+    xb = np.zeros(max(tau, 1))
+    lib().pcdm_oracle_glm_iteration(int(problem), *A.args(), _p(y), _p(L), float(lam), float(beta), tau, _p(S),
+                                    _p(x), _p(v), _p(hb), _p(xb))
+
+
+class GlmState:
+    """Oracle state (x, v, k) of one PCDM1 run on the SVM dual or logistic regression."""
+
+    def __init__(self, problem, A: Csc, y, lam, x0=None):
+        self.problem = int(problem)
+        self.A = A
+        self.y = _c(y, np.float64)
+        self.lam = float(lam)
+        self.L = glm_lipschitz(problem, A, lam)
+        self.omega = omega(A)
+        self.x = np.zeros(A.n) if x0 is None else _c(x0, np.float64).copy()
+        self.v = glm_residual(problem, A, self.y, self.x)
+        self.k = 0
+
+    def beta(self, tau):
+        return beta_nice(self.omega, tau, self.A.n)
+
+    def run(self, tau, iters, seed, refresh_every=0, beta=None):
+        b_ = self.beta(tau) if beta is None else float(beta)
+        rc = lib().pcdm_oracle_glm_run(self.problem, *self.A.args(), _p(self.y), _p(self.L), self.lam, b_, int(tau),
+                                       int(seed) & (2**64 - 1), int(self.k), int(iters), int(refresh_every),
+                                       _p(self.x), _p(self.v))
+        if rc != 0:
+            raise ValueError("oracle run failed")
+        self.k += int(iters)
+
+    def refresh(self):
+        self.v = glm_residual(self.problem, self.A, self.y, self.x)
+
+    def gradient(self):
+        return glm_gradient(self.problem, self.A, self.y, self.v, self.lam)
+
+    def objective(self):
+        return glm_objective(self.problem, self.A, self.y, self.x, self.lam)
+
+    def gap(self):
+        return glm_gap(self.problem, self.A, self.y, self.x, self.lam)

@@ -9,7 +9,9 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "pcdm_oracle.c")
+SRC = os.path.join(HERE, "pcdm_oracle.c")              # LASSO, the samplers
+SRC_GLM = os.path.join(HERE, "pcdm_oracle_glm.c")      # SVM dual and logistic regression
+SOURCES = (SRC, SRC_GLM)
 OUT_DIR = os.path.join(HERE, "_build")
 OUT = os.path.join(OUT_DIR, "liboracle.so")
 
@@ -17,11 +19,11 @@ OUT = os.path.join(OUT_DIR, "liboracle.so")
 def build(force: bool = False) -> str:
     """Build (if stale) and return the path of the shared library."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(OUT) and all(os.path.getmtime(OUT) >= os.path.getmtime(s) for s in SOURCES):
         return OUT
     tmp = OUT + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           "-Wall", "-Wextra", SRC, "-o", tmp, "-lm"]
+           "-Wall", "-Wextra", *SOURCES, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, OUT)
     return OUT

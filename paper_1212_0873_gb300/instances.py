@@ -1,4 +1,5 @@
-"""Seeded synthetic LASSO instances (numpy only).
+"""Seeded synthetic instances (numpy only): LASSO, and labelled data for the
+SVM dual and logistic regression.
 
 This module only synthesises inputs: sparse matrices, planted solutions,
 right-hand sides and the regularisation weight.  It holds none of the method's
@@ -262,3 +263,104 @@ def small_instances(count=256, lo=1_000, hi=100_000, per_col=8, val_dtype="bf16"
     ns = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
     return [per_col_instance(2 * int(n), int(n), per_col, density=0.01, noise=0.01, lam_frac=0.1,
                              val_dtype=val_dtype, seed=seed + 1 + q) for q, n in enumerate(ns)]
+
+
+# ----------------------------------------------------------------------------- labelled data
+@dataclass
+class LabeledInstance:
+    """A sparse data matrix with +-1 labels, for the SVM dual (labels on the
+    columns: one per example) and for logistic regression (labels on the rows)."""
+    m: int
+    n: int
+    col_ptr: np.ndarray          # int64[n+1]
+    row_idx: np.ndarray          # int32[nnz], ascending within each column
+    val: np.ndarray              # stored values: float64, float32 or uint16 (bf16 bits)
+    val_dtype: str
+    val64: np.ndarray            # stored values promoted exactly to float64
+    y: np.ndarray                # float64 labels in {-1, +1}: n of them (SVM) or m (logistic)
+    lam: float
+    problem: str                 # "svm_dual" | "logistic"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self):
+        return int(self.col_ptr[-1])
+
+
+def svm_instance(d, n, per_example, lam, zipf=0.0, label_noise=0.05, val_dtype="f64", seed=1008):
+    """Data for the dual of the L2-regularised hinge-loss SVM (Sec. 8.3).
+
+    A is d x n: column i is example i.  Each example draws `per_example`
+    features with replacement, with feature r drawn with probability proportional
+    to (r + 1)^-zipf (zipf = 0: uniform); repeats are dropped, so an example has
+    at most `per_example` distinct features.  A large zipf makes a few features
+    common to many examples, which is what gives rcv1 its large omega.  Values
+    are |N(0,1)| scaled to unit norm per example (tf-idf-like, nonnegative).
+    Labels: y_i = sign(<w*, A_i>) with w* ~ N(0, I_d), each flipped with
+    probability label_noise."""
+    rng = np.random.default_rng(seed)
+    if zipf > 0:
+        cdf = np.cumsum((np.arange(d) + 1.0) ** -float(zipf))
+        cdf /= cdf[-1]
+        draws = np.minimum(np.searchsorted(cdf, rng.random((n, per_example)), side="right"), d - 1)
+    else:
+        draws = rng.integers(0, d, size=(n, per_example))
+    draws.sort(axis=1)
+    keep = np.ones(draws.shape, dtype=bool)
+    keep[:, 1:] = draws[:, 1:] != draws[:, :-1]
+    counts = keep.sum(axis=1)
+    col_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=col_ptr[1:])
+    row_idx = draws[keep].astype(np.int32)
+    del draws, keep
+    cols = np.repeat(np.arange(n, dtype=np.int64), counts)
+    val = np.abs(rng.standard_normal(row_idx.size))
+    norms = np.sqrt(np.bincount(cols, weights=val * val, minlength=n))
+    val /= norms[cols]
+    stored, val64 = _store(val, val_dtype)
+    w = rng.standard_normal(d)
+    score = np.bincount(cols, weights=val64 * w[row_idx], minlength=n)
+    y = np.where(score >= 0.0, 1.0, -1.0)
+    flip = rng.random(n) < label_noise
+    y[flip] = -y[flip]
+    meta = dict(kind="svm", per_example=per_example, zipf=zipf, label_noise=label_noise, seed=seed)
+    return LabeledInstance(m=d, n=n, col_ptr=col_ptr, row_idx=row_idx, val=stored, val_dtype=val_dtype,
+                           val64=val64, y=y, lam=float(lam), problem="svm_dual", meta=meta)
+
+
+def logistic_instance(m, n, per_row, lam=1.0, val_dtype="f64", seed=1009):
+    """Data for L2-regularised logistic regression (Sec. 8.4).
+
+    A is m x n: row j is example j, with exactly `per_row` distinct features at
+    uniform columns (so omega = per_row exactly, as the paper stresses for
+    KDDB), N(0,1)/sqrt(per_row) values.  Labels: y_j = +1 with probability
+    1/(1 + exp(-A_j^T x*)), x* ~ N(0, I_n), else -1."""
+    rng = np.random.default_rng(seed)
+    cols = _distinct_rows(rng, m, per_row, n)
+    key = cols.reshape(-1)
+    key <<= 32
+    key |= np.repeat(np.arange(m, dtype=np.int64), per_row)
+    del cols
+    key.sort()
+    cols_sorted = key >> 32
+    row_idx = (key & 0xFFFFFFFF).astype(np.int32)
+    del key
+    counts = np.bincount(cols_sorted, minlength=n)
+    col_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=col_ptr[1:])
+    val = rng.standard_normal(row_idx.size) / np.sqrt(per_row)
+    stored, val64 = _store(val, val_dtype)
+    x_star = rng.standard_normal(n)
+    margin = np.bincount(row_idx.astype(np.int64), weights=val64 * x_star[cols_sorted], minlength=m)
+    y = np.where(rng.random(m) < 1.0 / (1.0 + np.exp(-margin)), 1.0, -1.0)
+    meta = dict(kind="logistic", per_row=per_row, seed=seed)
+    return LabeledInstance(m=m, n=n, col_ptr=col_ptr, row_idx=row_idx, val=stored, val_dtype=val_dtype,
+                           val64=val64, y=y, lam=float(lam), problem="logistic", meta=meta)
+
+
+def labeled_from_dense(Adense, y, lam, problem, val_dtype="f64"):
+    """LabeledInstance from a small dense matrix (tests)."""
+    inst = from_dense(Adense, np.zeros(np.asarray(Adense).shape[0]), lam, val_dtype)
+    return LabeledInstance(m=inst.m, n=inst.n, col_ptr=inst.col_ptr, row_idx=inst.row_idx, val=inst.val,
+                           val_dtype=val_dtype, val64=inst.val64, y=np.asarray(y, dtype=np.float64),
+                           lam=float(lam), problem=problem, meta=dict(kind="dense"))

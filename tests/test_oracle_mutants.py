@@ -11,11 +11,13 @@ import shutil
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 import oracle
 from oracle import build as oracle_build
 
+from . import test_oracle_glm as Glm
 from . import test_oracle_method as M
 from . import test_oracle_sampler as Smp
 from . import test_oracle_samplings as Smv
@@ -54,6 +56,51 @@ MUTANTS = {
     "q_recursion_sign": ("ck -= binom * c[i];", "ck += binom * c[i];"),
 }
 
+# Mistakes planted in oracle/pcdm_oracle_glm.c (SVM dual and logistic regression).
+MUTANTS_GLM = {
+    "svm_L_missing_n": ("L[i] = s / (lambda * (double)n * (double)n);", "L[i] = s / (lambda * (double)n);"),
+    "svm_linear_term_sign": ("return y[i] * s / (lambda * (double)n * (double)n) - 1.0 / (double)n;",
+                             "return y[i] * s / (lambda * (double)n * (double)n) + 1.0 / (double)n;"),
+    "svm_grad_drops_label": ("return y[i] * s / (lambda * (double)n * (double)n) - 1.0 / (double)n;",
+                             "return s / (lambda * (double)n * (double)n) - 1.0 / (double)n;"),
+    "svm_no_upper_clip": ("if (x_new > 1.0) x_new = 1.0;", ";"),
+    "svm_empty_example_to_zero": ("                x_new = 1.0;\n            }", "                x_new = 0.0;\n            }"),
+    "svm_residual_drops_label": ("const double c = problem == GLM_SVM_DUAL ? y[i] * x[i] : x[i];",
+                                 "const double c = x[i];"),
+    "svm_hinge_drops_label": ("const double margin = 1.0 - y[i] * wa;", "const double margin = 1.0 - wa;"),
+    "svm_dual_value_sign": ("out[1] = sx / nn - uu / (2.0 * lambda * nn * nn);",
+                            "out[1] = sx / nn + uu / (2.0 * lambda * nn * nn);"),
+    "logistic_L_half": ("L[i] = s / 4.0;", "L[i] = s / 2.0;"),
+    "logistic_grad_sign": ("s += -y[j] * val[p] / (1.0 + exp(y[j] * v[j]));",
+                           "s += y[j] * val[p] / (1.0 + exp(y[j] * v[j]));"),
+    "logistic_exp_sign": ("s += -y[j] * val[p] / (1.0 + exp(y[j] * v[j]));",
+                          "s += -y[j] * val[p] / (1.0 + exp(-y[j] * v[j]));"),
+    "logistic_regulariser_factor": ("x_new = x[i] - (grad + 2.0 * lambda * x[i]) / (beta * L[i] + 2.0 * lambda);",
+                                    "x_new = x[i] - (grad + lambda * x[i]) / (beta * L[i] + lambda);"),
+    "logistic_no_beta": ("x_new = x[i] - (grad + 2.0 * lambda * x[i]) / (beta * L[i] + 2.0 * lambda);",
+                         "x_new = x[i] - (grad + 2.0 * lambda * x[i]) / (L[i] + 2.0 * lambda);"),
+    "logistic_entropy_sign": ("ent += -alpha * softplus(t) - (1.0 - alpha) * softplus(-t);",
+                              "ent += alpha * softplus(t) - (1.0 - alpha) * softplus(-t);"),
+    "glm_gauss_seidel": ("        xbuf[t] = x_new;\n        hbuf[t] = x_new - x[i];",
+                         "        xbuf[t] = x_new;\n        hbuf[t] = 0.0;\n"
+                         "        {\n            const double c_ = problem == GLM_SVM_DUAL ? y[i] * (x_new - x[i]) : x_new - x[i];\n"
+                         "            for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) v[row_idx[p]] += val[p] * c_;\n"
+                         "        }\n        x[i] = x_new;"),
+}
+
+PINS_GLM = [
+    Glm.test_svm_gradient_and_L_match_the_dense_dual, Glm.test_svm_gap_matches_primal_and_dual_definitions,
+    Glm.test_svm_separable_full_step_is_the_exact_dual_solution,
+    lambda: [Glm.test_svm_converges_to_the_brute_force_dual_solution(s) for s in (5, 6)],
+    Glm.test_svm_monotone_with_conservative_beta, Glm.test_svm_empty_example_goes_to_one,
+    Glm.test_svm_eso_holds_for_nice_sampling_by_enumeration,
+    Glm.test_logistic_gradient_matches_finite_differences, Glm.test_logistic_L_is_the_coordinate_lipschitz_bound,
+    lambda: Glm.test_logistic_converges_to_the_newton_solution(15), Glm.test_logistic_gap_is_the_scaled_gradient_norm,
+    Glm.test_logistic_monotone_with_conservative_beta, Glm.test_logistic_separable_fixed_point_solves_each_coordinate,
+    lambda: [Glm.test_jacobi_steps_all_start_from_the_same_point(p) for p in (oracle.SVM_DUAL, oracle.LOGISTIC)],
+    lambda: [Glm.test_step_minimises_the_model_H(p, b) for p in (oracle.SVM_DUAL, oracle.LOGISTIC) for b in (1.0, 3.7)],
+]
+
 PINS = [
     M.test_beta_printed_values, M.test_L_and_omega_match_dense_definitions, M.test_dso_tightness_construction,
     M.test_eso_holds_for_nice_sampling_by_enumeration, M.test_eso_is_tight_on_the_01_matrix,
@@ -89,8 +136,8 @@ def test_pins_catch_mutant(name, workdir):
     so_path = os.path.join(workdir, name + ".so")
     with open(c_path, "w") as f:
         f.write(mutated)
-    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", c_path, "-o", so_path,
-                    "-lm"], check=True)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", c_path, oracle_build.SRC_GLM,
+                    "-o", so_path, "-lm"], check=True)
     caught = []
     oracle.use_library(so_path)
     try:
@@ -99,6 +146,32 @@ def test_pins_catch_mutant(name, workdir):
                 pin()
             except (AssertionError, ValueError, IndexError, KeyError, FloatingPointError):
                 caught.append(getattr(pin, "__name__", "sampler pin"))
+                break
+    finally:
+        oracle.use_library(None)
+    assert caught, "no pin caught mutant " + name
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_GLM))
+def test_pins_catch_glm_mutant(name, workdir):
+    old, new = MUTANTS_GLM[name]
+    src = open(oracle_build.SRC_GLM).read()
+    assert src.count(old) >= 1, "mutation site not found: " + name
+    c_path = os.path.join(workdir, "glm_" + name + ".c")
+    so_path = os.path.join(workdir, "glm_" + name + ".so")
+    with open(c_path, "w") as f:
+        f.write(src.replace(old, new))
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", oracle_build.SRC, c_path,
+                    "-o", so_path, "-lm"], check=True)
+    caught = []
+    oracle.use_library(so_path)
+    try:
+        for pin in PINS_GLM:
+            try:
+                with np.errstate(all="raise"):
+                    pin()
+            except (AssertionError, ValueError, IndexError, KeyError, FloatingPointError, np.linalg.LinAlgError):
+                caught.append(getattr(pin, "__name__", "glm pin"))
                 break
     finally:
         oracle.use_library(None)
