@@ -150,6 +150,53 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
                         const pcdm_opts *opts, void *cuda_stream, pcdm_handle *out);
 
 /*
+ * The two other objectives the paper runs PCDM1 on, with blocks of size 1:
+ *
+ *  PCDM_PROBLEM_SVM_DUAL (Sec. 8.3): A is d x n, column i the example A_i, y in
+ *    {-1,+1}^n one label per column, lambda > 0.  Minimise the negated dual of
+ *    the L2-regularised hinge-loss SVM over the box [0,1]^n:
+ *      F(x) = 1/(2 lambda n^2) ||sum_i y_i x_i A_i||^2 - (1/n) sum_i x_i
+ *    (the paper's f with Z_ij = y_i y_j <A_i, A_j>, Psi the box indicator).
+ *    L_i = ||A_i||^2/(lambda n^2); omega = the largest number of examples sharing
+ *    a feature (row counts).  The step clips x_i - grad_i/(beta L_i) to [0, 1];
+ *    an all-zero example goes to 1.  The maintained vector is g = sum_i y_i x_i A_i
+ *    (m = d entries); the primal point is w = g/(lambda n).
+ *    pcdm_gap: primal = (1/n) sum_i max(0, 1 - y_i <w, A_i>) + lambda/2 ||w||^2,
+ *    dual = -F(x), gap = primal - dual.
+ *
+ *  PCDM_PROBLEM_LOGISTIC (Sec. 8.4): A is m x n, row j the example A_j, y in
+ *    {-1,+1}^m one label per row, lambda > 0.  Minimise
+ *      F(x) = sum_j log(1 + exp(-y_j A_j^T x)) + lambda ||x||^2.
+ *    L_i = ||a_i||^2/4 (the logistic loss has curvature at most 1/4); omega = the
+ *    largest number of features of an example.  The step is
+ *    x_i - (grad_i + 2 lambda x_i)/(beta L_i + 2 lambda).  The maintained vector
+ *    is the margins g_j = y_j A_j^T x (m entries).
+ *    pcdm_gap: primal = F(x), dual = the Fenchel dual at alpha_j = 1/(1 + exp(g_j)),
+ *    gap = primal - dual = ||grad F(x)||^2/(4 lambda).
+ *
+ * pcdm_solve stops at gap/primal <= rel_gap_tol as for LASSO.  Layout,
+ * ownership, dtypes and options are those of pcdm_create; y is n (SVM dual) or
+ * m (logistic) doubles on the host or the device as A->on_device says, copied.
+ * The labels are folded into the stored values (a sign flip, exact in every
+ * dtype), so pcdm_get_residual returns the g above; pcdm_get_L returns ||A_i||^2
+ * for the SVM dual (the paper's L_i times lambda n^2) and ||a_i||^2/4 for
+ * logistic regression.  These handles run the tau-nice sampling in the pipelined
+ * kernel (when tau fits one pass of the grid) or in the two-kernel form;
+ * pcdm_polish, pcdm_backward, pcdm_set_b and the asynchronous mode return EINVAL,
+ * and pcdm_set_tuning accepts kernels 0 and 2 only.
+ * Errors: those of pcdm_create, plus EINVAL for an unknown problem, a NULL y,
+ * lambda <= 0 or not finite, a sampling other than PCDM_SAMPLING_NICE, and a
+ * label other than -1 or +1.
+ */
+enum { PCDM_PROBLEM_LASSO = 0, PCDM_PROBLEM_SVM_DUAL = 1, PCDM_PROBLEM_LOGISTIC = 2 };
+
+pcdm_status pcdm_create_problem(const pcdm_csc *A, int32_t problem, const double *y, double lambda,
+                                const pcdm_opts *opts, void *cuda_stream, pcdm_handle *out);
+
+/* The PCDM_PROBLEM_* of a handle. */
+pcdm_status pcdm_problem_kind(pcdm_handle h, int32_t *problem);
+
+/*
  * Run `iters` iterations of Algorithm 1 (PCDM1) with the tau-nice sampling,
  * continuing the handle's iteration counter k.  S_k depends only on
  * (seed, k, n, tau), so step(a) followed by step(b) equals step(a+b).

@@ -8,6 +8,7 @@ beta of Theorem ESO-nice, on a column-stored sparse A.
   solver     Lasso: one instance resident on the GPU (numpy or torch CUDA inputs);
              BatchLasso: up to 32 right-hand sides / lambdas sharing A;
              MultiLasso: many independent small problems, one block each
+             LabeledProblem: the SVM dual (Sec. 8.3) and logistic regression (Sec. 8.4)
   instances  seeded synthetic instances (numpy only)
   build      nvcc build of libpcdm.so for sm_103a
 
@@ -20,4 +21,4 @@ from ._binding import (PCDM_BF16, PCDM_EINVAL, PCDM_F32, PCDM_F64, PcdmError, pc
                        pcdm_refresh, pcdm_reset, pcdm_reset_stats, pcdm_sample, pcdm_selftest_barrier_timeout,
                        pcdm_set_iteration, pcdm_set_lambda, pcdm_set_x, pcdm_solve, pcdm_stats,
                        pcdm_status_string, pcdm_step)
-from .solver import BatchLasso, Lasso, MultiLasso, current_stream  # noqa: F401
+from .solver import BatchLasso, LabeledProblem, Lasso, MultiLasso, current_stream  # noqa: F401

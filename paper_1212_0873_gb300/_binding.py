@@ -46,6 +46,9 @@ SIGNATURES = {
     "pcdm_default_opts": (None, [ctypes.POINTER(pcdm_opts)]),
     "pcdm_create": (_i32, [ctypes.POINTER(pcdm_csc), _ptr, _i32, _dbl, ctypes.POINTER(pcdm_opts), _ptr,
                            ctypes.POINTER(_ptr)]),
+    "pcdm_create_problem": (_i32, [ctypes.POINTER(pcdm_csc), _i32, _ptr, _dbl, ctypes.POINTER(pcdm_opts), _ptr,
+                                   ctypes.POINTER(_ptr)]),
+    "pcdm_problem_kind": (_i32, [_ptr, ctypes.POINTER(_i32)]),
     "pcdm_step": (_i32, [_ptr, _i64, _i64, _u64]),
     "pcdm_refresh": (_i32, [_ptr]),
     "pcdm_gap": (_i32, [_ptr, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
@@ -154,6 +157,24 @@ def pcdm_create(A, b_ptr, b_dtype, lam, opts=None, stream=0):
                            ctypes.byref(opts) if opts is not None else None, _stream(stream), ctypes.byref(h))
     _check(st, None)
     return h
+
+
+PROBLEM_CODES = {"lasso": 0, "svm_dual": 1, "logistic": 2}
+
+
+def pcdm_create_problem(A, problem, y_ptr, lam, opts=None, stream=0):
+    h = _ptr()
+    st = lib().pcdm_create_problem(ctypes.byref(A), int(PROBLEM_CODES[problem]), _ptr(y_ptr), float(lam),
+                                   ctypes.byref(opts) if opts is not None else None, _stream(stream),
+                                   ctypes.byref(h))
+    _check(st, None)
+    return h
+
+
+def pcdm_problem_kind(h):
+    v = _i32()
+    _check(lib().pcdm_problem_kind(h, ctypes.byref(v)), h)
+    return {c: k for k, c in PROBLEM_CODES.items()}[v.value]
 
 
 def pcdm_step(h, tau, iters, seed):

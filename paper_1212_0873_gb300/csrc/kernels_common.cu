@@ -264,6 +264,131 @@ cudaError_t launch_gap_finish(const double *pc, int nbc, const double *pr, int n
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// SVM dual and logistic regression.
+__global__ void k_check_labels(const double *y, int64_t count, int *flags)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int f = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride)
+        if (!(y[i] == 1.0 || y[i] == -1.0)) f = FLAG_LABEL;
+    if (f) atomicOr(flags, f);
+}
+
+cudaError_t launch_check_labels(const double *y, int64_t count, int *flags, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    k_check_labels<<<grid_for(count), 256, 0, st>>>(y, count, flags);
+    return cudaGetLastError();
+}
+
+__global__ void k_scale(double *v, int64_t count, double factor)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += stride) v[i] *= factor;
+}
+
+cudaError_t launch_scale(double *v, int64_t count, double factor, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    k_scale<<<grid_for(count), 256, 0, st>>>(v, count, factor);
+    return cudaGetLastError();
+}
+
+// log(1 + e^t) without overflow.
+__device__ __forceinline__ double softplus(double t)
+{
+    return t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t));
+}
+
+__global__ void __launch_bounds__(kBlock) k_glm_gap_rows(int problem, const double *__restrict__ r, int64_t m,
+                                                         double *__restrict__ part)
+{
+    const int64_t stride = int64_t(gridDim.x) * kBlock;
+    double s = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * kBlock + threadIdx.x; i < m; i += stride) {
+        const double ri = r[i];
+        s += problem == 1 ? ri * ri : softplus(-ri);
+    }
+    __shared__ double sm[kBlock / 32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int q = 0; q < kBlock / 32; ++q) a += sm[q];
+        part[2 * blockIdx.x + 0] = a;
+        part[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+cudaError_t launch_glm_gap_rows(int problem, const double *r, int64_t m, double *part, int blocks, cudaStream_t st)
+{
+    k_glm_gap_rows<<<blocks, kBlock, 0, st>>>(problem, r, m, part);
+    return cudaGetLastError();
+}
+
+// SVM dual (Sec. 8.3), rows = ||r||^2 = ||u||^2, w = u/(lambda n):
+//   P = t2/n + ||u||^2/(2 lambda n^2)  (hinge loss + lambda/2 ||w||^2),
+//   D = t3/n - ||u||^2/(2 lambda n^2)  (= -f(x)),   gap = t1/n.
+// Logistic (Sec. 8.4), rows = sum_r log(1 + exp(-margin_r)):
+//   P = rows + lambda t2,  gap = t1/(4 lambda) (the Fenchel gap at
+//   alpha_r = 1/(1 + exp(margin_r)) equals ||grad F||^2/(4 lambda)),  D = P - gap.
+__global__ void __launch_bounds__(kFinishBlock) k_glm_gap_finish(int problem, const double *pc, int nbc,
+                                                                 const double *pr, int nbr, double lambda, int64_t n,
+                                                                 double *out)
+{
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0, rows = 0.0;
+    for (int q = threadIdx.x; q < nbc; q += kFinishBlock) {
+        t1 += pc[3 * q + 0];
+        t2 += pc[3 * q + 1];
+        t3 += pc[3 * q + 2];
+    }
+    for (int q = threadIdx.x; q < nbr; q += kFinishBlock) rows += pr[2 * q + 0];
+    __shared__ double sm[4][kFinishBlock / 32];
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    t3 = warp_sum(t3);
+    rows = warp_sum(rows);
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        sm[0][w] = t1;
+        sm[1][w] = t2;
+        sm[2][w] = t3;
+        sm[3][w] = rows;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < kFinishBlock / 32; ++w)
+            for (int q = 0; q < 4; ++q) a[q] += sm[q][w];
+        const double nn = double(n);
+        if (problem == 1) {
+            const double quad = a[3] / (2.0 * lambda * nn * nn);
+            out[0] = a[1] / nn + quad;
+            out[1] = a[2] / nn - quad;
+            out[2] = a[0] / nn;
+        } else {
+            out[0] = a[3] + lambda * a[1];
+            out[2] = a[0] / (4.0 * lambda);
+            out[1] = out[0] - out[2];
+        }
+        out[3] = a[0];
+        out[4] = a[1];
+        out[5] = a[2];
+        out[6] = a[3];
+        out[7] = 0.0;
+        out[8] = 0.0;
+    }
+}
+
+cudaError_t launch_glm_gap_finish(int problem, const double *pc, int nbc, const double *pr, int nbr, double lambda,
+                                  int64_t n, double *out, cudaStream_t st)
+{
+    k_glm_gap_finish<<<1, kFinishBlock, 0, st>>>(problem, pc, nbc, pr, nbr, lambda, n, out);
+    return cudaGetLastError();
+}
+
 // Support of x in increasing index order, by one block: each pass takes
 // kBlock entries, the block's ballots give every nonzero its rank.
 __global__ void __launch_bounds__(kBlock) k_compact_support(const double *__restrict__ x, int64_t n,

@@ -93,6 +93,8 @@ IterArgs<VT, XT> iter_args(pcdm_handle h, int64_t tau, uint64_t seed)
     a.win = h->win;
     a.head = h->head;
     a.lambda = h->lambda;
+    a.problem = h->problem;
+    a.kappa = h->lambda * double(h->n);
     a.n = h->n;
     a.tau = tau;
     a.seed = seed;
@@ -145,6 +147,16 @@ bool pipe_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads = 0
     sh->blocks = int(blocks);
     sh->threads = int(threads);
     return true;
+}
+
+// Whether the pipelined kernel takes tau with the handle's tuning (the kernels
+// other than it and the two-kernel form do not run the SVM dual or logistic regression).
+template <typename VT, typename XT>
+bool pipe_fits(pcdm_handle h, int64_t tau)
+{
+    if (h->tune_kernel != -1 && h->tune_kernel != 0) return false;
+    FusedShape sh;
+    return pipe_shape<VT, XT>(h, tau, &sh, h->tune_kernel == 0 ? h->tune_threads : 0);
 }
 
 // The per-column heads of the pipelined kernels, built on their first use.
@@ -206,7 +218,9 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         h->g2_valid = false;
         h->st_launches += iters;
         h->st_kernels += 3 * iters;
-    } else if (h->opts.fused && h->tune_kernel != 2) {
+    } else if (h->opts.fused && h->tune_kernel != 2 &&
+               (h->problem == PCDM_PROBLEM_LASSO || pipe_fits<VT, XT>(h, tau))) {
+        // (the SVM dual and logistic regression run in the pipelined kernel or the two-kernel form)
         FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
         const bool pipe = (h->tune_kernel == 1 || h->tune_kernel == 3)
@@ -308,11 +322,21 @@ pcdm_status gap_t(pcdm_handle h)
     if (s != PCDM_OK) return s;
     double *part_c = h->gap_part;
     double *part_r = h->gap_part + 3 * h->gap_blocks;
-    CK(h, Kernels<VT, XT>::gap_cols(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
-                                    static_cast<const VT *>(h->pval), h->g64, static_cast<const double *>(h->x), h->n,
-                                    part_c, h->gap_blocks, h->W, h->stream));
-    CK(h, launch_gap_rows(h->g64, h->b, h->m, part_r, h->gap_row_blocks, h->stream));
-    CK(h, launch_gap_finish(part_c, h->gap_blocks, part_r, h->gap_row_blocks, h->gap_out, h->lambda, h->stream));
+    if (h->problem == PCDM_PROBLEM_LASSO) {
+        CK(h, Kernels<VT, XT>::gap_cols(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
+                                        static_cast<const VT *>(h->pval), h->g64, static_cast<const double *>(h->x),
+                                        h->n, part_c, h->gap_blocks, h->W, h->stream));
+        CK(h, launch_gap_rows(h->g64, h->b, h->m, part_r, h->gap_row_blocks, h->stream));
+        CK(h, launch_gap_finish(part_c, h->gap_blocks, part_r, h->gap_row_blocks, h->gap_out, h->lambda, h->stream));
+    } else {
+        CK(h, Kernels<VT, XT>::glm_gap_cols(h->problem, static_cast<const ColDesc<XT> *>(h->desc), h->prow,
+                                            static_cast<const VT *>(h->pval), h->g64,
+                                            static_cast<const double *>(h->x), h->n, h->lambda,
+                                            h->lambda * double(h->n), part_c, h->gap_blocks, h->W, h->stream));
+        CK(h, launch_glm_gap_rows(h->problem, h->g64, h->m, part_r, h->gap_row_blocks, h->stream));
+        CK(h, launch_glm_gap_finish(h->problem, part_c, h->gap_blocks, part_r, h->gap_row_blocks, h->lambda, h->n,
+                                    h->gap_out, h->stream));
+    }
     CK(h, cudaMemcpyAsync(h->host_buf, h->gap_out, 9 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     h->st_gaps += 1;
     h->st_kernels += 3;
@@ -391,12 +415,18 @@ const char *pcdm_status_string(pcdm_status s)
 
 const char *pcdm_last_error(pcdm_handle h) { return h ? h->err.c_str() : g_free_error.c_str(); }
 
-pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, double lambda, const pcdm_opts *opts,
-                        void *cuda_stream, pcdm_handle *out)
+}  // extern "C"
+
+namespace {
+
+// pcdm_create (problem 0, b given) and pcdm_create_problem (problems 1 and 2:
+// b = 0 and the labels y folded into the stored values).
+pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, double lambda, const pcdm_opts *opts,
+                        void *cuda_stream, pcdm_handle *out, int problem, const double *y)
 {
     if (!out) return set_err(nullptr, PCDM_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!A || !b) return set_err(nullptr, PCDM_EINVAL, "A or b is NULL");
+    if (!A || (!b && problem == PCDM_PROBLEM_LASSO)) return set_err(nullptr, PCDM_EINVAL, "A or b is NULL");
     pcdm_opts o;
     pcdm_default_opts(&o);
     if (opts) o = *opts;
@@ -428,6 +458,7 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     h->val_dtype = A->val_dtype;
     h->xg_dtype = o.xg_dtype;
     h->lambda = lambda;
+    h->problem = problem;
     h->opts = o;
     h->W = o.lanes_per_col ? int(o.lanes_per_col) : auto_lanes(A->nnz, A->n);
 
@@ -474,9 +505,10 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         int32_t *row_idx = nullptr;
         void *val = nullptr;
         int *rowcnt = nullptr;
+        double *y = nullptr;
         ~Staging()
         {
-            void *p[] = {col_ptr, pbeg, tile, row_idx, val, rowcnt};
+            void *p[] = {col_ptr, pbeg, tile, row_idx, val, rowcnt, y};
             for (void *q : p)
                 if (q) cudaFree(q);
         }
@@ -491,7 +523,12 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         CKC(cudaMemcpyAsync(stg.row_idx, A->row_idx, size_t(h->nnz) * sizeof(int32_t), kin, st));
         CKC(cudaMemcpyAsync(stg.val, A->val, size_t(h->nnz * vb), kin, st));
     }
-    if (b_dtype == PCDM_F64) {
+    const int64_t ny = problem == PCDM_PROBLEM_SVM_DUAL ? h->n : h->m;   // labels: one per example
+    if (problem != PCDM_PROBLEM_LASSO) {
+        CKC(cudaMemsetAsync(h->b, 0, size_t(h->m) * sizeof(double), st));
+        CKC(dalloc(&stg.y, ny));
+        CKC(cudaMemcpyAsync(stg.y, y, size_t(ny) * sizeof(double), kin, st));
+    } else if (b_dtype == PCDM_F64) {
         CKC(cudaMemcpyAsync(h->b, b, size_t(h->m) * sizeof(double), kin, st));
     } else {
         // Stage the FP32 b in the g buffer (at least m floats) and widen it.
@@ -528,6 +565,8 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         break;
     }
     CKC(launch_check_finite(h->b, h->m, flags, st));
+    if (problem != PCDM_PROBLEM_LASSO) CKC(launch_check_labels(stg.y, ny, flags, st));
+    if (problem == PCDM_PROBLEM_LOGISTIC) CKC(launch_scale(h->L64, h->n, 0.25, st));   // L_i = ||a_i||^2 / 4
     CKC(launch_max_int(stg.rowcnt, h->m, omega_dev, st));
     CKC(cudaMemcpyAsync(hflags, flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
@@ -539,6 +578,7 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
             if (f & FLAG_ROW_ORDER) msg += " rows of a column not strictly increasing;";
             if (f & FLAG_NONFINITE) msg += " non-finite value in A;";
             if (f & FLAG_B_NONFINITE) msg += " non-finite value in b;";
+            if (f & FLAG_LABEL) msg += " a label other than -1 or +1;";
             h->err = msg;
             return fail(PCDM_EINVAL);
         }
@@ -580,6 +620,22 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
                                                  h->prow, static_cast<bf16_t *>(h->pval), st));
         break;
     }
+    if (problem != PCDM_PROBLEM_LASSO) {
+        switch (h->val_dtype) {
+        case PCDM_F64:
+            CKC(Kernels<double, double>::apply_labels(problem, static_cast<const ColDesc<double> *>(h->desc), h->prow,
+                                                      static_cast<double *>(h->pval), h->n, stg.y, st));
+            break;
+        case PCDM_F32:
+            CKC(Kernels<float, float>::apply_labels(problem, static_cast<const ColDesc<float> *>(h->desc), h->prow,
+                                                    static_cast<float *>(h->pval), h->n, stg.y, st));
+            break;
+        default:
+            CKC(Kernels<bf16_t, float>::apply_labels(problem, static_cast<const ColDesc<float> *>(h->desc), h->prow,
+                                                     static_cast<bf16_t *>(h->pval), h->n, stg.y, st));
+            break;
+        }
+    }
     CKC(cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st));
     {
         pcdm_status s = reset_state(h);
@@ -588,6 +644,38 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     CKC(cudaStreamSynchronize(st));
 #undef CKC
     *out = h;
+    return PCDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, double lambda, const pcdm_opts *opts,
+                        void *cuda_stream, pcdm_handle *out)
+{
+    return create_impl(A, b, b_dtype, lambda, opts, cuda_stream, out, PCDM_PROBLEM_LASSO, nullptr);
+}
+
+pcdm_status pcdm_create_problem(const pcdm_csc *A, int32_t problem, const double *y, double lambda,
+                                const pcdm_opts *opts, void *cuda_stream, pcdm_handle *out)
+{
+    if (out) *out = nullptr;
+    if (problem != PCDM_PROBLEM_SVM_DUAL && problem != PCDM_PROBLEM_LOGISTIC)
+        return set_err(nullptr, PCDM_EINVAL, "problem must be PCDM_PROBLEM_SVM_DUAL or PCDM_PROBLEM_LOGISTIC");
+    if (!y) return set_err(nullptr, PCDM_EINVAL, "y is NULL");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return set_err(nullptr, PCDM_EINVAL, "lambda must be finite and > 0");
+    if (opts && opts->sampling != PCDM_SAMPLING_NICE)
+        return set_err(nullptr, PCDM_EINVAL, "the SVM dual and logistic regression take the tau-nice sampling");
+    return create_impl(A, nullptr, PCDM_F64, lambda, opts, cuda_stream, out, problem, y);
+}
+
+pcdm_status pcdm_problem_kind(pcdm_handle h, int32_t *problem)
+{
+    pcdm_status s = usable(h);
+    if (s != PCDM_OK) return s;
+    if (!problem) return set_err(h, PCDM_EINVAL, "problem is NULL");
+    *problem = h->problem;
     return PCDM_OK;
 }
 
@@ -750,6 +838,8 @@ pcdm_status pcdm_set_lambda(pcdm_handle h, double lambda)
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
     if (!(lambda >= 0.0) || !std::isfinite(lambda)) return set_err(h, PCDM_EINVAL, "lambda must be finite and >= 0");
+    if (h->problem != PCDM_PROBLEM_LASSO && !(lambda > 0.0))
+        return set_err(h, PCDM_EINVAL, "the SVM dual and logistic regression need lambda > 0");
     h->lambda = lambda;
     return PCDM_OK;
 }
@@ -998,6 +1088,7 @@ pcdm_status pcdm_polish(pcdm_handle h, int64_t tau, uint64_t seed, double tol, i
 {
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
+    if (h->problem != PCDM_PROBLEM_LASSO) return set_err(h, PCDM_EINVAL, "pcdm_polish applies to LASSO handles only");
     if (tau < 0 || max_iters < 0 || !(tol >= 0.0)) return set_err(h, PCDM_EINVAL, "bad tau, max_iters or tol");
     return dispatch(h, [&](auto *vt, auto *xt) {
         using VT = std::remove_pointer_t<decltype(vt)>;
@@ -1012,6 +1103,7 @@ pcdm_status pcdm_backward(pcdm_handle h, const double *dx, int32_t dx_on_device,
 {
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
+    if (h->problem != PCDM_PROBLEM_LASSO) return set_err(h, PCDM_EINVAL, "pcdm_backward applies to LASSO handles only");
     if (!dx) return set_err(h, PCDM_EINVAL, "dx is NULL");
     if (tau < 0 || max_iters < 0 || !(tol >= 0.0)) return set_err(h, PCDM_EINVAL, "bad tau, max_iters or tol");
     s = ensure_as(h, 1);
@@ -1042,6 +1134,7 @@ pcdm_status pcdm_set_b(pcdm_handle h, const void *b, int32_t b_dtype, int32_t on
 {
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
+    if (h->problem != PCDM_PROBLEM_LASSO) return set_err(h, PCDM_EINVAL, "pcdm_set_b applies to LASSO handles only");
     if (!b) return set_err(h, PCDM_EINVAL, "b is NULL");
     if (b_dtype != PCDM_F64 && b_dtype != PCDM_F32) return set_err(h, PCDM_EINVAL, "b_dtype must be F64 or F32");
     cudaStream_t st = h->stream;
@@ -1180,6 +1273,7 @@ pcdm_status pcdm_step_async(pcdm_handle h, int64_t updates, uint64_t seed, int32
 {
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
+    if (h->problem != PCDM_PROBLEM_LASSO) return set_err(h, PCDM_EINVAL, "pcdm_step_async applies to LASSO handles only");
     if (updates < 0 || threads < 0) return set_err(h, PCDM_EINVAL, "updates and threads must be >= 0");
     if (updates == 0) return PCDM_OK;
     s = dispatch(h, [&](auto *vt, auto *xt) {
@@ -1196,6 +1290,7 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
 {
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
+    if (h->problem != PCDM_PROBLEM_LASSO) return set_err(h, PCDM_EINVAL, "pcdm_solve_async applies to LASSO handles only");
     if (max_updates < 0 || threads < 0 || !(rel_gap_tol >= 0.0))
         return set_err(h, PCDM_EINVAL, "bad max_updates, threads or tolerance");
     const int64_t epoch = h->n;   // updates between the first checks
@@ -1238,6 +1333,8 @@ pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
         return PCDM_OK;
     }
     if (t->heads != 0 && t->heads != 1) return set_err(h, PCDM_EINVAL, "heads must be 0 or 1");
+    if (h->problem != PCDM_PROBLEM_LASSO && (t->kernel == 1 || t->kernel == 3))
+        return set_err(h, PCDM_EINVAL, "the SVM dual and logistic regression run in kernels 0 and 2 only");
     const bool lanes_ok = t->lanes_per_col == 1 || t->lanes_per_col == 2 || t->lanes_per_col == 4 ||
                           t->lanes_per_col == 8 || t->lanes_per_col == 16 || t->lanes_per_col == 32;
     if (t->kernel < 0 || t->kernel > 3 || !lanes_ok)
@@ -1318,6 +1415,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
             if (!ok) continue;
         }
         if (c.kernel == 0 && c.heads && h->head_off) continue;   // the heads do not fit
+        if (h->problem != PCDM_PROBLEM_LASSO && (c.kernel == 1 || c.kernel == 3)) continue;
         h->tune_kernel = c.kernel;
         h->tune_W = c.W;
         h->tune_threads = c.threads;

@@ -42,6 +42,7 @@ struct pcdm_ctx {
     int64_t m = 0, n = 0, nnz = 0;
     int val_dtype = PCDM_F64, xg_dtype = PCDM_F64;
     double lambda = 0.0;
+    int problem = 0;              // PCDM_PROBLEM_*: LASSO, SVM dual, logistic regression
     pcdm_opts opts{};
     int W = 8;
     int sms = 0;

@@ -85,6 +85,11 @@ struct IterArgs {
     // separately): column i's first kLaneRun row indices at head + i * stride,
     // its first kLaneRun values 64 bytes further.
     const unsigned char *head;
+    // Objective: 0 LASSO, 1 SVM dual (Sec. 8.3), 2 logistic regression (Sec. 8.4);
+    // kappa = lambda n for the SVM dual (the linear term in the scale of ||a_i||^2).
+    // Only the two-kernel form and the pipelined kernel take problems 1 and 2.
+    int problem;
+    double kappa;
 };
 
 // Bytes of one column head: kLaneRun row indices, then kLaneRun values.
@@ -141,6 +146,14 @@ struct Kernels {
     // Per-block partials (max |c_i|, sum |x_i|, sum x_i c_i), c = A^T r.
     static cudaError_t gap_cols(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, const double *r,
                                 const double *x, int64_t n, double *part, int blocks, int W, cudaStream_t st);
+    // The same for the SVM dual (problem 1) and logistic regression (problem 2):
+    // three per-block sums each (see k_glm_gap_cols).
+    static cudaError_t glm_gap_cols(int problem, const ColDesc<XT> *desc, const int32_t *prow, const VT *pval,
+                                    const double *r, const double *x, int64_t n, double lambda, double kappa,
+                                    double *part, int blocks, int W, cudaStream_t st);
+    // Sign the stored values by the labels y (problem 1: y_i on column i; 2: y_r on row r).
+    static cudaError_t apply_labels(int problem, const ColDesc<XT> *desc, const int32_t *prow, VT *pval, int64_t n,
+                                    const double *y, cudaStream_t st);
 };
 
 template <typename VT, typename XT>
@@ -258,6 +271,16 @@ cudaError_t launch_f64_to_f32(float *dst, const double *src, int64_t count, cuda
 cudaError_t launch_gap_rows(const double *r, const double *b, int64_t m, double *part, int blocks, cudaStream_t st);
 cudaError_t launch_gap_finish(const double *pc, int nbc, const double *pr, int nbr, double *out, double lambda,
                               cudaStream_t st);
+// SVM dual and logistic regression (problems 1 and 2): flag labels other than
+// +-1; scale v by a constant; rows part of the gap (block partials of ||r||^2
+// for the SVM dual, of sum_r log(1 + exp(-r_r)) for logistic regression); and
+// the record out = {P, D, gap, t1, t2, t3, rows, 0, 0} from the column
+// partials t of k_glm_gap_cols (n = number of columns).
+cudaError_t launch_check_labels(const double *y, int64_t count, int *flags, cudaStream_t st);
+cudaError_t launch_scale(double *v, int64_t count, double factor, cudaStream_t st);
+cudaError_t launch_glm_gap_rows(int problem, const double *r, int64_t m, double *part, int blocks, cudaStream_t st);
+cudaError_t launch_glm_gap_finish(int problem, const double *pc, int nbc, const double *pr, int nbr, double lambda,
+                                  int64_t n, double *out, cudaStream_t st);
 cudaError_t launch_barrier_selftest(unsigned long long *bar, int *status, uint64_t timeout_ns, int blocks,
                                     cudaStream_t st);
 // Exclusive scan of the padded column lengths: pbeg[i] = sum_{q<i} roundup(cnt_q, granule),
@@ -279,7 +302,8 @@ enum : int {
     FLAG_ROW_RANGE = 2,   // a row index outside [0, m)
     FLAG_ROW_ORDER = 4,   // rows of a column not strictly increasing
     FLAG_NONFINITE = 8,   // a non-finite value in A
-    FLAG_B_NONFINITE = 16 // a non-finite value in b
+    FLAG_B_NONFINITE = 16,// a non-finite value in b
+    FLAG_LABEL = 32       // a label other than -1 or +1
 };
 
 }  // namespace pcdm

@@ -224,8 +224,24 @@ __device__ __forceinline__ void ld_chunk(Chunk<E, XT> &c, const int32_t *prow, c
     ld_vals<E>(c.val, pval + p);
 }
 
-// sum_e val[e] * v[row[e]] over the first `valid` entries of the lane's run.
-template <int E, typename XT, typename GT, typename AT>
+// The coordinate gradient of the smooth part is grad_i = sum_r a_ri phi(g_r).
+// GM = 0: phi is the identity (the square losses: LASSO with g = A x - b, the
+// SVM dual with g = A x for the label-signed examples).  GM = 1: the logistic
+// loss (Sec. 8.4), g holds the margins y_r A_r^T x (labels folded into the
+// rows) and phi(t) = d/dt log(1 + e^-t) = -1/(1 + e^t).
+template <int GM, typename T>
+__device__ __forceinline__ T grad_map(T v)
+{
+    if constexpr (GM == 0)
+        return v;
+    else if constexpr (sizeof(T) == 8)
+        return -1.0 / (1.0 + exp(v));
+    else
+        return -1.0f / (1.0f + expf(v));
+}
+
+// sum_e val[e] * phi(v[row[e]]) over the first `valid` entries of the lane's run.
+template <int E, typename XT, typename GT, typename AT, int GM = 0>
 __device__ __forceinline__ AT chunk_dot(const Chunk<E, XT> &c, const GT *v, int valid)
 {
     GT gv[E];
@@ -234,7 +250,7 @@ __device__ __forceinline__ AT chunk_dot(const Chunk<E, XT> &c, const GT *v, int 
     AT acc = AT(0);
 #pragma unroll
     for (int e = 0; e < E; ++e)
-        if (e < valid) acc = fma(AT(c.val[e]), AT(gv[e]), acc);
+        if (e < valid) acc = fma(AT(c.val[e]), AT(grad_map<GM>(gv[e])), acc);
     return acc;
 }
 
@@ -254,7 +270,7 @@ __device__ __forceinline__ void chunk_scatter_hint(const Chunk<E, XT> &c, XT *g,
         if (e < valid) red_add(g + c.row[e], c.val[e] * h, pol);
 }
 
-template <int E, typename XT, typename GT = XT>
+template <int E, typename XT, typename GT = XT, int GM = 0>
 __device__ __forceinline__ GT chunk_dot_hint(const Chunk<E, XT> &c, const GT *v, int valid, uint64_t pol)
 {
     GT gv[E];
@@ -263,12 +279,12 @@ __device__ __forceinline__ GT chunk_dot_hint(const Chunk<E, XT> &c, const GT *v,
     GT acc = GT(0);
 #pragma unroll
     for (int e = 0; e < E; ++e)
-        if (e < valid) acc = fma(GT(c.val[e]), gv[e], acc);
+        if (e < valid) acc = fma(GT(c.val[e]), grad_map<GM>(gv[e]), acc);
     return acc;
 }
 
-// a_i^T g over a whole column, chunk by chunk (all W lanes of the group together).
-template <int W, typename VT, typename XT>
+// a_i^T phi(g) over a whole column, chunk by chunk (all W lanes of the group together).
+template <int W, typename VT, typename XT, int GM = 0>
 __device__ __forceinline__ XT column_dot(const IterArgs<VT, XT> &a, const Col<XT> &c, int lane, unsigned gmask)
 {
     constexpr int CH = W * kE;
@@ -277,7 +293,7 @@ __device__ __forceinline__ XT column_dot(const IterArgs<VT, XT> &a, const Col<XT
         Chunk<kE, XT> t;
         const int st = cs + lane * kE;
         if (st < c.cnt) ld_chunk<kE>(t, a.prow, a.pval, c.pbeg + st);
-        acc += chunk_dot<kE, XT, XT, XT>(t, a.g, c.cnt - st);
+        acc += chunk_dot<kE, XT, XT, XT, GM>(t, a.g, c.cnt - st);
     }
     return group_sum<W>(acc, gmask);
 }
@@ -309,8 +325,30 @@ __device__ __forceinline__ double prox_step(double xi, double grad, double invL,
     return soft_threshold<double>(fma(-grad, ibl, xi), lambda * ibl);
 }
 
+// The new coordinate for each objective (argmin over t of the model of eq.
+// (h(x)): grad_i t + (beta L_i / 2) t^2 + Psi_i(x_i + t)), from grad = a_i^T phi(g):
+//   problem 0, LASSO: prox_step above.
+//   problem 1, SVM dual (Sec. 8.3), Psi the indicator of [0, 1]: with the examples
+//     signed by their labels and 1/L stored as 1/||a_i||^2, the paper's
+//     grad_i/(beta L_i) = (a_i^T g - kappa)/(beta ||a_i||^2), kappa = lambda n;
+//     the step is clip(x_i - that, 0, 1); an all-zero example goes to 1.
+//   problem 2, logistic (Sec. 8.4), Psi_i = lambda x_i^2, 1/L stored as 4/||a_i||^2:
+//     x_i - (grad + 2 lambda x_i)/(beta L_i + 2 lambda).
+__device__ __forceinline__ double coord_step(int problem, double xi, double grad, double invL, double inv_beta,
+                                             double lambda, double kappa)
+{
+    if (problem == 0) return prox_step(xi, grad, invL, inv_beta, lambda);
+    if (problem == 1) {
+        if (invL == 0.0) return 1.0;
+        const double u = fma(-(grad - kappa), invL * inv_beta, xi);
+        return fmin(fmax(u, 0.0), 1.0);
+    }
+    const double bl = invL == 0.0 ? 0.0 : 1.0 / (invL * inv_beta);
+    return xi - fma(2.0 * lambda, xi, grad) / (bl + 2.0 * lambda);
+}
+
 // Phase 1 for sampled position j, columns read from memory (no prefetch).
-template <int W, typename VT, typename XT>
+template <int W, typename VT, typename XT, int GM = 0>
 __device__ __forceinline__ void gather_generic(const IterArgs<VT, XT> &a, const int32_t *S, int64_t j, int lane,
                                                unsigned gmask, Counters &cnt, int64_t k = -1)
 {
@@ -327,8 +365,8 @@ __device__ __forceinline__ void gather_generic(const IterArgs<VT, XT> &a, const 
     }
     const Col<XT> c = load_col(a.desc, i);
     const double xi = ldcg(a.x + i);
-    const XT grad = column_dot<W>(a, c, lane, gmask);
-    const double xn = prox_step(xi, double(grad), double(c.invL), a.inv_beta, a.lambda);
+    const XT grad = column_dot<W, VT, XT, GM>(a, c, lane, gmask);
+    const double xn = coord_step(a.problem, xi, double(grad), double(c.invL), a.inv_beta, a.lambda, a.kappa);
     const double h64 = xn - xi;
     if (lane == 0) {
         if (h64 != 0.0) a.x[i] = xn;
@@ -353,14 +391,14 @@ __device__ __forceinline__ void scatter_generic(const IterArgs<VT, XT> &a, const
 
 // ---------------------------------------------------------------------------
 // Two-kernel form.
-template <int W, typename VT, typename XT>
+template <int W, typename VT, typename XT, int GM = 0>
 __global__ void __launch_bounds__(kBlock) k_gather(const IterArgs<VT, XT> a, int64_t k)
 {
     const int lane = threadIdx.x & (W - 1);
     const unsigned gmask = group_mask<W>(threadIdx.x & 31);
     const int64_t grp = (int64_t(blockIdx.x) * kBlock + threadIdx.x) / W;
     Counters cnt;
-    if (grp < a.tau) gather_generic<W>(a, sample_buf(a, k), grp, lane, gmask, cnt, k);
+    if (grp < a.tau) gather_generic<W, VT, XT, GM>(a, sample_buf(a, k), grp, lane, gmask, cnt, k);
     flush_counters(cnt, a.counters);
 }
 
@@ -578,7 +616,7 @@ __device__ __forceinline__ void slot_scatter(const IterArgs<VT, XT> &a, const un
     }
 }
 
-template <typename VT, typename XT>
+template <typename VT, typename XT, int GM = 0>
 __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -695,17 +733,17 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                 decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
 #pragma unroll
                 for (int q = 0; q < EPW; ++q)
-                    if (w * EPW + q < valid) acc = fma(vw[q], gv[w * EPW + q], acc);
+                    if (w * EPW + q < valid) acc = fma(vw[q], grad_map<GM>(gv[w * EPW + q]), acc);
             }
 #pragma unroll
             for (int e = 0; e < kT; ++e)
-                if (kE + e < valid) acc = fma(tl.val[e], gt[e], acc);
+                if (kE + e < valid) acc = fma(tl.val[e], grad_map<GM>(gt[e]), acc);
             for (int cs = kE + kT; cs < valid; cs += kE) {
                 Chunk<kE, XT> tc;
                 ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
-                acc += chunk_dot_hint<kE, XT>(tc, gk, valid - cs, pl);
+                acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
             }
-            const double xn = prox_step(xi, double(acc), double(d_cur.invL), a.inv_beta, a.lambda);
+            const double xn = coord_step(a.problem, xi, double(acc), double(d_cur.invL), a.inv_beta, a.lambda, a.kappa);
             const double h64 = xn - xi;
             h = XT(h64);
             if (h64 != 0.0) st_hint(a.x + i_cur, xn, pf);   // most steps are zero: x_i unchanged
@@ -1178,6 +1216,108 @@ __global__ void __launch_bounds__(kBlock) k_gap_cols(const ColDesc<XT> *__restri
     }
 }
 
+// Gap of the SVM dual and of logistic regression, column part (FP64, r = the
+// refreshed g).  c_i = a_i^T phi(r) for the label-signed a_i; block partials:
+//   problem 1 (SVM dual, s_i = c_i / kappa = y_i <w, A_i> with w = r/(lambda n)):
+//     sum_i [(1 - s_i)_+ (1 - x_i) + (s_i - 1)_+ x_i],  sum_i (1 - s_i)_+,  sum_i x_i
+//     (with ||r||^2 = x^T c the duality gap is the first sum over n, each term >= 0 on the box)
+//   problem 2 (logistic, c = grad f):
+//     sum_i (c_i + 2 lambda x_i)^2,  sum_i x_i^2,  sum_i c_i x_i
+template <int W, typename VT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_glm_gap_cols(int problem, const ColDesc<XT> *__restrict__ desc,
+                                                         const int32_t *__restrict__ prow,
+                                                         const VT *__restrict__ pval, const double *__restrict__ r,
+                                                         const double *__restrict__ x, int64_t n, double lambda,
+                                                         double kappa, double *__restrict__ part)
+{
+    constexpr int CH = W * kE;
+    const int lane = threadIdx.x & (W - 1);
+    const unsigned gmask = group_mask<W>(threadIdx.x & 31);
+    const int64_t ngrp = int64_t(gridDim.x) * kBlock / W;
+    double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    const uint64_t pf = l2_evict_first(), pl = l2_evict_last();
+    for (int64_t i = (int64_t(blockIdx.x) * kBlock + threadIdx.x) / W; i < n; i += ngrp) {
+        const Col<XT> c = load_col(desc, int32_t(i), pf);
+        double acc = 0.0;
+        for (int cs = 0; cs < c.cnt; cs += CH) {
+            Chunk<kE, XT> t;
+            const int st = cs + lane * kE;
+            if (st < c.cnt) ld_chunk_hint<kE>(t, prow, pval, c.pbeg + st, pf);
+            acc += problem == 2 ? chunk_dot_hint<kE, XT, double, 1>(t, r, c.cnt - st, pl)
+                                : chunk_dot_hint<kE, XT, double, 0>(t, r, c.cnt - st, pl);
+        }
+        acc = group_sum<W>(acc, gmask);
+        if (lane == 0) {
+            const double xi = __ldg(x + i);
+            if (problem == 1) {
+                const double s = acc / kappa;
+                const double below = 1.0 - s > 0.0 ? 1.0 - s : 0.0, above = s - 1.0 > 0.0 ? s - 1.0 : 0.0;
+                t1 += below * (1.0 - xi) + above * xi;
+                t2 += below;
+                t3 += xi;
+            } else {
+                const double q = fma(2.0 * lambda, xi, acc);
+                t1 += q * q;
+                t2 += xi * xi;
+                t3 += acc * xi;
+            }
+        }
+    }
+    __shared__ double sm[3][kBlock / 32];
+    t1 = warp_sum(t1);
+    t2 = warp_sum(t2);
+    t3 = warp_sum(t3);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sm[0][w] = t1;
+        sm[1][w] = t2;
+        sm[2][w] = t3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int q = 0; q < kBlock / 32; ++q) {
+            a0 += sm[0][q];
+            a1 += sm[1][q];
+            a2 += sm[2][q];
+        }
+        part[3 * blockIdx.x + 0] = a0;
+        part[3 * blockIdx.x + 1] = a1;
+        part[3 * blockIdx.x + 2] = a2;
+    }
+}
+
+// Labels folded into the stored values: the SVM dual signs column i by y_i
+// (examples are columns), logistic regression signs entry (r, i) by y_r
+// (examples are rows).  A sign flip is exact in every value type.
+template <typename VT>
+__device__ __forceinline__ VT negate_value(VT v)
+{
+    if constexpr (sizeof(VT) == 2) {
+        VT o;
+        o.bits = uint16_t(v.bits ^ 0x8000u);
+        return o;
+    } else {
+        return -v;
+    }
+}
+
+template <typename VT, typename XT>
+__global__ void __launch_bounds__(kBlock) k_apply_labels(int problem, const ColDesc<XT> *__restrict__ desc,
+                                                         const int32_t *__restrict__ prow, VT *__restrict__ pval,
+                                                         int64_t n, const double *__restrict__ y)
+{
+    const int64_t stride = int64_t(gridDim.x) * kBlock;
+    for (int64_t i = int64_t(blockIdx.x) * kBlock + threadIdx.x; i < n; i += stride) {
+        const Col<XT> c = load_col(desc, int32_t(i));
+        const bool col_neg = problem == 1 && y[i] < 0.0;
+        for (int e = 0; e < c.cnt; ++e) {
+            const int64_t p = c.pbeg + e;
+            if (problem == 1 ? col_neg : (y[prow[p]] < 0.0)) pval[p] = negate_value(pval[p]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 #define PCDM_DISPATCH_W(W, ...)                                    \
@@ -1203,7 +1343,11 @@ template <typename VT, typename XT>
 cudaError_t Kernels<VT, XT>::gather(const IterArgs<VT, XT> &a, int W, int64_t k, cudaStream_t st)
 {
     if (a.tau <= 0) return cudaSuccess;
-    PCDM_DISPATCH_W(W, { k_gather<W_, VT, XT><<<blocks_for_threads(a.tau * W_, 0), kBlock, 0, st>>>(a, k); });
+    if (a.problem == 2) {
+        PCDM_DISPATCH_W(W, { k_gather<W_, VT, XT, 1><<<blocks_for_threads(a.tau * W_, 0), kBlock, 0, st>>>(a, k); });
+    } else {
+        PCDM_DISPATCH_W(W, { k_gather<W_, VT, XT, 0><<<blocks_for_threads(a.tau * W_, 0), kBlock, 0, st>>>(a, k); });
+    }
     return cudaGetLastError();
 }
 
@@ -1258,12 +1402,19 @@ int Kernels<VT, XT>::pipe_max_blocks(int threads)
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     const size_t bytes = pipe_smem_bytes<VT>(threads);
-    if (cudaFuncSetAttribute(k_fused_pipe<VT, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) !=
-        cudaSuccess)
+    // the same grid serves both gradient maps: the smaller co-resident grid of the two
+    int per_sm_map = 0;
+    if (cudaFuncSetAttribute(k_fused_pipe<VT, XT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_fused_pipe<VT, XT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) !=
+            cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_pipe<VT, XT>, threads, bytes) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_pipe<VT, XT, 0>, threads, bytes) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_map, k_fused_pipe<VT, XT, 1>, threads, bytes) !=
+            cudaSuccess)
         return 0;
-    return per_sm * sms;
+    return (per_sm < per_sm_map ? per_sm : per_sm_map) * sms;
 }
 
 template <typename VT, typename XT>
@@ -1273,8 +1424,9 @@ cudaError_t Kernels<VT, XT>::fused_pipe(const IterArgs<VT, XT> &a, const FusedSh
     if (iters <= 0 || a.tau <= 0) return cudaSuccess;
     IterArgs<VT, XT> args = a;
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
-    return cudaLaunchCooperativeKernel((const void *)k_fused_pipe<VT, XT>, dim3(unsigned(sh.blocks)),
-                                       dim3(unsigned(sh.threads)), params, pipe_smem_bytes<VT>(sh.threads), st);
+    const void *fn = a.problem == 2 ? (const void *)k_fused_pipe<VT, XT, 1> : (const void *)k_fused_pipe<VT, XT, 0>;
+    return cudaLaunchCooperativeKernel(fn, dim3(unsigned(sh.blocks)), dim3(unsigned(sh.threads)), params,
+                                       pipe_smem_bytes<VT>(sh.threads), st);
 }
 
 template <typename VT, typename XT>
@@ -1364,6 +1516,27 @@ cudaError_t Kernels<VT, XT>::refresh_cols(const ColDesc<XT> *desc, const int32_t
         k_refresh_cols<W_, VT, XT><<<blocks_for_threads(n * W_, 152 * 16), kBlock, 0, st>>>(desc, prow, pval, x,
                                                                                               n, g64);
     });
+    return cudaGetLastError();
+}
+
+template <typename VT, typename XT>
+cudaError_t Kernels<VT, XT>::glm_gap_cols(int problem, const ColDesc<XT> *desc, const int32_t *prow, const VT *pval,
+                                          const double *r, const double *x, int64_t n, double lambda, double kappa,
+                                          double *part, int blocks, int W, cudaStream_t st)
+{
+    PCDM_DISPATCH_W(W, {
+        k_glm_gap_cols<W_, VT, XT><<<dim3(unsigned(blocks)), kBlock, 0, st>>>(problem, desc, prow, pval, r, x, n,
+                                                                               lambda, kappa, part);
+    });
+    return cudaGetLastError();
+}
+
+template <typename VT, typename XT>
+cudaError_t Kernels<VT, XT>::apply_labels(int problem, const ColDesc<XT> *desc, const int32_t *prow, VT *pval,
+                                          int64_t n, const double *y, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_apply_labels<VT, XT><<<blocks_for_threads(n, 152 * 64), kBlock, 0, st>>>(problem, desc, prow, pval, n, y);
     return cudaGetLastError();
 }
 

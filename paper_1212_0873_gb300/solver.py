@@ -388,3 +388,50 @@ class MultiLasso:
             self.close()
         except Exception:
             pass
+
+
+class LabeledProblem(Lasso):
+    """PCDM1 on the SVM dual (Sec. 8.3, problem "svm_dual": A is d x n with one
+    example per column and y one label per column) or on L2-regularised logistic
+    regression (Sec. 8.4, problem "logistic": one example per row, y one label
+    per row), through pcdm_create_problem.  Same methods as Lasso; residual()
+    returns sum_i y_i x_i A_i (SVM dual) or the margins y_j A_j^T x (logistic),
+    and gap() the primal, dual and duality gap of that problem."""
+
+    def __init__(self, problem, m, n, col_ptr, row_idx, val, y, lam, *, xg_dtype=None, fused=True, refresh_every=0,
+                 check_every=0, lanes_per_col=0, profile=False, barrier_timeout_ns=None, stream=None,
+                 sampling="nice", p_b=1.0):
+        val_dtype = _val_code(val)
+        if xg_dtype is None:
+            xg_dtype = "f64" if val_dtype == "f64" else "f32"
+        self.m, self.n = int(m), int(n)
+        self.val_dtype, self.xg_dtype = val_dtype, xg_dtype
+        self.problem = problem
+        p_cp, d_cp = _ptr_and_device(col_ptr)
+        p_ri, d_ri = _ptr_and_device(row_idx)
+        p_v, d_v = _ptr_and_device(val)
+        if not _is_tensor(y):
+            y = np.ascontiguousarray(y, dtype=np.float64)
+        p_y, d_y = _ptr_and_device(y)
+        if len({d_cp, d_ri, d_v, d_y}) != 1:
+            raise ValueError("A and y must all be host arrays or all be device tensors")
+        nnz = int(col_ptr[-1]) if not _is_tensor(col_ptr) else int(col_ptr[-1].item())
+        A = B.pcdm_csc(self.m, self.n, nnz, p_cp, p_ri, p_v, B.DTYPE_CODES[val_dtype], d_cp)
+        opts = B.pcdm_default_opts()
+        opts.xg_dtype = B.DTYPE_CODES[xg_dtype]
+        opts.fused = 1 if fused else 0
+        opts.refresh_every = int(refresh_every)
+        opts.check_every = int(check_every)
+        opts.lanes_per_col = int(lanes_per_col)
+        opts.profile = 1 if profile else 0
+        opts.sampling = B.SAMPLING_CODES[sampling]
+        opts.p_b = float(p_b)
+        if barrier_timeout_ns is not None:
+            opts.barrier_timeout_ns = int(barrier_timeout_ns)
+        self.stream = current_stream() if stream is None else stream
+        self._h = B.pcdm_create_problem(A, problem, p_y, lam, opts, self.stream)
+        self.lam = float(lam)
+
+    @classmethod
+    def from_instance(cls, inst, **kw):
+        return cls(inst.problem, inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val, inst.y, inst.lam, **kw)

@@ -219,3 +219,21 @@ def test_generator_library_exports_its_header():
     assert names == ["pcdm_gen_per_col"]
     lib = ctypes.CDLL(build.GEN_LIB)
     assert all(hasattr(lib, n) for n in names)
+
+
+def test_create_problem_rejects_bad_arguments_before_device_work(B):
+    L = B.lib()
+    A = B.pcdm_csc(4, 3, 0, None, None, None, B.PCDM_F64, 0)
+    y = (ctypes.c_double * 4)(1.0, -1.0, 1.0, 1.0)
+    h = ctypes.c_void_p()
+    opts = B.pcdm_default_opts()
+    assert L.pcdm_create_problem(ctypes.byref(A), 0, y, 1.0, None, None, ctypes.byref(h)) == B.PCDM_EINVAL
+    assert L.pcdm_create_problem(ctypes.byref(A), 3, y, 1.0, None, None, ctypes.byref(h)) == B.PCDM_EINVAL
+    assert L.pcdm_create_problem(ctypes.byref(A), 1, None, 1.0, None, None, ctypes.byref(h)) == B.PCDM_EINVAL
+    for lam in (0.0, -1.0, float("inf"), float("nan")):
+        assert L.pcdm_create_problem(ctypes.byref(A), 2, y, lam, None, None, ctypes.byref(h)) == B.PCDM_EINVAL
+    opts.sampling = 1
+    assert L.pcdm_create_problem(ctypes.byref(A), 1, y, 1.0, ctypes.byref(opts), None,
+                                 ctypes.byref(h)) == B.PCDM_EINVAL
+    assert not h.value
+    assert L.pcdm_problem_kind(None, None) != 0
