@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the batched regularisation-path measurement")
     p.add_argument("--path-len", type=int, default=32, help="lambdas on the batched regularisation path")
     p.add_argument("--no-grad", action="store_true", help="skip the differentiation measurement")
+    p.add_argument("--no-svm", action="store_true", help="skip the SVM-dual measurement (Sec. 8.3 workload)")
+    p.add_argument("--no-logistic", action="store_true", help="skip the logistic-regression measurement (Sec. 8.4)")
     p.add_argument("--no-tvr", action="store_true", help="skip the theory-versus-reality experiment")
     p.add_argument("--no-async", action="store_true", help="skip the asynchronous-mode measurement")
     p.add_argument("--no-multi", action="store_true", help="skip the many-small-problems measurement")
@@ -406,6 +408,111 @@ def run_multi():
 
 
 # ----------------------------------------------------------------------------- differentiation
+def _timed_cuda(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def run_svm():
+    """The SVM-dual workload of Sec. 8.3 on rcv1-shaped synthetic data: n =
+    677,399 examples, d = 47,236 features, 73 feature draws per example with
+    popularity proportional to (r+1)^-0.64 (so the most common feature is in
+    about 43% of the examples: omega / n near the paper's 291,516 / 677,399),
+    unit-norm nonnegative values, lambda = 1e-5.  Each tau solves from x = 0 to
+    relative duality gap 1e-2 (the paper: a gap near 0.01 suffices for
+    training).  Reported per tau: beta, iterations, epochs, time, and the
+    speedup in iterations over tau = 1 beside the theory's tau / beta."""
+    import numpy as np
+    from paper_1212_0873_gb300 import LabeledProblem, instances
+
+    t0 = time.perf_counter()
+    inst = instances.svm_instance(47_236, 677_399, 73, lam=1e-5, zipf=0.64, val_dtype="f64", seed=1010)
+    t_gen = time.perf_counter() - t0
+    rows = []
+    with LabeledProblem.from_instance(inst, check_every=0) as s:
+        for tau in (1, 16, 256):
+            s.reset()
+            tuning = s.autotune(tau, 200)
+            s.solve(tau, 0, 0.5, 10**7)                      # warm-up: the kernel of this tau, column heads
+            s.reset()
+            t, (ok, it, rel) = _timed_cuda(lambda: s.solve(tau, 0, 1e-2, 10**8))
+            x = s.x()
+            rows.append({"tau": tau, "beta": s.beta(tau), "tuning": tuning, "converged": ok, "iterations": it,
+                         "epochs": it * tau / inst.n, "seconds": t, "rel_gap": rel,
+                         "updates_per_s": it * tau / t, "at_upper_bound": float(np.mean(x == 1.0)),
+                         "at_zero": float(np.mean(x == 0.0))})
+        omega = s.omega
+    base = rows[0]["iterations"]
+    for r in rows:
+        r["iteration_speedup"] = base / r["iterations"]
+        r["theory_tau_over_beta"] = r["tau"] / r["beta"]
+        r["time_speedup"] = rows[0]["seconds"] / r["seconds"]
+    return {"workload": "SVM dual (Sec. 8.3), rcv1-shaped synthetic: n=677399 examples, d=47236 features, %d "
+                        "nonzeros (about 72 per example), omega=%d, lambda=1e-5, fp64; from x=0 to relative duality "
+                        "gap 1e-2" % (inst.nnz, omega),
+            "generate_s": t_gen, "omega": omega, "rows": rows}
+
+
+def run_logistic(a):
+    """L2-regularised logistic regression (Sec. 8.4) on KDDB-shaped synthetic
+    data at a smaller scale: m = 2e6 examples (rows) with exactly 29 features each
+    (KDDB's mean; so omega = 29) out of n = 3e6, N(0,1)/sqrt(29) values, labels
+    from a logistic model, lambda = 1 as in the paper.  tau = 65536; from x = 0
+    to relative duality gap 1e-6, FP64 values and margins; the time of one
+    epoch and F(x_0)/F(x_k) after it (the paper's table reports that ratio)."""
+    import numpy as np
+    from paper_1212_0873_gb300 import LabeledProblem, instances
+
+    t0 = time.perf_counter()
+    inst = instances.logistic_instance(2_000_000, 3_000_000, 29, lam=1.0, val_dtype="f64", seed=1011)
+    t_gen = time.perf_counter() - t0
+    tau = 65536
+    with LabeledProblem.from_instance(inst, profile=True) as s:
+        tuning = s.autotune(tau, 20)
+        s.reset()
+        s.solve(tau, 0, 1e-6, 10**6)                          # warm-up
+        s.reset()
+        F0 = s.gap()["primal"]
+        epoch_iters = (inst.n + tau - 1) // tau
+        s.reset()
+        t_epoch, _ = _timed_cuda(lambda: s.step(tau, epoch_iters, 0))
+        F1 = s.gap()["primal"]
+        s.reset()
+        s.reset_stats()
+        t_solve, (ok, it, rel) = _timed_cuda(lambda: s.solve(tau, 0, 1e-6, 10**6))
+        st = s.stats()
+        beta = s.beta(tau)
+    # algorithmic bytes as for LASSO (FP64): per gathered nonzero value + index + margin,
+    # per update x read and write, 1/L and the descriptor, per scattered nonzero value + index + margin read/write
+    alg = st["gathered_nnz"] * 20 + st["updates"] * 32 + st["scattered_nnz"] * 28
+    kernel_s = st["iter_kernel_ms"] / 1e3
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+        ost = oracle.GlmState(oracle.LOGISTIC, A, inst.y, inst.lam)
+        c0 = time.perf_counter()
+        ost.run(tau, 4, 0)
+        c1 = time.perf_counter() - c0
+        cpu = {"value": 4 * tau / c1, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first 4 iterations (tau=%d) of the same run, single-threaded FP64 oracle, %.1f s" % (tau, c1)}
+    return {"workload": "L2-regularised logistic regression (Sec. 8.4), KDDB-shaped synthetic at 1/10 scale: "
+                        "m=2e6 examples x n=3e6 features, 29 nonzeros per example (omega=29), lambda=1, fp64; "
+                        "tau=65536 from x=0 to relative duality gap 1e-6",
+            "generate_s": t_gen, "beta": beta, "tuning": tuning, "epoch_s": t_epoch, "epoch_iterations": epoch_iters,
+            "F0_over_F1epoch": F0 / F1, "solve_s": t_solve, "converged": ok, "iterations": it, "rel_gap": rel,
+            "updates_per_s": it * tau / t_solve,
+            "iteration_kernel": {"alg_GB_per_s": alg / kernel_s / 1e9 if kernel_s > 0 else None,
+                                 "note": "each gathered nonzero also costs one FP64 exp (the logistic gradient map)"},
+            "cpu_baseline": cpu}
+
+
 def run_grad():
     """Forward (solve to relative gap 1e-6, then the FP64 polish on the support)
     and backward (pcdm_backward: dL/db and dL/dlambda for L = 1/2 ||x - x*||^2)
@@ -634,6 +741,12 @@ def run_pcdm(a, rank, local, world):
     grad = None
     if rank == 0 and world == 1 and not a.no_grad:
         grad = run_grad()
+    svm = None
+    if rank == 0 and world == 1 and not a.no_svm:
+        svm = run_svm()
+    logistic = None
+    if rank == 0 and world == 1 and not a.no_logistic:
+        logistic = run_logistic(a)
     tvr = None
     if rank == 0 and world == 1 and not a.no_tvr:
         tvr = run_theory_vs_reality()
@@ -660,6 +773,8 @@ def run_pcdm(a, rank, local, world):
             "asynchronous": asyn,
             "many_small_problems": multi,
             "differentiation": grad,
+            "svm_dual": svm,
+            "logistic": logistic,
             "theory_vs_reality": tvr,
             "extras": {"nonzero_update_frac": st["nonzero_updates"] / max(st["updates"], 1),
                        "mean_col_nnz_gathered": st["gathered_nnz"] / max(st["updates"], 1),

@@ -181,9 +181,9 @@ pcdm_status pcdm_create(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
  * dtype), so pcdm_get_residual returns the g above; pcdm_get_L returns ||A_i||^2
  * for the SVM dual (the paper's L_i times lambda n^2) and ||a_i||^2/4 for
  * logistic regression.  These handles run the tau-nice sampling in the pipelined
- * kernel (when tau fits one pass of the grid) or in the two-kernel form;
- * pcdm_polish, pcdm_backward, pcdm_set_b and the asynchronous mode return EINVAL,
- * and pcdm_set_tuning accepts kernels 0 and 2 only.
+ * kernel, the fused kernel with lanes per column or the two-kernel form (not in
+ * the rounds kernel); pcdm_polish, pcdm_backward, pcdm_set_b and the
+ * asynchronous mode return EINVAL, and pcdm_set_tuning rejects kernel 3.
  * Errors: those of pcdm_create, plus EINVAL for an unknown problem, a NULL y,
  * lambda <= 0 or not finite, a sampling other than PCDM_SAMPLING_NICE, and a
  * label other than -1 or +1.

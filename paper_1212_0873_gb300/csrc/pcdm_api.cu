@@ -149,16 +149,6 @@ bool pipe_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads = 0
     return true;
 }
 
-// Whether the pipelined kernel takes tau with the handle's tuning (the kernels
-// other than it and the two-kernel form do not run the SVM dual or logistic regression).
-template <typename VT, typename XT>
-bool pipe_fits(pcdm_handle h, int64_t tau)
-{
-    if (h->tune_kernel != -1 && h->tune_kernel != 0) return false;
-    FusedShape sh;
-    return pipe_shape<VT, XT>(h, tau, &sh, h->tune_kernel == 0 ? h->tune_threads : 0);
-}
-
 // The per-column heads of the pipelined kernels, built on their first use.
 template <typename VT, typename XT>
 pcdm_status ensure_heads(pcdm_handle h, IterArgs<VT, XT> &a)
@@ -218,9 +208,7 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         h->g2_valid = false;
         h->st_launches += iters;
         h->st_kernels += 3 * iters;
-    } else if (h->opts.fused && h->tune_kernel != 2 &&
-               (h->problem == PCDM_PROBLEM_LASSO || pipe_fits<VT, XT>(h, tau))) {
-        // (the SVM dual and logistic regression run in the pipelined kernel or the two-kernel form)
+    } else if (h->opts.fused && h->tune_kernel != 2) {
         FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
         const bool pipe = (h->tune_kernel == 1 || h->tune_kernel == 3)
@@ -229,7 +217,7 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         // rounds: when chosen (pcdm_autotune / pcdm_set_tuning); on the workloads measured so far
         // it did not beat the fused kernel where the one-pass grid cannot hold tau
         bool rounds = false;
-        if (!pipe && h->tune_kernel == 3) {
+        if (!pipe && h->tune_kernel == 3 && h->problem == PCDM_PROBLEM_LASSO) {
             const int thr = h->tune_kernel == 3 && h->tune_threads > 0 ? h->tune_threads : kPipeRoundsMaxBlock;
             const int cap = Kernels<VT, XT>::pipe_rounds_max_blocks(thr);
             if (cap > 0) {
@@ -1333,8 +1321,8 @@ pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
         return PCDM_OK;
     }
     if (t->heads != 0 && t->heads != 1) return set_err(h, PCDM_EINVAL, "heads must be 0 or 1");
-    if (h->problem != PCDM_PROBLEM_LASSO && (t->kernel == 1 || t->kernel == 3))
-        return set_err(h, PCDM_EINVAL, "the SVM dual and logistic regression run in kernels 0 and 2 only");
+    if (h->problem != PCDM_PROBLEM_LASSO && t->kernel == 3)
+        return set_err(h, PCDM_EINVAL, "the SVM dual and logistic regression run in kernels 0, 1 and 2");
     const bool lanes_ok = t->lanes_per_col == 1 || t->lanes_per_col == 2 || t->lanes_per_col == 4 ||
                           t->lanes_per_col == 8 || t->lanes_per_col == 16 || t->lanes_per_col == 32;
     if (t->kernel < 0 || t->kernel > 3 || !lanes_ok)
@@ -1415,7 +1403,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
             if (!ok) continue;
         }
         if (c.kernel == 0 && c.heads && h->head_off) continue;   // the heads do not fit
-        if (h->problem != PCDM_PROBLEM_LASSO && (c.kernel == 1 || c.kernel == 3)) continue;
+        if (h->problem != PCDM_PROBLEM_LASSO && c.kernel == 3) continue;
         h->tune_kernel = c.kernel;
         h->tune_W = c.W;
         h->tune_threads = c.threads;

@@ -87,7 +87,7 @@ struct IterArgs {
     const unsigned char *head;
     // Objective: 0 LASSO, 1 SVM dual (Sec. 8.3), 2 logistic regression (Sec. 8.4);
     // kappa = lambda n for the SVM dual (the linear term in the scale of ||a_i||^2).
-    // Only the two-kernel form and the pipelined kernel take problems 1 and 2.
+    // The rounds kernel, the asynchronous kernel and the batched kernels take problem 0 only.
     int problem;
     double kappa;
 };

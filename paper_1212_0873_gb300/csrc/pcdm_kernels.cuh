@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const IterArgs<VT, XT> a, in
 // Position j0 = (global thread index) / W is this group's register-resident
 // column; positions j0 + ngrp, j0 + 2 ngrp, ... (only when tau exceeds the
 // number of groups) go through the generic path.
-template <int W, typename VT, typename XT>
+template <int W, typename VT, typename XT, int GM = 0>
 __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
 {
     constexpr int CH = W * kE;
@@ -470,15 +470,15 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
             XT acc = XT(0);
 #pragma unroll
             for (int e = 0; e < kE; ++e)
-                if (e < valid0) acc = fma(ch.val[e], gv[e], acc);
+                if (e < valid0) acc = fma(ch.val[e], grad_map<GM>(gv[e]), acc);
             for (int cs = CH; cs < c0.cnt; cs += CH) {
                 Chunk<kE, XT> t;
                 const int st = cs + lane * kE;
                 if (st < c0.cnt) ld_chunk<kE>(t, a.prow, a.pval, c0.pbeg + st);
-                acc += chunk_dot<kE, XT, XT, XT>(t, a.g, c0.cnt - st);
+                acc += chunk_dot<kE, XT, XT, XT, GM>(t, a.g, c0.cnt - st);
             }
             acc = group_sum<W>(acc, gmask);
-            const double xn = prox_step(xi, double(acc), double(c0.invL), a.inv_beta, a.lambda);
+            const double xn = coord_step(a.problem, xi, double(acc), double(c0.invL), a.inv_beta, a.lambda, a.kappa);
             const double h64 = xn - xi;
             h0 = XT(h64);
             if (lane == 0) {
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
                 }
             }
         }
-        for (int64_t j = j0 + ngrp; j < a.tau; j += ngrp) gather_generic<W>(a, S, j, lane, gmask, cnt);
+        for (int64_t j = j0 + ngrp; j < a.tau; j += ngrp) gather_generic<W, VT, XT, GM>(a, S, j, lane, gmask, cnt);
         target += gridDim.x;
         if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) return;
 
@@ -1367,18 +1367,26 @@ int Kernels<VT, XT>::fused_max_blocks(int W, int threads)
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    cudaError_t e = cudaErrorInvalidValue;
+    // the same grid serves both gradient maps: the smaller co-resident grid of the two
+    int per_sm_map = 0;
+    cudaError_t e = cudaErrorInvalidValue, e2 = cudaErrorInvalidValue;
+#define PCDM_FUSED_OCC(WW)                                                                            \
+    case WW:                                                                                          \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<WW, VT, XT, 0>, threads, 0);   \
+        e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_map, k_fused<WW, VT, XT, 1>, threads, 0); \
+        break;
     switch (W) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<1, VT, XT>, threads, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<2, VT, XT>, threads, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<4, VT, XT>, threads, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<8, VT, XT>, threads, 0); break;
-    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<16, VT, XT>, threads, 0); break;
-    case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<32, VT, XT>, threads, 0); break;
+        PCDM_FUSED_OCC(1)
+        PCDM_FUSED_OCC(2)
+        PCDM_FUSED_OCC(4)
+        PCDM_FUSED_OCC(8)
+        PCDM_FUSED_OCC(16)
+        PCDM_FUSED_OCC(32)
     default: return 0;
     }
-    if (e != cudaSuccess) return 0;
-    return per_sm * sms;
+#undef PCDM_FUSED_OCC
+    if (e != cudaSuccess || e2 != cudaSuccess) return 0;
+    return (per_sm < per_sm_map ? per_sm : per_sm_map) * sms;
 }
 
 template <typename VT, typename XT>
@@ -1388,9 +1396,10 @@ cudaError_t Kernels<VT, XT>::fused(const IterArgs<VT, XT> &a, const FusedShape &
     if (iters <= 0 || a.tau <= 0) return cudaSuccess;
     IterArgs<VT, XT> args = a;
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
+    const bool map = a.problem == 2;
     PCDM_DISPATCH_W(sh.W, {
-        return cudaLaunchCooperativeKernel((const void *)k_fused<W_, VT, XT>, dim3(unsigned(sh.blocks)),
-                                           dim3(unsigned(sh.threads)), params, 0, st);
+        const void *fn = map ? (const void *)k_fused<W_, VT, XT, 1> : (const void *)k_fused<W_, VT, XT, 0>;
+        return cudaLaunchCooperativeKernel(fn, dim3(unsigned(sh.blocks)), dim3(unsigned(sh.threads)), params, 0, st);
     });
     return cudaErrorInvalidValue;
 }

@@ -1,7 +1,7 @@
 """PCDM1 on the SVM dual (Sec. 8.3) and on L2-regularised logistic regression
 (Sec. 8.4) on the GPU against the oracle: the same tau-nice samples, iterate by
-iterate, in every kernel that runs these problems (pipelined, two-kernel form
-with 1 and 4 lanes per column) and every precision pair; the duality-gap record;
+iterate, in every kernel that runs these problems (pipelined, fused with 1, 8
+and 32 lanes per column, two-kernel form with 1 and 4) and every precision pair; the duality-gap record;
 solves to a tight gap; edge cases (an all-zero example, columns longer than one
 chunk, ragged tau, bad labels)."""
 import numpy as np
@@ -52,7 +52,7 @@ def _gpu_residual_as_oracle(inst, g):
 
 
 # (kernel, lanes per column, threads per block, heads)
-CHOICES = [(0, 1, 64, 1), (0, 1, 160, 0), (2, 1, 0, 1), (2, 4, 0, 1)]
+CHOICES = [(0, 1, 64, 1), (0, 1, 160, 0), (1, 1, 0, 1), (1, 8, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1), (2, 4, 0, 1)]
 
 
 @pytest.mark.parametrize("problem", sorted(PROBLEMS))
@@ -134,5 +134,5 @@ def test_bad_labels_and_lasso_only_calls_are_rejected():
         with pytest.raises(PcdmError):
             s.step_async(100)
         with pytest.raises(PcdmError):
-            s.set_tuning(1, 4, 0)
+            s.set_tuning(3, 1, 128)
         s.step(64, 2, 0)                                # the handle stays usable
