@@ -463,54 +463,64 @@ def run_logistic(a):
     """L2-regularised logistic regression (Sec. 8.4) on KDDB-shaped synthetic
     data at a smaller scale: m = 2e6 examples (rows) with exactly 29 features each
     (KDDB's mean; so omega = 29) out of n = 3e6, N(0,1)/sqrt(29) values, labels
-    from a logistic model, lambda = 1 as in the paper.  tau = 65536; from x = 0
-    to relative duality gap 1e-6, FP64 values and margins; the time of one
-    epoch and F(x_0)/F(x_k) after it (the paper's table reports that ratio)."""
-    import numpy as np
+    from a logistic model, lambda = 1 as in the paper.  tau = 65536 from x = 0 to
+    relative duality gap 1e-6, once with FP64 values and margins and once with
+    BF16 values and FP32 margins (FP64 x and steps, FP64 refresh every 64
+    iterations); the time of one epoch and F(x_0)/F(x_k) after it (the ratio the
+    paper's table reports)."""
     from paper_1212_0873_gb300 import LabeledProblem, instances
 
-    t0 = time.perf_counter()
-    inst = instances.logistic_instance(2_000_000, 3_000_000, 29, lam=1.0, val_dtype="f64", seed=1011)
-    t_gen = time.perf_counter() - t0
     tau = 65536
-    with LabeledProblem.from_instance(inst, profile=True) as s:
-        tuning = s.autotune(tau, 20)
-        s.reset()
-        s.solve(tau, 0, 1e-6, 10**6)                          # warm-up
-        s.reset()
-        F0 = s.gap()["primal"]
-        epoch_iters = (inst.n + tau - 1) // tau
-        s.reset()
-        t_epoch, _ = _timed_cuda(lambda: s.step(tau, epoch_iters, 0))
-        F1 = s.gap()["primal"]
-        s.reset()
-        s.reset_stats()
-        t_solve, (ok, it, rel) = _timed_cuda(lambda: s.solve(tau, 0, 1e-6, 10**6))
-        st = s.stats()
-        beta = s.beta(tau)
-    # algorithmic bytes as for LASSO (FP64): per gathered nonzero value + index + margin,
-    # per update x read and write, 1/L and the descriptor, per scattered nonzero value + index + margin read/write
-    alg = st["gathered_nnz"] * 20 + st["updates"] * 32 + st["scattered_nnz"] * 28
-    kernel_s = st["iter_kernel_ms"] / 1e3
+    rows = []
     cpu = None
-    if not a.no_cpu_baseline:
-        import oracle
-        A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
-        ost = oracle.GlmState(oracle.LOGISTIC, A, inst.y, inst.lam)
-        c0 = time.perf_counter()
-        ost.run(tau, 4, 0)
-        c1 = time.perf_counter() - c0
-        cpu = {"value": 4 * tau / c1, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first 4 iterations (tau=%d) of the same run, single-threaded FP64 oracle, %.1f s" % (tau, c1)}
+    for val_dtype in ("f64", "bf16"):
+        t0 = time.perf_counter()
+        inst = instances.logistic_instance(2_000_000, 3_000_000, 29, lam=1.0, val_dtype=val_dtype, seed=1011)
+        t_gen = time.perf_counter() - t0
+        refresh = 0 if val_dtype == "f64" else 64
+        with LabeledProblem.from_instance(inst, profile=True, refresh_every=refresh) as s:
+            tuning = s.autotune(tau, 20)
+            s.reset()
+            s.solve(tau, 0, 1e-6, 10**6)                      # warm-up
+            s.reset()
+            F0 = s.gap()["primal"]
+            epoch_iters = (inst.n + tau - 1) // tau
+            s.reset()
+            t_epoch, _ = _timed_cuda(lambda: s.step(tau, epoch_iters, 0))
+            F1 = s.gap()["primal"]
+            s.reset()
+            s.reset_stats()
+            t_solve, (ok, it, rel) = _timed_cuda(lambda: s.solve(tau, 0, 1e-6, 10**6))
+            st = s.stats()
+            beta = s.beta(tau)
+        # algorithmic bytes as for LASSO: per gathered nonzero value + index + margin, per update
+        # x read and write, 1/L and the descriptor, per scattered nonzero value + index + margin read/write
+        sv, sg = st["val_bytes"], st["xg_bytes"]
+        alg = st["gathered_nnz"] * (sv + 4 + sg) + st["updates"] * (16 + sg + 8) + st["scattered_nnz"] * (sv + 4 + 2 * sg)
+        kernel_s = st["iter_kernel_ms"] / 1e3
+        rows.append({"values": val_dtype, "margins": "f64" if val_dtype == "f64" else "f32", "generate_s": t_gen,
+                     "beta": beta, "tuning": tuning, "epoch_s": t_epoch, "epoch_iterations": epoch_iters,
+                     "F0_over_F1epoch": F0 / F1, "solve_s": t_solve, "converged": ok, "iterations": it,
+                     "rel_gap": rel, "updates_per_s": it * tau / t_solve,
+                     "us_per_iteration_kernel": 1e6 * kernel_s / max(st["iterations"], 1),
+                     "alg_GB_per_s": alg / kernel_s / 1e9 if kernel_s > 0 else None})
+        if val_dtype == "f64" and not a.no_cpu_baseline:
+            import oracle
+            A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+            ost = oracle.GlmState(oracle.LOGISTIC, A, inst.y, inst.lam)
+            c0 = time.perf_counter()
+            ost.run(tau, 4, 0)
+            c1 = time.perf_counter() - c0
+            cpu = {"value": 4 * tau / c1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "first 4 iterations (tau=%d) of the FP64 run, single-threaded FP64 oracle, %.1f s"
+                             % (tau, c1)}
+        del inst
     return {"workload": "L2-regularised logistic regression (Sec. 8.4), KDDB-shaped synthetic at 1/10 scale: "
-                        "m=2e6 examples x n=3e6 features, 29 nonzeros per example (omega=29), lambda=1, fp64; "
+                        "m=2e6 examples x n=3e6 features, 29 nonzeros per example (omega=29), lambda=1; "
                         "tau=65536 from x=0 to relative duality gap 1e-6",
-            "generate_s": t_gen, "beta": beta, "tuning": tuning, "epoch_s": t_epoch, "epoch_iterations": epoch_iters,
-            "F0_over_F1epoch": F0 / F1, "solve_s": t_solve, "converged": ok, "iterations": it, "rel_gap": rel,
-            "updates_per_s": it * tau / t_solve,
-            "iteration_kernel": {"alg_GB_per_s": alg / kernel_s / 1e9 if kernel_s > 0 else None,
-                                 "note": "each gathered nonzero also costs one FP64 exp (the logistic gradient map)"},
-            "cpu_baseline": cpu}
+            "note": "every gathered nonzero costs one exp (the logistic gradient map): an FP64 exp in the FP64 "
+                    "form, an FP32 one in the BF16/FP32 form",
+            "rows": rows, "cpu_baseline": cpu}
 
 
 def run_grad():
