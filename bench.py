@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--no-async", action="store_true", help="skip the asynchronous-mode measurement")
     p.add_argument("--no-multi", action="store_true", help="skip the many-small-problems measurement")
     p.add_argument("--no-tune", action="store_true", help="keep the built-in kernel choice (no pcdm_autotune)")
+    p.add_argument("--no-l2-persist", action="store_true",
+                   help="FP64: leave the context's L2 persisting-lines limit as it is (no opts.l2_persist)")
     p.add_argument("--tuning", default=None,
                    help="kernel,lanes_per_col,threads_per_block,heads set by hand (pcdm_set_tuning) instead of "
                         "pcdm_autotune, e.g. 0,1,448,1 for the pipelined kernel with 448-thread blocks")
@@ -624,7 +626,11 @@ def run_pcdm(a, rank, local, world):
     inst = make_instance(a)
     t_gen = time.perf_counter() - t_gen
     refresh = a.refresh_every if a.refresh_every >= 0 else (0 if a.dtype == "f64" else 64)
-    kw = dict(fused=not a.unfused, refresh_every=refresh, check_every=a.check_every, lanes_per_col=a.lanes)
+    # FP64: the double-buffered FP64 residual (2 x 8m bytes) only stays in L2 next to the
+    # streamed columns with the largest persisting-lines set-aside (opts.l2_persist)
+    l2p = a.dtype == "f64" and not a.no_l2_persist
+    kw = dict(fused=not a.unfused, refresh_every=refresh, check_every=a.check_every, lanes_per_col=a.lanes,
+              l2_persist=l2p)
     seed = rank
     solver = Lasso.from_instance(inst, profile=True, **kw)
     omega = solver.omega
@@ -712,7 +718,10 @@ def run_pcdm(a, rank, local, world):
         for q in range(a.warmup + a.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            s2 = Lasso(inst.m, inst.n, pin["col_ptr"], pin["row_idx"], pin["val"], pin["b"], inst.lam, **kw)
+            # a one-shot handle: no persisting-L2 set-aside (changing the context limit costs
+            # about 14 ms at create and destroy, more than it saves in one solve)
+            s2 = Lasso(inst.m, inst.n, pin["col_ptr"], pin["row_idx"], pin["val"], pin["b"], inst.lam,
+                       **dict(kw, l2_persist=False))
             t1 = time.perf_counter()
             ok, it, rel = s2.solve(a.tau, seed, a.tol, a.max_iters)
             t2 = time.perf_counter()
@@ -730,7 +739,7 @@ def run_pcdm(a, rank, local, world):
         e2e_value, _, _ = aggregate(e2e_updates, sum(e2e_s), world)
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * sum(e2e_s) / len(e2e_s),
-               "ms_create_solve_finish": [round(1e3 * p / len(e2e_s), 2) for p in phases]}
+               "ms_create_solve_finish": [round(1e3 * p / len(e2e_s), 2) for p in phases], "l2_persist": False}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -771,7 +780,8 @@ def run_pcdm(a, rank, local, world):
                        "refresh_every": refresh, "check_every": a.check_every or math.ceil(a.n / a.tau),
                        "iters_per_solve": iters[-1], "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "256 MB buffer written between timed steps (outside the events); A is %.2f GB"
-                             % ((inst.col_ptr.nbytes + inst.row_idx.nbytes + inst.val.nbytes) / 1e9)},
+                             % ((inst.col_ptr.nbytes + inst.row_idx.nbytes + inst.val.nbytes) / 1e9),
+                       "l2_persist": l2p},
             "time_to_gap_s": max_seconds / a.steps,
             "tuning": tuning,
             "roofline": roofline,

@@ -87,6 +87,16 @@ typedef struct {
     int32_t profile;             /* 1: time every iteration-kernel launch with CUDA events        */
     int32_t sampling;            /* PCDM_SAMPLING_NICE (default), _INDEPENDENT or _BINOMIAL       */
     double p_b;                  /* binomial sampling: probability that a position is kept, (0, 1] */
+    int32_t l2_persist;          /* 1: raise the CUDA context's L2 persisting-lines limit
+                                    (cudaLimitPersistingL2CacheSize) to the device maximum from
+                                    pcdm_create to pcdm_destroy, which restores the previous value.
+                                    The kernels mark the residual evict-last; the set-aside keeps
+                                    more of it in L2.  The limit is context-wide: it holds for every
+                                    kernel of the process while the handle lives.  Changing the
+                                    limit costs milliseconds at create and destroy, so it pays off
+                                    for handles that run many iterations.  0: leave it.
+                                    Single-problem handles only (the batch and multi APIs ignore it). */
+    int32_t reserved2;           /* 0 */
 } pcdm_opts;
 
 /*
@@ -127,7 +137,8 @@ typedef struct {
 } pcdm_stats;
 
 /* Default options: xg_dtype F64, fused 1, refresh_every 0, check_every 0,
- * lanes_per_col 0, barrier_timeout_ns 2e9, profile 0, sampling NICE, p_b 1. */
+ * lanes_per_col 0, barrier_timeout_ns 2e9, profile 0, sampling NICE, p_b 1,
+ * l2_persist 0. */
 void pcdm_default_opts(pcdm_opts *opts);
 
 /*

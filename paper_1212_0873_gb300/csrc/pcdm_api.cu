@@ -27,6 +27,11 @@ void free_all(pcdm_handle h)
                     h->as_S, h->as_part, h->win, h->head};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (h->l2_set) {
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, h->l2_prev);
+        cudaCtxResetPersistingL2Cache();
+        h->l2_set = false;
+    }
     if (h->g64 && h->g64 != h->g) cudaFree(h->g64);
     if (h->host_buf) cudaFreeHost(h->host_buf);
     for (auto &pr : h->ev_pending) {
@@ -436,6 +441,7 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         return set_err(nullptr, PCDM_EINVAL, "unknown sampling");
     if (o.sampling == PCDM_SAMPLING_BINOMIAL && !(o.p_b > 0.0 && o.p_b <= 1.0))
         return set_err(nullptr, PCDM_EINVAL, "p_b must be in (0, 1]");
+    if (o.l2_persist != 0 && o.l2_persist != 1) return set_err(nullptr, PCDM_EINVAL, "l2_persist must be 0 or 1");
 
     pcdm_ctx *h = new (std::nothrow) pcdm_ctx();
     if (!h) return set_err(nullptr, PCDM_ENOMEM, "host allocation failed");
@@ -465,6 +471,15 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     CKC(cudaGetDevice(&h->device));
     const int64_t vb = dtype_bytes(h->val_dtype), xb = dtype_bytes(h->xg_dtype);
     CKC(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device));
+    if (o.l2_persist) {
+        int maxp = 0;
+        CKC(cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, h->device));
+        CKC(cudaDeviceGetLimit(&h->l2_prev, cudaLimitPersistingL2CacheSize));
+        if (maxp > 0) {
+            CKC(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, size_t(maxp)));
+            h->l2_set = true;
+        }
+    }
     {
         int64_t gb = (h->n * h->W + kBlock - 1) / kBlock;
         const int64_t cap = int64_t(h->sms) * 8;

@@ -65,3 +65,26 @@ def test_rounds_kernel_with_several_positions_per_thread(val_dtype, tol):
         assert _rel(s.x(), ref.x) <= tol
         ok, it, rel = s.solve(tau, 8, 1e-8 if val_dtype == "f64" else 1e-6, 100_000)
         assert ok
+
+
+def _cu_limit_persisting_l2():
+    import ctypes
+    cu = ctypes.CDLL("libcuda.so.1")
+    v = ctypes.c_size_t(0)
+    assert cu.cuCtxGetLimit(ctypes.byref(v), 0x06) == 0        # CU_LIMIT_PERSISTING_L2_CACHE_SIZE (read only)
+    return v.value
+
+
+def test_l2_persist_option_is_scoped_to_the_handle():
+    import torch
+    torch.zeros(1, device="cuda")
+    before = _cu_limit_persisting_l2()
+    inst = instances.per_col_instance(2000, 1000, 20, nnz_star=50, val_dtype="f64", seed=1003)
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    with Lasso.from_instance(inst, l2_persist=True) as s:
+        assert _cu_limit_persisting_l2() >= before
+        s.step(96, 12, 2)
+        ref.run(96, 12, 2)
+        assert _rel(s.x(), ref.x) <= 1e-10
+    assert _cu_limit_persisting_l2() == before
