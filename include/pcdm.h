@@ -204,6 +204,25 @@ enum { PCDM_PROBLEM_LASSO = 0, PCDM_PROBLEM_SVM_DUAL = 1, PCDM_PROBLEM_LOGISTIC 
 pcdm_status pcdm_create_problem(const pcdm_csc *A, int32_t problem, const double *y, double lambda,
                                 const pcdm_opts *opts, void *cuda_stream, pcdm_handle *out);
 
+/*
+ * Device memory of the single-problem handles (pcdm_create,
+ * pcdm_create_problem) comes from a per-device stream-ordered pool owned by
+ * the library: a handle's buffers are allocated and freed in order on its
+ * stream, and freed memory stays in the pool for the next handle, so that
+ * creating and destroying handles costs microseconds of allocation instead of
+ * milliseconds of cudaMalloc and cudaFree.
+ *   pcdm_set_memory_cache       the most memory the pool of the current device
+ *                               keeps after it is freed (bytes; default 16 GiB);
+ *                               the rest goes back to the device at the next
+ *                               synchronisation
+ *   pcdm_release_cached_memory  return the cached memory of the current
+ *                               device's pool now (memory whose stream-ordered
+ *                               free has not yet executed stays)
+ * ECUDA on a CUDA error.
+ */
+pcdm_status pcdm_set_memory_cache(uint64_t bytes);
+pcdm_status pcdm_release_cached_memory(void);
+
 /* The PCDM_PROBLEM_* of a handle. */
 pcdm_status pcdm_problem_kind(pcdm_handle h, int32_t *problem);
 

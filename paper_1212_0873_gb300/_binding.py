@@ -49,6 +49,8 @@ SIGNATURES = {
     "pcdm_create_problem": (_i32, [ctypes.POINTER(pcdm_csc), _i32, _ptr, _dbl, ctypes.POINTER(pcdm_opts), _ptr,
                                    ctypes.POINTER(_ptr)]),
     "pcdm_problem_kind": (_i32, [_ptr, ctypes.POINTER(_i32)]),
+    "pcdm_set_memory_cache": (_i32, [_u64]),
+    "pcdm_release_cached_memory": (_i32, []),
     "pcdm_step": (_i32, [_ptr, _i64, _i64, _u64]),
     "pcdm_refresh": (_i32, [_ptr]),
     "pcdm_gap": (_i32, [_ptr, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
@@ -495,3 +497,11 @@ def pcdm_set_tuning(h, kernel=None, lanes_per_col=1, threads_per_block=0, heads=
         return
     t = pcdm_tuning(int(kernel), int(lanes_per_col), int(threads_per_block), int(heads), 0.0)
     _check(lib().pcdm_set_tuning(h, ctypes.byref(t)), h)
+
+
+def pcdm_set_memory_cache(nbytes):
+    _check(lib().pcdm_set_memory_cache(int(nbytes)), None)
+
+
+def pcdm_release_cached_memory():
+    _check(lib().pcdm_release_cached_memory(), None)

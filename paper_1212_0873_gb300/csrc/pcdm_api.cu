@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -18,6 +19,38 @@ using namespace pcdm_host;
 thread_local std::string pcdm_host::g_free_error;
 
 namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+uint64_t g_cache_limit = uint64_t(16) << 30;   // bytes of freed handle memory a pool keeps
+}  // namespace
+
+cudaError_t pcdm_host::handle_pool(int device, cudaMemPool_t *pool)
+{
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (device < 0 || device >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    if (!g_pools[device]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t limit = g_cache_limit;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &limit);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[device] = p;
+    }
+    *pool = g_pools[device];
+    return cudaSuccess;
+}
+
+namespace {
 
 void free_all(pcdm_handle h)
 {
@@ -25,14 +58,13 @@ void free_all(pcdm_handle h)
                     h->S[0], h->S[1], h->h, h->counters, h->bar, h->status, h->gap_part, h->gap_out,
                     h->as_sidx, h->as_c, h->as_sgn, h->as_u, h->as_dx, h->as_q, h->as_rowcnt, h->as_H,
                     h->as_S, h->as_part, h->win, h->head};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    for (void *p : ptrs) hfree(h, p);
     if (h->l2_set) {
         cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, h->l2_prev);
         cudaCtxResetPersistingL2Cache();
         h->l2_set = false;
     }
-    if (h->g64 && h->g64 != h->g) cudaFree(h->g64);
+    if (h->g64 && h->g64 != h->g) hfree(h, h->g64);
     if (h->host_buf) cudaFreeHost(h->host_buf);
     for (auto &pr : h->ev_pending) {
         cudaEventDestroy(pr.first);
@@ -65,16 +97,15 @@ pcdm_status ensure_tau(pcdm_handle h, int64_t tau)
     if (tau <= h->tau_cap) return PCDM_OK;
     // Buffers are replaced only between calls; the stream must be idle first.
     CK(h, cudaStreamSynchronize(h->stream));
-    for (int q = 0; q < 2; ++q)
-        if (h->S[q]) cudaFree(h->S[q]);
-    if (h->h) cudaFree(h->h);
+    for (int q = 0; q < 2; ++q) hfree(h, h->S[q]);
+    hfree(h, h->h);
     h->S[0] = h->S[1] = nullptr;
     h->h = nullptr;
     h->tau_cap = 0;
     h->sample_valid = false;
-    CK(h, dalloc(&h->S[0], tau));
-    CK(h, dalloc(&h->S[1], tau));
-    CK(h, dalloc_bytes(&h->h, tau * dtype_bytes(h->xg_dtype)));
+    CK(h, halloc(h, &h->S[0], tau));
+    CK(h, halloc(h, &h->S[1], tau));
+    CK(h, halloc_bytes(h, &h->h, tau * dtype_bytes(h->xg_dtype)));
     h->tau_cap = tau;
     return PCDM_OK;
 }
@@ -169,7 +200,7 @@ pcdm_status ensure_heads(pcdm_handle h, IterArgs<VT, XT> &a)
             return PCDM_OK;
         }
         void *p = nullptr;
-        CK(h, dalloc_bytes(&p, need));
+        CK(h, halloc_bytes(h, &p, need));
         h->head = static_cast<unsigned char *>(p);
         CK(h, Kernels<VT, XT>::build_heads(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
                                            static_cast<const VT *>(h->pval), h->n, h->head, h->stream));
@@ -196,7 +227,7 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         if (h->opts.sampling == PCDM_SAMPLING_INDEPENDENT) {
             if (!h->win) {
                 CK(h, cudaStreamSynchronize(h->stream));
-                CK(h, dalloc(&h->win, h->n));
+                CK(h, halloc(h, &h->win, h->n));
                 a.win = h->win;
             }
             // keys of a later iteration than k would shadow this run's (after set_iteration)
@@ -242,7 +273,7 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
             const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
             if (!h->g2) {
                 CK(h, cudaStreamSynchronize(h->stream));
-                CK(h, dalloc_bytes(&h->g2, int64_t(gbytes)));
+                CK(h, halloc_bytes(h, &h->g2, int64_t(gbytes)));
                 a.g2 = static_cast<XT *>(h->g2);
                 h->g2_valid = false;
             }
@@ -253,7 +284,7 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
             const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
             if (!h->g2) {
                 CK(h, cudaStreamSynchronize(h->stream));
-                CK(h, dalloc_bytes(&h->g2, int64_t(gbytes)));
+                CK(h, halloc_bytes(h, &h->g2, int64_t(gbytes)));
                 a.g2 = static_cast<XT *>(h->g2);
                 h->g2_valid = false;
             }
@@ -487,19 +518,19 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         int64_t rb = (h->m + kBlock - 1) / kBlock;
         h->gap_row_blocks = int(rb < 1 ? 1 : (rb > cap ? cap : rb));
     }
-    CKC(dalloc(&h->b, h->m));
-    CKC(dalloc(&h->L64, h->n));
-    CKC(dalloc(&h->x, h->n));
-    CKC(dalloc_bytes(&h->g, h->m * xb));
+    CKC(halloc(h, &h->b, h->m));
+    CKC(halloc(h, &h->L64, h->n));
+    CKC(halloc(h, &h->x, h->n));
+    CKC(halloc_bytes(h, &h->g, h->m * xb));
     if (h->xg_dtype == PCDM_F64)
         h->g64 = static_cast<double *>(h->g);
     else
-        CKC(dalloc(&h->g64, h->m));
-    CKC(dalloc(&h->counters, 3));
-    CKC(dalloc(&h->bar, 1));
-    CKC(dalloc(&h->status, 4));
-    CKC(dalloc(&h->gap_part, 3 * int64_t(h->gap_blocks) + 2 * int64_t(h->gap_row_blocks)));
-    CKC(dalloc(&h->gap_out, 9));
+        CKC(halloc(h, &h->g64, h->m));
+    CKC(halloc(h, &h->counters, 3));
+    CKC(halloc(h, &h->bar, 1));
+    CKC(halloc(h, &h->status, 4));
+    CKC(halloc(h, &h->gap_part, 3 * int64_t(h->gap_blocks) + 2 * int64_t(h->gap_row_blocks)));
+    CKC(halloc(h, &h->gap_out, 9));
     CKC(cudaMallocHost(reinterpret_cast<void **>(&h->host_buf), 16 * sizeof(double)));
 
     // Stage the caller's CSC on the device (freed once the padded layout exists).
@@ -509,18 +540,20 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         void *val = nullptr;
         int *rowcnt = nullptr;
         double *y = nullptr;
+        cudaStream_t stream = nullptr;   // the handle's stream (the handle may be gone by destruction)
         ~Staging()
         {
             void *p[] = {col_ptr, pbeg, tile, row_idx, val, rowcnt, y};
             for (void *q : p)
-                if (q) cudaFree(q);
+                if (q) cudaFreeAsync(q, stream);
         }
     } stg;
+    stg.stream = h->stream;
     cudaStream_t st = h->stream;
     const cudaMemcpyKind kin = copy_kind(A->on_device, 1);
-    CKC(dalloc(&stg.col_ptr, h->n + 1));
-    CKC(dalloc(&stg.row_idx, h->nnz));
-    CKC(dalloc_bytes(&stg.val, h->nnz * vb));
+    CKC(halloc(h, &stg.col_ptr, h->n + 1));
+    CKC(halloc(h, &stg.row_idx, h->nnz));
+    CKC(halloc_bytes(h, &stg.val, h->nnz * vb));
     CKC(cudaMemcpyAsync(stg.col_ptr, A->col_ptr, size_t(h->n + 1) * sizeof(int64_t), kin, st));
     if (h->nnz > 0) {
         CKC(cudaMemcpyAsync(stg.row_idx, A->row_idx, size_t(h->nnz) * sizeof(int32_t), kin, st));
@@ -529,7 +562,7 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     const int64_t ny = problem == PCDM_PROBLEM_SVM_DUAL ? h->n : h->m;   // labels: one per example
     if (problem != PCDM_PROBLEM_LASSO) {
         CKC(cudaMemsetAsync(h->b, 0, size_t(h->m) * sizeof(double), st));
-        CKC(dalloc(&stg.y, ny));
+        CKC(halloc(h, &stg.y, ny));
         CKC(cudaMemcpyAsync(stg.y, y, size_t(ny) * sizeof(double), kin, st));
     } else if (b_dtype == PCDM_F64) {
         CKC(cudaMemcpyAsync(h->b, b, size_t(h->m) * sizeof(double), kin, st));
@@ -551,7 +584,7 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         h->err = "col_ptr must start at 0, be non-decreasing and end at nnz";
         return fail(PCDM_EINVAL);
     }
-    CKC(dalloc(&stg.rowcnt, h->m));
+    CKC(halloc(h, &stg.rowcnt, h->m));
     CKC(cudaMemsetAsync(stg.rowcnt, 0, size_t(h->m) * sizeof(int), st));
     switch (h->val_dtype) {
     case PCDM_F64:
@@ -590,8 +623,8 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
 
     // Padded layout: exclusive scan of the padded lengths, then copy and descriptors.
     const int granule = h->val_dtype == PCDM_BF16 ? 8 : 4;
-    CKC(dalloc(&stg.pbeg, h->n + 1));
-    CKC(dalloc(&stg.tile, scan_tile_count(h->n) + 1));
+    CKC(halloc(h, &stg.pbeg, h->n + 1));
+    CKC(halloc(h, &stg.tile, scan_tile_count(h->n) + 1));
     CKC(launch_padded_scan(stg.col_ptr, h->n, granule, stg.pbeg, stg.tile, st));
     int64_t *hP = reinterpret_cast<int64_t *>(h->host_buf + 11);
     CKC(cudaMemcpyAsync(hP, stg.pbeg + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -601,9 +634,9 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
         h->err = "matrix too large for the padded layout (more than 2^34 padded entries)";
         return fail(PCDM_EINVAL);
     }
-    CKC(dalloc(&h->prow, h->P + kSlack));
-    CKC(dalloc_bytes(&h->pval, (h->P + kSlack) * vb));
-    CKC(dalloc_bytes(&h->desc, h->n * 16));
+    CKC(halloc(h, &h->prow, h->P + kSlack));
+    CKC(halloc_bytes(h, &h->pval, (h->P + kSlack) * vb));
+    CKC(halloc_bytes(h, &h->desc, h->n * 16));
     CKC(cudaMemsetAsync(h->prow, 0, size_t(h->P + kSlack) * sizeof(int32_t), st));
     CKC(cudaMemsetAsync(h->pval, 0, size_t((h->P + kSlack) * vb), st));
     switch (h->val_dtype) {
@@ -946,26 +979,26 @@ namespace {
 pcdm_status ensure_as(pcdm_handle h, int64_t tau)
 {
     if (!h->as_sidx) {
-        CK(h, dalloc(&h->as_sidx, h->n));
-        CK(h, dalloc(&h->as_c, h->n));
-        CK(h, dalloc(&h->as_sgn, h->n));
-        CK(h, dalloc(&h->as_u, h->n));
-        CK(h, dalloc(&h->as_q, h->m));
-        CK(h, dalloc(&h->as_rowcnt, h->m + 4));
+        CK(h, halloc(h, &h->as_sidx, h->n));
+        CK(h, halloc(h, &h->as_c, h->n));
+        CK(h, halloc(h, &h->as_sgn, h->n));
+        CK(h, halloc(h, &h->as_u, h->n));
+        CK(h, halloc(h, &h->as_q, h->m));
+        CK(h, halloc(h, &h->as_rowcnt, h->m + 4));
         const int64_t cap = int64_t(h->sms) * 4;
         int64_t blocks = (h->n + kBlock - 1) / kBlock;
         h->as_blocks = int(blocks < 1 ? 1 : (blocks > cap ? cap : blocks));
-        CK(h, dalloc(&h->as_part, 3 * int64_t(h->as_blocks)));
+        CK(h, halloc(h, &h->as_part, 3 * int64_t(h->as_blocks)));
     }
     if (tau > h->as_tau_cap) {
         CK(h, cudaStreamSynchronize(h->stream));
-        if (h->as_H) cudaFree(h->as_H);
-        if (h->as_S) cudaFree(h->as_S);
+        hfree(h, h->as_H);
+        hfree(h, h->as_S);
         h->as_H = nullptr;
         h->as_S = nullptr;
         h->as_tau_cap = 0;
-        CK(h, dalloc(&h->as_H, tau));
-        CK(h, dalloc(&h->as_S, tau));
+        CK(h, halloc(h, &h->as_H, tau));
+        CK(h, halloc(h, &h->as_S, tau));
         h->as_tau_cap = tau;
     }
     return PCDM_OK;
@@ -1113,7 +1146,7 @@ pcdm_status pcdm_backward(pcdm_handle h, const double *dx, int32_t dx_on_device,
     if (s != PCDM_OK) return s;
     const double *dx_dev = dx;
     if (!dx_on_device) {
-        if (!h->as_dx) CK(h, dalloc(&h->as_dx, h->n));
+        if (!h->as_dx) CK(h, halloc(h, &h->as_dx, h->n));
         CK(h, cudaMemcpyAsync(h->as_dx, dx, sizeof(double) * size_t(h->n), cudaMemcpyHostToDevice, h->stream));
         dx_dev = h->as_dx;
     }
@@ -1366,10 +1399,10 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     const size_t xbytes = sizeof(double) * size_t(h->n), gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
     double *x0 = nullptr;
     void *g0 = nullptr;
-    CK(h, dalloc(&x0, h->n));
-    cudaError_t e = dalloc_bytes(&g0, int64_t(gbytes));
+    CK(h, halloc(h, &x0, h->n));
+    cudaError_t e = halloc_bytes(h, &g0, int64_t(gbytes));
     if (e != cudaSuccess) {
-        cudaFree(x0);
+        hfree(h, x0);
         return cuda_fail(h, e, "autotune state copy");
     }
     const int64_t k0 = h->k;
@@ -1442,8 +1475,8 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     cudaEventDestroy(e1);
     if (rs == PCDM_OK && e == cudaSuccess) rs = restore();
     if (rs == PCDM_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(x0);
-    cudaFree(g0);
+    hfree(h, x0);
+    hfree(h, g0);
     h->st_iterations = st_it;
     h->st_updates = st_up;
     h->st_launches = st_la;
@@ -1490,6 +1523,33 @@ pcdm_status pcdm_sample_kind(int32_t kind, uint64_t seed, int64_t k, int64_t n, 
                                        kind == PCDM_SAMPLING_INDEPENDENT ? nullptr : keep_device,
                                        static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "launch_sample_kind");
+    return PCDM_OK;
+}
+
+pcdm_status pcdm_set_memory_cache(uint64_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaMemPool_t pool = nullptr;
+    if (e == cudaSuccess) e = handle_pool(dev, &pool);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        g_cache_limit = bytes;
+        uint64_t limit = bytes;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &limit);
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "pcdm_set_memory_cache");
+    return PCDM_OK;
+}
+
+pcdm_status pcdm_release_cached_memory(void)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaMemPool_t pool = nullptr;
+    if (e == cudaSuccess) e = handle_pool(dev, &pool);
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "pcdm_release_cached_memory");
     return PCDM_OK;
 }
 

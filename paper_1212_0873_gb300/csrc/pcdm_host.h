@@ -203,6 +203,39 @@ inline cudaMemcpyKind copy_kind(int on_device_src, int on_device_dst)
 
 // Synchronise, fold finished event timings into the stats, and read the
 // device status word.  Every call that returns host values goes through here.
+// Device memory of single-problem handles comes from a per-device
+// stream-ordered pool owned by the library (pcdm_api.cu).  The pool keeps
+// freed blocks, up to the cache limit (pcdm_set_memory_cache), for the next
+// handle: creating and destroying a handle then costs microseconds of
+// allocation instead of milliseconds of cudaMalloc and cudaFree.
+cudaError_t handle_pool(int device, cudaMemPool_t *pool);
+
+inline cudaError_t halloc_bytes(pcdm_ctx *h, void **p, int64_t bytes)
+{
+    *p = nullptr;
+    if (bytes <= 0) bytes = 16;
+    cudaMemPool_t pool;
+    cudaError_t e = handle_pool(h->device, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, size_t(bytes), pool, h->stream);
+}
+
+template <typename T>
+inline cudaError_t halloc(pcdm_ctx *h, T **p, int64_t count)
+{
+    void *q = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = halloc_bytes(h, &q, count * int64_t(sizeof(T)));
+    *p = static_cast<T *>(q);
+    return e;
+}
+
+// Stream-ordered free of a halloc block (after the work already enqueued on the handle's stream).
+inline void hfree(pcdm_ctx *h, void *p)
+{
+    if (p) cudaFreeAsync(p, h->stream);
+}
+
 inline pcdm_status sync_check(pcdm_handle h)
 {
     int *hs = reinterpret_cast<int *>(h->host_buf + 9);

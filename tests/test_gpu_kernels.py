@@ -88,3 +88,27 @@ def test_l2_persist_option_is_scoped_to_the_handle():
         ref.run(96, 12, 2)
         assert _rel(s.x(), ref.x) <= 1e-10
     assert _cu_limit_persisting_l2() == before
+
+
+def test_handle_memory_comes_back_from_the_pool():
+    # destroyed handles leave their memory in the library's pool; the next handle
+    # reuses it, and pcdm_release_cached_memory returns it to the device
+    import torch
+    from paper_1212_0873_gb300 import _binding as B
+    torch.cuda.synchronize()
+    B.pcdm_release_cached_memory()
+    free0, _ = torch.cuda.mem_get_info()
+    inst = instances.per_col_instance(400_000, 200_000, 20, nnz_star=100, val_dtype="f64", seed=1041)
+    xs = []
+    for _ in range(3):
+        with Lasso.from_instance(inst) as s:
+            s.step(4096, 5, 1)
+            xs.append(s.x())
+        torch.cuda.synchronize()
+    assert all(np.array_equal(xs[0], x) for x in xs[1:])
+    B.pcdm_set_memory_cache(0)                 # keep nothing: freed memory goes back at synchronisation
+    torch.cuda.synchronize()
+    B.pcdm_release_cached_memory()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (64 << 20)
+    B.pcdm_set_memory_cache(16 << 30)
