@@ -263,6 +263,13 @@ __device__ __forceinline__ double ldcg_hint(const double *p, uint64_t pol)
     asm volatile("ld.global.cg.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
     return v;
 }
+// The high 32-bit word of the double at p (sign, exponent, 20 mantissa bits).
+__device__ __forceinline__ uint32_t ldcg_hi_hint(const double *p, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.cg.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(reinterpret_cast<const char *>(p) + 4), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ float ldcg_hint(const float *p, uint64_t pol)
 {
     float v;

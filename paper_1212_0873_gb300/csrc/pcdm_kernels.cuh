@@ -325,6 +325,75 @@ __device__ __forceinline__ double prox_step(double xi, double grad, double invL,
     return soft_threshold<double>(fma(-grad, ibl, xi), lambda * ibl);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 certificate of a zero LASSO step.
+//
+// With x_i = 0 (either sign), prox_step returns exactly 0 whenever |grad| <=
+// lambda: grad*ibl and lambda*ibl are rounded monotonically, so |u| <= t.  On
+// GB300 an FP64 instruction (FMA, compare, or conversion to or from FP32)
+// occupies a sub-partition's FP64 unit for about 76 cycles per warp, masked
+// lanes included, while most sampled coordinates of a LASSO solve sit at
+// x_i = 0 with |grad_i| < lambda.  The FP64 form therefore first sums
+// grad_i = sum_e v_e g_e in FP32 over images of the FP64 operands made with
+// integer operations, with a bound on the distance to the FP64 sum.  When the
+// bound shows |grad_i| <= lambda the step is 0, the value the FP64 path would
+// return, and the lane needs no FP64 instruction; a warp skips the FP64 block
+// when all its lanes are certified.
+//
+// Image of a double y with high word hi: the FP32 number with y's sign,
+// exponent and 20 leading mantissa bits, its magnitude clamped to [2^-126, inf]:
+// |y| - |image| < 2^-20 |image| for 2^-126 <= |y| < 2^128, |y - image| <= 2^-126
+// below that, and inf (no certificate) above.
+__device__ __forceinline__ float f32_image(uint32_t hi)
+{
+    const uint32_t m = min(max(hi & 0x7FFFFFFFu, 0x38100000u), 0x47F00000u);
+    return __uint_as_float(((m - 0x38000000u) << 3) | (hi & 0x80000000u));
+}
+
+__device__ __forceinline__ uint32_t hi_word(double y)
+{
+    return uint32_t(__double2hiint(y));
+}
+
+// Either zero (the sign bit ignored), by integer compare.
+__device__ __forceinline__ bool is_zero_bits(double y)
+{
+    return (uint64_t(__double_as_longlong(y)) << 1) == 0;
+}
+__device__ __forceinline__ bool is_zero_bits(float y)
+{
+    return (__float_as_uint(y) << 1) == 0;
+}
+
+// Running FP32 sums of one column's products v_e g_e (operands as high words).
+// Error analysis, u = 2^-24, c products, vi, gi the images, M = max |image|,
+// S = sum |vi gi|, D = sum v g exactly, a32 / s32 the FP32 FMA sums:
+//   |D - sum vi gi| <= (2^-19 + 2^-40) S + c 2^-125 M      (images)
+//   |a32 - sum vi gi| <= gamma_c S + c 2^-149,  S <= (s32 + c 2^-149)/(1 - gamma_c)
+//   the FP64 sum differs from D by at most gamma64_2c sum |v g| <= 2^-38 S (c <= 1024)
+// so for c <= 1024, |FP64 sum| <= |a32| + (c + 40) u s32 + c 2^-123 M + 2^-120,
+// the left side of the test below, evaluated rounding upwards.
+struct ZeroCert {
+    float acc = 0.f, sabs = 0.f, mx = 0.f;
+    __device__ __forceinline__ void add(uint32_t hv, uint32_t hg)
+    {
+        const float v = f32_image(hv), g = f32_image(hg);
+        acc = fmaf(v, g, acc);
+        sabs = fmaf(fabsf(v), fabsf(g), sabs);
+        mx = fmaxf(mx, fmaxf(fabsf(v), fabsf(g)));
+    }
+    // true only if the FP64 sum of the c products added is at most lamf <= lambda
+    // in magnitude (inf or NaN operands never certify)
+    __device__ __forceinline__ bool below(int c, float lamf) const
+    {
+        if (c > 1024) return false;
+        float lhs = __fadd_ru(fabsf(acc), 0x1p-120f);
+        lhs = __fmaf_ru(mx, float(c) * 0x1p-123f, lhs);
+        lhs = __fmaf_ru(sabs, float(c + 40) * 0x1p-24f, lhs);
+        return lhs <= lamf;
+    }
+};
+
 // The new coordinate for each objective (argmin over t of the model of eq.
 // (h(x)): grad_i t + (beta L_i / 2) t^2 + Psi_i(x_i + t)), from grad = a_i^T phi(g):
 //   problem 0, LASSO: prox_step above.
@@ -627,11 +696,11 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     const int64_t j0 = int64_t(blockIdx.x) * nt + t;
     const bool own = j0 < a.tau;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + size_t(2) * nt * SB);
-    unsigned long long target = 0;
-    uint32_t phase = 0;   // bit b: parity of the next completion of mbar[b]
     Counters cnt;
     const uint64_t pf = l2_evict_first();   // A, descriptors, x: touched once per iteration
     const uint64_t pl = l2_evict_last();    // the residual buffers: gathered at random rows
+    const float lamf = __double2float_rd(a.lambda);   // the largest float <= lambda (ZeroCert)
+    constexpr bool CERT = sizeof(XT) == 8 && GM == 0;   // the FP64 form tries the FP32 certificate
 
     auto slot = [&](int b) { return smem + (size_t(b) * nt + t) * SB; };
     // the residual buffer that holds g_k at iteration k
@@ -656,10 +725,10 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
             mbar_arrive(&mbar[b]);
         }
     };
-    auto wait_buf = [&](int b) {
-        const bool ok = mbar_wait_bounded(&mbar[b], (phase >> b) & 1u, a.status, a.timeout_ns);
-        phase ^= 1u << b;
-        return ok;
+    // The chunks of iteration it sit in buffer it & 1, whose (it >> 1)-th
+    // completion that is: its phase parity is (it >> 1) & 1.
+    auto wait_buf = [&](int64_t it) {
+        return mbar_wait_bounded(&mbar[it & 1], uint32_t(it >> 1) & 1u, a.status, a.timeout_ns);
     };
 
     if (t == 0) {
@@ -689,7 +758,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         const int64_t k = k0 + it;
         const int b = int(it & 1);
         // the chunks of this iteration's columns (filled during the previous iteration)
-        if (!wait_buf(b)) return;
+        if (!wait_buf(it)) return;
         const unsigned char *my = slot(b);
         const XT *gk = gbuf(k);
         XT *gn = gbuf(k + 1);
@@ -715,43 +784,127 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                 row[4 * q + 2] = int32_t(r4.z);
                 row[4 * q + 3] = int32_t(r4.w);
             }
-            XT gv[kE];
-#pragma unroll
-            for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
-            Chunk<kT, XT> tl;
-            if (valid > kE) ld_chunk_hint<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE, pf);
-            i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
-            d_nn = load_col(a.desc, i_nn, pf);
-            XT gt[kT];
-#pragma unroll
-            for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg_hint(gk + tl.row[e], pl) : XT(0);
             constexpr int EPW = 16 / int(sizeof(VT));
-            XT acc = XT(0);
+            // the step from the gradient (FP64), x_i and the counters
+            auto take_step = [&](XT grad) {
+                const double xn =
+                    coord_step(a.problem, xi, double(grad), double(d_cur.invL), a.inv_beta, a.lambda, a.kappa);
+                const double h64 = xn - xi;
+                h = XT(h64);
+                if (h64 != 0.0) {   // most steps are zero: x_i unchanged
+                    st_hint(a.x + i_cur, xn, pf);
+                    cnt.nonzero += 1;
+                    cnt.scattered += (unsigned long long)valid;
+                }
+            };
+            // every other form: FP64 or FP32 values of g in registers
+            auto full_path = [&]() {
+                XT gv[kE];
 #pragma unroll
-            for (int w = 0; w < VW; ++w) {
-                XT vw[EPW];
-                decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
+                for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
+                Chunk<kT, XT> tl;
+                if (valid > kE) ld_chunk_hint<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE, pf);
+                i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
+                d_nn = load_col(a.desc, i_nn, pf);
+                XT gt[kT];
 #pragma unroll
-                for (int q = 0; q < EPW; ++q)
-                    if (w * EPW + q < valid) acc = fma(vw[q], grad_map<GM>(gv[w * EPW + q]), acc);
+                for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg_hint(gk + tl.row[e], pl) : XT(0);
+                XT acc = XT(0);
+#pragma unroll
+                for (int w = 0; w < VW; ++w) {
+                    XT vw[EPW];
+                    decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
+#pragma unroll
+                    for (int q = 0; q < EPW; ++q)
+                        if (w * EPW + q < valid) acc = fma(vw[q], grad_map<GM>(gv[w * EPW + q]), acc);
+                }
+#pragma unroll
+                for (int e = 0; e < kT; ++e)
+                    if (kE + e < valid) acc = fma(tl.val[e], grad_map<GM>(gt[e]), acc);
+                for (int cs = kE + kT; cs < valid; cs += kE) {
+                    Chunk<kE, XT> tc;
+                    ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
+                    acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
+                }
+                // FP32 sums (the FP32 and BF16 forms): at x_i = 0 the LASSO step is
+                // 0 when |grad| <= lambda, with no FP64 instruction
+                const bool zero_step = sizeof(XT) == 4 && GM == 0 && a.problem == 0 && is_zero_bits(xi) &&
+                                       fabsf(float(acc)) <= lamf;
+                if (!zero_step) take_step(acc);
+            };
+            if constexpr (CERT) {
+                // FP64 form: the gathers bring only the high words of g, enough
+                // for the FP32 certificate of a zero LASSO step (ZeroCert).  A
+                // lane the certificate does not cover (x_i != 0, |grad| near
+                // lambda, the SVM dual) gathers the column again in FP64, from L2:
+                // keeping the FP64 values in registers across the certificate
+                // would spill.
+                uint32_t gh[kE];
+#pragma unroll
+                for (int e = 0; e < kE; ++e) gh[e] = (e < valid) ? ldcg_hi_hint(gk + row[e], pl) : 0u;
+                Chunk<kT, XT> tl;
+                if (valid > kE) ld_chunk_hint<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE, pf);
+                i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
+                d_nn = load_col(a.desc, i_nn, pf);
+                uint32_t gth[kT];
+#pragma unroll
+                for (int e = 0; e < kT; ++e) gth[e] = (kE + e < valid) ? ldcg_hi_hint(gk + tl.row[e], pl) : 0u;
+                bool zero_step = false;
+                if (a.problem == 0 && is_zero_bits(xi)) {
+                    ZeroCert zc;
+#pragma unroll
+                    for (int w = 0; w < VW; ++w) {
+                        const uint4 u = reinterpret_cast<const uint4 *>(my + 64)[w];
+                        if (2 * w < valid) zc.add(u.y, gh[2 * w]);
+                        if (2 * w + 1 < valid) zc.add(u.w, gh[2 * w + 1]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < kT; ++e)
+                        if (kE + e < valid) zc.add(hi_word(tl.val[e]), gth[e]);
+                    for (int cs = kE + kT; cs < valid; cs += kT) {
+                        Chunk<kT, XT> tc;
+                        ld_chunk_hint<kT>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
+                        uint32_t gc[kT];
+#pragma unroll
+                        for (int e = 0; e < kT; ++e) gc[e] = (cs + e < valid) ? ldcg_hi_hint(gk + tc.row[e], pl) : 0u;
+#pragma unroll
+                        for (int e = 0; e < kT; ++e)
+                            if (cs + e < valid) zc.add(hi_word(tc.val[e]), gc[e]);
+                    }
+                    zero_step = zc.below(valid, lamf);
+                }
+                if (!zero_step) {
+                    // FP64 sum over the whole column: the first chunk (rows and
+                    // values read again from the slot), the rest from memory
+                    XT gf[kE];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const uint4 r4 = reinterpret_cast<const uint4 *>(my)[q];
+                        const int32_t rq[4] = {int32_t(r4.x), int32_t(r4.y), int32_t(r4.z), int32_t(r4.w)};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            gf[4 * q + e] = (4 * q + e < valid) ? ldcg_hint(gk + rq[e], pl) : XT(0);
+                    }
+                    XT acc = XT(0);
+#pragma unroll
+                    for (int w = 0; w < VW; ++w) {
+                        XT vw[EPW];
+                        decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
+#pragma unroll
+                        for (int q = 0; q < EPW; ++q)
+                            if (w * EPW + q < valid) acc = fma(vw[q], gf[w * EPW + q], acc);
+                    }
+                    for (int cs = kE; cs < valid; cs += kE) {
+                        Chunk<kE, XT> tc;
+                        ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
+                        acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
+                    }
+                    take_step(acc);
+                }
+            } else {
+                full_path();
             }
-#pragma unroll
-            for (int e = 0; e < kT; ++e)
-                if (kE + e < valid) acc = fma(tl.val[e], grad_map<GM>(gt[e]), acc);
-            for (int cs = kE + kT; cs < valid; cs += kE) {
-                Chunk<kE, XT> tc;
-                ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
-                acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
-            }
-            const double xn = coord_step(a.problem, xi, double(acc), double(d_cur.invL), a.inv_beta, a.lambda, a.kappa);
-            const double h64 = xn - xi;
-            h = XT(h64);
-            if (h64 != 0.0) st_hint(a.x + i_cur, xn, pf);   // most steps are zero: x_i unchanged
             cnt.gathered += (unsigned long long)valid;
-            if (h64 != 0.0) {
-                cnt.nonzero += 1;
-                cnt.scattered += (unsigned long long)valid;
-            }
         }
 
         // ---------------- scatter into the other buffer (g_{k-1} -> g_{k+1})
@@ -759,8 +912,8 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         // which nobody writes during iteration k.  The other buffer holds g_{k-1}
         // and receives the steps of iterations k-1 and k.  The previous column's
         // chunk sits in slot b^1, so it is re-scattered before that slot is refilled.
-        if (own && h_prev != XT(0)) slot_scatter<VT, XT>(a, slot(b ^ 1), d_prev, h_prev, gn, pf, pl);
-        if (own && h != XT(0)) slot_scatter<VT, XT>(a, my, d_cur, h, gn, pf, pl);
+        if (own && !is_zero_bits(h_prev)) slot_scatter<VT, XT>(a, slot(b ^ 1), d_prev, h_prev, gn, pf, pl);
+        if (own && !is_zero_bits(h)) slot_scatter<VT, XT>(a, my, d_cur, h, gn, pf, pl);
         h_prev = h;
         d_prev = d_cur;
 
@@ -770,12 +923,13 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
         // it, so the release does not wait for them, and they overlap the wait.
         // (The column's tail is not prefetched into L2: the extra TMA issue cost
         // on the last block to arrive outweighed the shorter tail loads.)
-        target += gridDim.x;
+        // the barrier counter is 0 at launch and gains gridDim.x per iteration
+        const unsigned long long target = (unsigned long long)(it + 1) * gridDim.x;
         grid_arrive(a.bar);
         fence_proxy_async_shared();
         fill(b ^ 1, d_nxt, i_nxt, own);
         if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) {
-            wait_buf(b ^ 1);   // the copies just issued land before the block leaves
+            wait_buf(it + 1);   // the copies just issued land before the block leaves
             return;
         }
         i_cur = i_nxt;
@@ -785,10 +939,10 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     }
     // Both buffers equal again: the last iteration's steps (still in slot
     // (iters-1)&1) go into the buffer that holds g_{k0+iters-1}.
-    if (iters > 0 && own && h_prev != XT(0))
+    if (iters > 0 && own && !is_zero_bits(h_prev))
         slot_scatter<VT, XT>(a, slot(int((iters - 1) & 1)), d_prev, h_prev, gbuf(k0 + iters - 1), pf, pl);
     // the last fill (the chunks of i_{k0+iters}) lands before the block leaves
-    wait_buf(int(iters & 1));
+    wait_buf(iters);
     // S_{k0+iters} for the caller (the sample of the next launch).
     if (own) sample_buf(a, k0 + iters)[j0] = i_cur;
     flush_counters(cnt, a.counters);
