@@ -71,7 +71,7 @@ def parse():
     p.add_argument("--no-l2-persist", action="store_true",
                    help="FP64: leave the context's L2 persisting-lines limit as it is (no opts.l2_persist)")
     p.add_argument("--tuning", default=None,
-                   help="kernel,lanes_per_col,threads_per_block,heads set by hand (pcdm_set_tuning) instead of "
+                   help="kernel,lanes_per_col,threads_per_block,heads[,zero_cert] set by hand (pcdm_set_tuning) instead of "
                         "pcdm_autotune, e.g. 0,1,448,1 for the pipelined kernel with 448-thread blocks")
     p.add_argument("--sweep", action="store_true", help="print the omega x tau x dtype table of the scale workload")
     p.add_argument("--huge", action="store_true", help="time the 4e9-nonzero configuration (about 140 GB of HBM)")
@@ -160,7 +160,10 @@ def traffic_per_update(a, tuning):
     ent = d.get("workloads", {}).get(key)
     if ent is None or tuning is None:
         return None, None
-    if any(ent.get("tuning", {}).get(f) != tuning.get(f) for f in ("kernel", "lanes_per_col", "heads")):
+    if any(ent.get("tuning", {}).get(f, 0) != tuning.get(f, 0) for f in ("kernel", "lanes_per_col", "heads")):
+        return None, None
+    # the zero-step certificate changes the kernel's loads (taken without it unless recorded)
+    if int(ent.get("tuning", {}).get("zero_cert", 0)) != (1 if tuning.get("zero_cert", 0) == 1 else 0):
         return None, None
     return float(ent["dram_bytes_per_update"]), ent["tuning"]
 
@@ -635,9 +638,12 @@ def run_pcdm(a, rank, local, world):
     solver = Lasso.from_instance(inst, profile=True, **kw)
     omega = solver.omega
     if a.tuning:
-        k, w, t, hd = (int(v) for v in a.tuning.split(","))
-        solver.set_tuning(k, w, t, hd)
-        tuning = {"kernel": k, "lanes_per_col": w, "threads_per_block": t, "heads": hd, "set_by_hand": True}
+        f = [int(v) for v in a.tuning.split(",")]
+        k, w, t, hd = f[:4]
+        zc = f[4] if len(f) > 4 else -1
+        solver.set_tuning(k, w, t, hd, zc)
+        tuning = {"kernel": k, "lanes_per_col": w, "threads_per_block": t, "heads": hd, "zero_cert": zc,
+                  "set_by_hand": True}
     else:
         tuning = solver.autotune(a.tau, 30) if (not a.unfused and not a.no_tune) else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2

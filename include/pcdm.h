@@ -268,7 +268,8 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
  * state (which is restored afterwards; the counters of pcdm_get_stats are not
  * changed).  Candidates: the pipelined one-lane-per-column kernel with blocks
  * of 128 .. 448 threads (the tau positions per block; when tau fits one pass of
- * the grid), each with and without the column heads, its rounds form with blocks of 128 or 256 threads (several
+ * the grid), each with and without the column heads (and, in the FP64 form of LASSO,
+ * with and without zero_cert), its rounds form with blocks of 128 or 256 threads (several
  * positions per thread and iteration), the fused kernel with 1 .. 32 lanes per
  * column (its scatter reloads the column), and the two-kernel form with 1, 4 or
  * 16 lanes.  The fastest is kept for later pcdm_step /
@@ -285,15 +286,26 @@ typedef struct {
                                    per-column head array, n * (64 + 16 sizeof(value)) bytes built
                                    on first use when free device memory holds four times that;
                                    0 = two copies from the padded CSC arrays */
+    int32_t zero_cert;          /* pipelined kernel, FP64 form, LASSO: 1 = before the FP64 sum
+                                   a_i^T g, bound it in FP32 from the high words of the operands
+                                   and take the step as 0 when the bound shows |a_i^T g| <= lambda
+                                   at x_i = 0 (the same step the FP64 sum gives: eq. (h(x)) with
+                                   x_i = 0 is 0 exactly when |grad_i| <= lambda); a warp whose
+                                   lanes are all certified issues no FP64 instruction;
+                                   0 = the FP64 sum for every column; -1 (pcdm_set_tuning only) =
+                                   the built-in rule, on when nnz <= 8 n.  The FP32 and BF16
+                                   forms always compare their FP32 gradient with lambda rounded
+                                   down, an exact test, and ignore this field. */
     double us_per_iteration;    /* measured */
 } pcdm_tuning;
 
 pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_tuning *best);
 
 /* Choose the iteration kernel by hand (the fields of pcdm_tuning; us_per_iteration
- * is ignored; heads 0 or 1; threads_per_block a multiple of 32, up to 448 for kernel 0 and
- * 256 for kernel 3), or return to the built-in rule with t = NULL.  A pipelined
- * kernel that cannot hold tau at that block size falls back to the fused one. */
+ * is ignored; heads 0 or 1; zero_cert -1, 0 or 1; threads_per_block a multiple of 32,
+ * up to 448 for kernel 0 and 256 for kernel 3), or return to the built-in rule with
+ * t = NULL.  A pipelined kernel that cannot hold tau at that block size falls back to
+ * the fused one. */
 pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t);
 
 /* Recompute g = A x - b in FP64 (stored in g's dtype). */

@@ -25,7 +25,7 @@ class pcdm_csc(ctypes.Structure):
 
 class pcdm_tuning(ctypes.Structure):
     _fields_ = [("kernel", _i32), ("lanes_per_col", _i32), ("threads_per_block", _i32), ("heads", _i32),
-                ("us_per_iteration", _dbl)]
+                ("zero_cert", _i32), ("us_per_iteration", _dbl)]
 
 
 class pcdm_opts(ctypes.Structure):
@@ -490,12 +490,12 @@ def pcdm_autotune(h, tau, trial_iters):
     return {name: getattr(t, name) for name, _ in pcdm_tuning._fields_}
 
 
-def pcdm_set_tuning(h, kernel=None, lanes_per_col=1, threads_per_block=0, heads=1):
+def pcdm_set_tuning(h, kernel=None, lanes_per_col=1, threads_per_block=0, heads=1, zero_cert=-1):
     """kernel None: back to the built-in rule."""
     if kernel is None:
         _check(lib().pcdm_set_tuning(h, None), h)
         return
-    t = pcdm_tuning(int(kernel), int(lanes_per_col), int(threads_per_block), int(heads), 0.0)
+    t = pcdm_tuning(int(kernel), int(lanes_per_col), int(threads_per_block), int(heads), int(zero_cert), 0.0)
     _check(lib().pcdm_set_tuning(h, ctypes.byref(t)), h)
 
 

@@ -289,7 +289,9 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
                 h->g2_valid = false;
             }
             if (!h->g2_valid) CK(h, cudaMemcpyAsync(h->g2, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
-            CK(h, Kernels<VT, XT>::fused_pipe(a, sh, h->k, iters, h->stream));
+            // the FP64 zero-step certificate: by the tuning, else for short columns
+            const bool zc = h->tune_zc < 0 ? (h->nnz <= 8 * h->n) : (h->tune_zc == 1);
+            CK(h, Kernels<VT, XT>::fused_pipe(a, sh, h->k, iters, zc, h->stream));
             h->g2_valid = true;
         } else {
             pcdm_status s = fused_shape<VT, XT>(h, tau, h->tune_kernel == 1 ? h->tune_W : h->W, &sh);
@@ -1366,9 +1368,11 @@ pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
         h->tune_W = 0;
         h->tune_threads = 0;
         h->tune_heads = 1;
+        h->tune_zc = -1;
         return PCDM_OK;
     }
     if (t->heads != 0 && t->heads != 1) return set_err(h, PCDM_EINVAL, "heads must be 0 or 1");
+    if (t->zero_cert < -1 || t->zero_cert > 1) return set_err(h, PCDM_EINVAL, "zero_cert must be -1, 0 or 1");
     if (h->problem != PCDM_PROBLEM_LASSO && t->kernel == 3)
         return set_err(h, PCDM_EINVAL, "the SVM dual and logistic regression run in kernels 0, 1 and 2");
     const bool lanes_ok = t->lanes_per_col == 1 || t->lanes_per_col == 2 || t->lanes_per_col == 4 ||
@@ -1383,6 +1387,7 @@ pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
     h->tune_W = t->lanes_per_col;
     h->tune_threads = t->threads_per_block;
     h->tune_heads = t->heads;
+    h->tune_zc = t->zero_cert;
     return PCDM_OK;
 }
 
@@ -1408,7 +1413,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     const int64_t k0 = h->k;
     const int64_t st_it = h->st_iterations, st_up = h->st_updates, st_la = h->st_launches, st_ke = h->st_kernels;
     const double st_ms = h->st_kernel_ms;
-    const int keep[4] = {h->tune_kernel, h->tune_W, h->tune_threads, h->tune_heads};
+    const int keep[5] = {h->tune_kernel, h->tune_W, h->tune_threads, h->tune_heads, h->tune_zc};
     auto restore = [&]() -> pcdm_status {
         CK(h, cudaMemcpyAsync(h->x, x0, xbytes, cudaMemcpyDeviceToDevice, h->stream));
         CK(h, cudaMemcpyAsync(h->g, g0, gbytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -1420,18 +1425,23 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     CK(h, cudaMemcpyAsync(x0, h->x, xbytes, cudaMemcpyDeviceToDevice, h->stream));
     CK(h, cudaMemcpyAsync(g0, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
     struct Cand {
-        int kernel, W, threads, heads;
+        int kernel, W, threads, heads, zc;
     };
+    // the zero-step certificate is a choice of the FP64 form of LASSO only
+    const bool zc_choice = h->xg_dtype == PCDM_F64 && h->problem == PCDM_PROBLEM_LASSO;
     std::vector<Cand> cands;
-    for (int hd : {1, 0})
-        for (int t : {128, 192, 256, 320, 384, 448}) cands.push_back({0, 1, t, hd});
-    for (int W : {1, 2, 4, 8, 16, 32}) cands.push_back({1, W, 0, 1});
-    for (int W : {1, 4, 16}) cands.push_back({2, W, 0, 1});
-    for (int t : {128, 256}) cands.push_back({3, 1, t, 1});
+    for (int zc : {1, 0}) {
+        if (zc == 0 && !zc_choice) continue;
+        for (int hd : {1, 0})
+            for (int t : {128, 192, 256, 320, 384, 448}) cands.push_back({0, 1, t, hd, zc_choice ? zc : -1});
+    }
+    for (int W : {1, 2, 4, 8, 16, 32}) cands.push_back({1, W, 0, 1, -1});
+    for (int W : {1, 4, 16}) cands.push_back({2, W, 0, 1, -1});
+    for (int t : {128, 256}) cands.push_back({3, 1, t, 1, -1});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
-    Cand bestc{-1, 0, 0, 1};
+    Cand bestc{-1, 0, 0, 1, -1};
     double best_us = 0.0;
     pcdm_status rs = PCDM_OK;
     for (const Cand &c : cands) {
@@ -1456,6 +1466,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
         h->tune_W = c.W;
         h->tune_threads = c.threads;
         h->tune_heads = c.heads;
+        h->tune_zc = c.zc;
         if ((rs = restore()) != PCDM_OK) break;
         if ((rs = pcdm_step(h, tau, 2, 0x5eedULL)) != PCDM_OK) break;   // warm-up (first launch of a shape)
         if ((rs = restore()) != PCDM_OK) break;
@@ -1493,17 +1504,20 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
         h->tune_W = keep[1];
         h->tune_threads = keep[2];
         h->tune_heads = keep[3];
+        h->tune_zc = keep[4];
         return rs;
     }
     h->tune_kernel = bestc.kernel;
     h->tune_W = bestc.W;
     h->tune_threads = bestc.threads;
     h->tune_heads = bestc.heads;
+    h->tune_zc = bestc.zc;
     if (best) {
         best->kernel = bestc.kernel;
         best->lanes_per_col = bestc.W;
         best->threads_per_block = bestc.threads;
         best->heads = bestc.heads && !h->head_off ? 1 : 0;
+        best->zero_cert = bestc.kernel == 0 && zc_choice ? bestc.zc : 0;
         best->us_per_iteration = best_us;
     }
     return PCDM_OK;

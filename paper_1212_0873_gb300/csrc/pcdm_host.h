@@ -96,6 +96,7 @@ struct pcdm_ctx {
     int tune_W = 0;
     int tune_threads = 0;           // block size of the pipelined kernel (0: built-in rule)
     int tune_heads = 1;             // pipelined kernels read the column heads (when they fit)
+    int tune_zc = -1;               // FP32 certificate of zero steps in the FP64 pipelined kernel (-1: built-in rule)
     bool head_off = false;          // the column heads did not fit in device memory
     bool rounds_last = false;       // the last segment ran the pipelined rounds kernel (S_{k} not left drawn)
     bool sample_valid = false;

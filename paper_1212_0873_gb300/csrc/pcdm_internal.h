@@ -120,7 +120,7 @@ struct Kernels {
     static int fused_max_blocks(int W, int threads);
     // Pipelined persistent kernel (one lane per column, tau <= blocks * threads).
     static cudaError_t fused_pipe(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
-                                  cudaStream_t st);
+                                  bool zero_cert, cudaStream_t st);
     static int pipe_max_blocks(int threads);
     // Pipelined kernel for tau beyond the grid (several positions per thread per iteration).
     static cudaError_t fused_pipe_rounds(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,

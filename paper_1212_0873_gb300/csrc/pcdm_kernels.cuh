@@ -685,7 +685,7 @@ __device__ __forceinline__ void slot_scatter(const IterArgs<VT, XT> &a, const un
     }
 }
 
-template <typename VT, typename XT, int GM = 0>
+template <typename VT, typename XT, int GM = 0, bool ZC = false>
 __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     const uint64_t pf = l2_evict_first();   // A, descriptors, x: touched once per iteration
     const uint64_t pl = l2_evict_last();    // the residual buffers: gathered at random rows
     const float lamf = __double2float_rd(a.lambda);   // the largest float <= lambda (ZeroCert)
-    constexpr bool CERT = sizeof(XT) == 8 && GM == 0;   // the FP64 form tries the FP32 certificate
+    constexpr bool CERT = sizeof(XT) == 8 && GM == 0 && ZC;   // the FP64 form tries the FP32 certificate
 
     auto slot = [&](int b) { return smem + (size_t(b) * nt + t) * SB; };
     // the residual buffer that holds g_k at iteration k
@@ -839,9 +839,9 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                 // lambda, the SVM dual) gathers the column again in FP64, from L2:
                 // keeping the FP64 values in registers across the certificate
                 // would spill.
-                uint32_t gh[kE];
+                XT gv[kE];
 #pragma unroll
-                for (int e = 0; e < kE; ++e) gh[e] = (e < valid) ? ldcg_hi_hint(gk + row[e], pl) : 0u;
+                for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
                 Chunk<kT, XT> tl;
                 if (valid > kE) ld_chunk_hint<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE, pf);
                 i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
@@ -855,8 +855,8 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
 #pragma unroll
                     for (int w = 0; w < VW; ++w) {
                         const uint4 u = reinterpret_cast<const uint4 *>(my + 64)[w];
-                        if (2 * w < valid) zc.add(u.y, gh[2 * w]);
-                        if (2 * w + 1 < valid) zc.add(u.w, gh[2 * w + 1]);
+                        if (2 * w < valid) zc.add(u.y, hi_word(gv[2 * w]));
+                        if (2 * w + 1 < valid) zc.add(u.w, hi_word(gv[2 * w + 1]));
                     }
 #pragma unroll
                     for (int e = 0; e < kT; ++e)
@@ -874,17 +874,8 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                     zero_step = zc.below(valid, lamf);
                 }
                 if (!zero_step) {
-                    // FP64 sum over the whole column: the first chunk (rows and
-                    // values read again from the slot), the rest from memory
-                    XT gf[kE];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint4 r4 = reinterpret_cast<const uint4 *>(my)[q];
-                        const int32_t rq[4] = {int32_t(r4.x), int32_t(r4.y), int32_t(r4.z), int32_t(r4.w)};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            gf[4 * q + e] = (4 * q + e < valid) ? ldcg_hint(gk + rq[e], pl) : XT(0);
-                    }
+                    // FP64 sum over the whole column: the first chunk from the
+                    // slot and registers, the rest from memory
                     XT acc = XT(0);
 #pragma unroll
                     for (int w = 0; w < VW; ++w) {
@@ -892,7 +883,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                         decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
 #pragma unroll
                         for (int q = 0; q < EPW; ++q)
-                            if (w * EPW + q < valid) acc = fma(vw[q], gf[w * EPW + q], acc);
+                            if (w * EPW + q < valid) acc = fma(vw[q], gv[w * EPW + q], acc);
                     }
                     for (int cs = kE; cs < valid; cs += kE) {
                         Chunk<kE, XT> tc;
@@ -1565,29 +1556,32 @@ int Kernels<VT, XT>::pipe_max_blocks(int threads)
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     const size_t bytes = pipe_smem_bytes<VT>(threads);
-    // the same grid serves both gradient maps: the smaller co-resident grid of the two
-    int per_sm_map = 0;
-    if (cudaFuncSetAttribute(k_fused_pipe<VT, XT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_fused_pipe<VT, XT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) !=
-            cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_pipe<VT, XT, 0>, threads, bytes) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_map, k_fused_pipe<VT, XT, 1>, threads, bytes) !=
-            cudaSuccess)
-        return 0;
-    return (per_sm < per_sm_map ? per_sm : per_sm_map) * sms;
+    // the same grid serves every variant (gradient maps, zero-step certificate):
+    // the smallest co-resident grid of them
+    const void *fns[3] = {(const void *)k_fused_pipe<VT, XT, 0, false>, (const void *)k_fused_pipe<VT, XT, 1, false>,
+                          (const void *)k_fused_pipe<VT, XT, 0, true>};
+    const int nf = sizeof(XT) == 8 ? 3 : 2;
+    int best = -1;
+    for (int f = 0; f < nf; ++f) {
+        if (cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[f], threads, bytes) != cudaSuccess) return 0;
+        if (best < 0 || per_sm < best) best = per_sm;
+    }
+    return best * sms;
 }
 
 template <typename VT, typename XT>
 cudaError_t Kernels<VT, XT>::fused_pipe(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
-                                        cudaStream_t st)
+                                        bool zero_cert, cudaStream_t st)
 {
     if (iters <= 0 || a.tau <= 0) return cudaSuccess;
     IterArgs<VT, XT> args = a;
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
-    const void *fn = a.problem == 2 ? (const void *)k_fused_pipe<VT, XT, 1> : (const void *)k_fused_pipe<VT, XT, 0>;
+    // the certificate applies to the FP64 form of LASSO (the FP32 forms test |grad| <= lambda exactly anyway)
+    const void *fn = a.problem == 2 ? (const void *)k_fused_pipe<VT, XT, 1, false>
+                     : (sizeof(XT) == 8 && zero_cert && a.problem == 0) ? (const void *)k_fused_pipe<VT, XT, 0, true>
+                                                                       : (const void *)k_fused_pipe<VT, XT, 0, false>;
     return cudaLaunchCooperativeKernel(fn, dim3(unsigned(sh.blocks)), dim3(unsigned(sh.threads)), params,
                                        pipe_smem_bytes<VT>(sh.threads), st);
 }

@@ -129,11 +129,12 @@ class Lasso:
         """Pick the fastest iteration kernel for tau on this matrix (pcdm_autotune)."""
         return B.pcdm_autotune(self._h, tau, trial_iters)
 
-    def set_tuning(self, kernel=None, lanes_per_col=1, threads_per_block=0, heads=1):
+    def set_tuning(self, kernel=None, lanes_per_col=1, threads_per_block=0, heads=1, zero_cert=-1):
         """Choose the iteration kernel (0 pipelined, 1 fused, 2 two-kernel, 3 pipelined
-        rounds) by hand, and whether the pipelined kernels read the column heads;
-        None returns to the built-in rule."""
-        B.pcdm_set_tuning(self._h, kernel, lanes_per_col, threads_per_block, heads)
+        rounds) by hand, whether the pipelined kernels read the column heads, and
+        whether the FP64 pipelined kernel certifies zero steps in FP32 first (-1: the
+        built-in rule); None returns to the built-in rule."""
+        B.pcdm_set_tuning(self._h, kernel, lanes_per_col, threads_per_block, heads, zero_cert)
 
     def step_async(self, updates, seed=0, threads=0):
         """Asynchronous updates (pcdm_step_async); threads = 1 is the serial method."""

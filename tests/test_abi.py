@@ -49,9 +49,9 @@ def test_struct_layout_matches_header(B):
 #include <stddef.h>
 #include "pcdm.h"
 int main(void) {
-  printf("%zu %zu %zu\n", sizeof(pcdm_csc), sizeof(pcdm_opts), sizeof(pcdm_stats));
-  printf("%zu %zu %zu\n", offsetof(pcdm_csc, val_dtype), offsetof(pcdm_opts, barrier_timeout_ns),
-         offsetof(pcdm_stats, iter_kernel_ms));
+  printf("%zu %zu %zu %zu\n", sizeof(pcdm_csc), sizeof(pcdm_opts), sizeof(pcdm_stats), sizeof(pcdm_tuning));
+  printf("%zu %zu %zu %zu\n", offsetof(pcdm_csc, val_dtype), offsetof(pcdm_opts, barrier_timeout_ns),
+         offsetof(pcdm_stats, iter_kernel_ms), offsetof(pcdm_tuning, us_per_iteration));
   return 0;
 }
 """
@@ -65,9 +65,11 @@ int main(void) {
     assert sizes[0] == ctypes.sizeof(B.pcdm_csc)
     assert sizes[1] == ctypes.sizeof(B.pcdm_opts)
     assert sizes[2] == ctypes.sizeof(B.pcdm_stats)
-    assert sizes[3] == B.pcdm_csc.val_dtype.offset
-    assert sizes[4] == B.pcdm_opts.barrier_timeout_ns.offset
-    assert sizes[5] == B.pcdm_stats.iter_kernel_ms.offset
+    assert sizes[3] == ctypes.sizeof(B.pcdm_tuning)
+    assert sizes[4] == B.pcdm_csc.val_dtype.offset
+    assert sizes[5] == B.pcdm_opts.barrier_timeout_ns.offset
+    assert sizes[6] == B.pcdm_stats.iter_kernel_ms.offset
+    assert sizes[7] == B.pcdm_tuning.us_per_iteration.offset
 
 
 def test_default_opts_and_status_strings(B):

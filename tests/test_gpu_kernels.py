@@ -1,5 +1,6 @@
 """Every iteration kernel (pipelined, fused with several lane widths, two-kernel,
-pipelined rounds; the pipelined ones with and without the column heads)
+pipelined rounds; the pipelined ones with and without the column heads, the
+pipelined one also with and without the FP32 certificate of zero steps)
 selected by hand through pcdm_set_tuning follows the oracle;
 the rounds kernel also with several positions per thread (tau beyond the grid)."""
 import numpy as np
@@ -25,9 +26,9 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b))) / max(float(np.max(np.abs(b))), 1e-300)
 
 
-# (kernel, lanes per column, threads per block, column heads)
-CHOICES = [(0, 1, 64, 1), (0, 1, 448, 1), (0, 1, 128, 0), (1, 1, 0, 1), (1, 4, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1),
-           (2, 16, 0, 1), (3, 1, 128, 1), (3, 1, 256, 0)]
+# (kernel, lanes per column, threads per block, column heads[, zero-step certificate])
+CHOICES = [(0, 1, 64, 1), (0, 1, 448, 1), (0, 1, 128, 0), (0, 1, 64, 1, 1), (0, 1, 128, 0, 1), (0, 1, 448, 1, 0),
+           (1, 1, 0, 1), (1, 4, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1), (2, 16, 0, 1), (3, 1, 128, 1), (3, 1, 256, 0)]
 
 
 @pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])

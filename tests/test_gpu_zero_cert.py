@@ -78,7 +78,8 @@ def _rel(a, b):
 # (scale of the values, scale of b): ordinary; large b with small values; images
 # of the values clamped to 2^-126; images of b infinite; products underflowing FP32.
 SCALES = [(1.0, 1.0), (2.0 ** -100, 2.0 ** 100), (2.0 ** -130, 2.0 ** 20), (1.0, 2.0 ** 130), (2.0 ** -70, 2.0 ** -70)]
-CHOICES = [(0, 1, 448, 1), (0, 1, 64, 0)]
+# (kernel, lanes per column, threads per block, column heads, zero-step certificate on)
+CHOICES = [(0, 1, 448, 1, 1), (0, 1, 64, 0, 1)]
 
 
 @pytest.mark.parametrize("choice", CHOICES)
