@@ -176,7 +176,10 @@ bool pipe_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads = 0
     threads = (threads + 31) / 32 * 32;
     if (threads < 32) threads = 32;
     if (threads > kPipeMaxBlock) return false;
-    const int64_t blocks = (tau + threads - 1) / threads;
+    int64_t blocks = (tau + threads - 1) / threads;
+    // the kernel deals positions round-robin over its blocks: one block per SM
+    // when tau leaves SMs without a block
+    if (blocks < h->sms) blocks = tau < h->sms ? tau : h->sms;
     const int cap = Kernels<VT, XT>::pipe_max_blocks(int(threads));
     if (cap <= 0 || blocks > cap) return false;
     sh->W = 1;

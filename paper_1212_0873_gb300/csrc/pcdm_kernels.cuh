@@ -693,7 +693,10 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
     constexpr int SB = pipe_slot_bytes<VT>();
     constexpr int G = pad_granule<VT>();
     const int nt = blockDim.x, t = threadIdx.x;
-    const int64_t j0 = int64_t(blockIdx.x) * nt + t;
+    // Sampled position j belongs to block j mod gridDim.x, thread j / gridDim.x:
+    // with one block per SM the positions spread over every SM even when tau
+    // does not fill the last block.
+    const int64_t j0 = int64_t(t) * gridDim.x + blockIdx.x;
     const bool own = j0 < a.tau;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + size_t(2) * nt * SB);
     Counters cnt;
