@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--tuning", default=None,
                    help="kernel,lanes_per_col,threads_per_block,heads[,zero_cert] set by hand (pcdm_set_tuning) instead of "
                         "pcdm_autotune, e.g. 0,1,448,1 for the pipelined kernel with 448-thread blocks")
+    p.add_argument("--no-gather-ceiling", action="store_true",
+                   help="skip the random-gather ceiling measured beside the roofline")
     p.add_argument("--sweep", action="store_true", help="print the omega x tau x dtype table of the scale workload")
     p.add_argument("--huge", action="store_true", help="time the 4e9-nonzero configuration (about 140 GB of HBM)")
     return p.parse_args()
@@ -166,6 +168,42 @@ def traffic_per_update(a, tuning):
     if int(ent.get("tuning", {}).get("zero_cert", 0)) != (1 if tuning.get("zero_cert", 0) == 1 else 0):
         return None, None
     return float(ent["dram_bytes_per_update"]), ent["tuning"]
+
+
+def gather_ceiling(m, elem_bytes, kernel_gathers_per_s, n_idx=1 << 24, reps=5):
+    """Random-gather rates of this GPU as a second ceiling for the iteration
+    kernel, whose time goes to scattered gathers of g: torch.index_select of
+    elem_bytes-wide values at n_idx uniform random int32 indices, from a vector of
+    m entries (the size of one residual buffer, L2-resident) and from a 4 GiB one
+    (every gather a DRAM access).  Reported beside the kernel's own rate of
+    gathered nonzeros per second."""
+    import torch
+    dt = torch.float64 if elem_bytes == 8 else torch.float32
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(12345)
+    out = {}
+    for name, size in (("l2_resident", int(m)), ("hbm", (4 << 30) // elem_bytes)):
+        src = torch.ones(size, dtype=dt, device="cuda")
+        idx = torch.randint(0, size, (n_idx,), generator=gen, device="cuda", dtype=torch.int32)
+        dst = torch.empty(n_idx, dtype=dt, device="cuda")
+        for _ in range(2):
+            torch.index_select(src, 0, idx, out=dst)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.index_select(src, 0, idx, out=dst)
+        e1.record()
+        e1.synchronize()
+        out["gathers_per_s_" + name] = n_idx * reps / (e0.elapsed_time(e1) / 1e3)
+        del src, idx, dst
+    torch.cuda.empty_cache()
+    out["kernel_gathers_per_s"] = kernel_gathers_per_s
+    out["kernel_frac_of_l2_resident"] = kernel_gathers_per_s / out["gathers_per_s_l2_resident"]
+    out["how"] = ("torch.index_select of %d-byte values at %d uniform random int32 indices from a vector of "
+                  "%d entries (one residual buffer) and from a 4 GiB vector; kernel: gathered nonzeros per "
+                  "second of the iteration kernel's launches" % (elem_bytes, n_idx, int(m)))
+    return out
 
 
 class ClockSampler:
@@ -705,6 +743,8 @@ def run_pcdm(a, rank, local, world):
                            "k_fused_pipe (persistent PCDM1 iterations)"), "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes / launches, "avg_launch_ms": avg_launch_s * 1e3,
                 "launches": st["iter_launches"], "traffic_taken_at": tpu_tuning}
+    if avg_launch_s > 0 and not a.no_gather_ceiling:
+        roofline["gather_ceiling"] = gather_ceiling(a.n, sg, st["gathered_nnz"] / launches / avg_launch_s)
 
     # end to end through the public API from pinned host memory
     e2e = None
