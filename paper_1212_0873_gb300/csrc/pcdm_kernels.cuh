@@ -355,6 +355,13 @@ __device__ __forceinline__ uint32_t hi_word(double y)
     return uint32_t(__double2hiint(y));
 }
 
+// |v| <= lam for a finite lam >= 0, by integer compare of the bit patterns
+// (non-negative doubles order as their bits; a NaN v compares above any finite lam).
+__device__ __forceinline__ bool abs_le_bits(double v, double lam)
+{
+    return (uint64_t(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull) <= uint64_t(__double_as_longlong(lam));
+}
+
 // Either zero (the sign bit ignored), by integer compare.
 __device__ __forceinline__ bool is_zero_bits(double y)
 {
@@ -829,10 +836,16 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                     ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
                     acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
                 }
-                // FP32 sums (the FP32 and BF16 forms): at x_i = 0 the LASSO step is
-                // 0 when |grad| <= lambda, with no FP64 instruction
-                const bool zero_step = sizeof(XT) == 4 && GM == 0 && a.problem == 0 && is_zero_bits(xi) &&
-                                       fabsf(float(acc)) <= lamf;
+                // At x_i = 0 the LASSO step is 0 when |grad| <= lambda: tested in FP32
+                // against lambda rounded down (FP32 and BF16 forms) or on the FP64
+                // bit patterns as integers (FP64 form), with no FP64 instruction
+                bool zero_step = false;
+                if constexpr (GM == 0) {
+                    if constexpr (sizeof(XT) == 4)
+                        zero_step = a.problem == 0 && is_zero_bits(xi) && fabsf(float(acc)) <= lamf;
+                    else
+                        zero_step = a.problem == 0 && is_zero_bits(xi) && abs_le_bits(double(acc), a.lambda);
+                }
                 if (!zero_step) take_step(acc);
             };
             if constexpr (CERT) {
@@ -893,7 +906,8 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                         ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
                         acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
                     }
-                    take_step(acc);
+                    // the exact test on the FP64 sum (the bound may not have decided it)
+                    if (!(a.problem == 0 && is_zero_bits(xi) && abs_le_bits(acc, a.lambda))) take_step(acc);
                 }
             } else {
                 full_path();
