@@ -510,6 +510,7 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
     const bool own = j0 < a.tau;
     unsigned long long target = 0;
     Counters cnt;
+    const float lamf = __double2float_rd(a.lambda);   // the largest float <= lambda
 
     // Prologue: the column of iteration k0 into registers.
     int32_t i0 = 0;
@@ -554,17 +555,28 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
                 acc += chunk_dot<kE, XT, XT, XT, GM>(t, a.g, c0.cnt - st);
             }
             acc = group_sum<W>(acc, gmask);
-            const double xn = coord_step(a.problem, xi, double(acc), double(c0.invL), a.inv_beta, a.lambda, a.kappa);
-            const double h64 = xn - xi;
-            h0 = XT(h64);
-            if (lane == 0) {
-                if (h64 != 0.0) a.x[i0] = xn;
-                cnt.gathered += (unsigned long long)c0.cnt;
-                if (h64 != 0.0) {
+            // At x_i = 0 the LASSO step is 0 when |grad| <= lambda: tested in FP32
+            // against lambda rounded down, or on the FP64 bit patterns as integers,
+            // so that a warp whose columns all pass runs no FP64 instruction.
+            bool zero_step = false;
+            if constexpr (GM == 0) {
+                if constexpr (sizeof(XT) == 4)
+                    zero_step = a.problem == 0 && is_zero_bits(xi) && fabsf(float(acc)) <= lamf;
+                else
+                    zero_step = a.problem == 0 && is_zero_bits(xi) && abs_le_bits(double(acc), a.lambda);
+            }
+            if (!zero_step) {
+                const double xn =
+                    coord_step(a.problem, xi, double(acc), double(c0.invL), a.inv_beta, a.lambda, a.kappa);
+                const double h64 = xn - xi;
+                h0 = XT(h64);
+                if (lane == 0 && h64 != 0.0) {
+                    a.x[i0] = xn;
                     cnt.nonzero += 1;
                     cnt.scattered += (unsigned long long)c0.cnt;
                 }
             }
+            if (lane == 0) cnt.gathered += (unsigned long long)c0.cnt;
         }
         for (int64_t j = j0 + ngrp; j < a.tau; j += ngrp) gather_generic<W, VT, XT, GM>(a, S, j, lane, gmask, cnt);
         target += gridDim.x;
@@ -572,7 +584,7 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
 
         // ---------------- phase 2: residual update, next sample
         // the chunk registers are free by now (reloaded from L2 for the few columns with h != 0)
-        if (own && h0 != XT(0)) column_scatter<W>(a, c0, lane, h0, 0);
+        if (own && !is_zero_bits(h0)) column_scatter<W>(a, c0, lane, h0, 0);
         for (int64_t j = j0 + ngrp; j < a.tau; j += ngrp) scatter_generic<W>(a, S, j, lane);
         int32_t *Sn = sample_buf(a, k + 1);
         for (int64_t j = ngrp + gid; j < a.tau; j += nthreads) Sn[j] = sample_index(uint32_t(j), key);

@@ -1,9 +1,11 @@
-"""The zero-step shortcut of the pipelined kernel changes no result.
+"""The zero-step shortcuts of the iteration kernels change no result.
 
 At x_i = 0 the LASSO step is zero exactly when |grad_i| <= lambda.  The
-pipelined kernel decides that in FP32 (FP64 form: a sum over FP32 images of
-the operands with an error bound; FP32 and BF16 forms: the FP32 gradient against
-lambda rounded down) and runs no FP64 instruction for a lane it certifies.  A
+pipelined kernel can decide that in FP32 before any FP64 work (FP64 form: a sum
+over FP32 images of the operands with an error bound); both it and the
+lanes-per-column kernel test the finished gradient exactly (FP32 and BF16 forms:
+the FP32 gradient against lambda rounded down; FP64 form: the bit patterns
+compared as integers) and run no FP64 instruction for a lane that passes.  A
 wrong certificate zeroes a step that should be nonzero, so these instances put
 |grad_i| just above lambda for whole families of columns (nonzero but tiny
 steps, which the oracle computes in FP64) next to columns just below it, with
@@ -78,8 +80,10 @@ def _rel(a, b):
 # (scale of the values, scale of b): ordinary; large b with small values; images
 # of the values clamped to 2^-126; images of b infinite; products underflowing FP32.
 SCALES = [(1.0, 1.0), (2.0 ** -100, 2.0 ** 100), (2.0 ** -130, 2.0 ** 20), (1.0, 2.0 ** 130), (2.0 ** -70, 2.0 ** -70)]
-# (kernel, lanes per column, threads per block, column heads, zero-step certificate on)
-CHOICES = [(0, 1, 448, 1, 1), (0, 1, 64, 0, 1)]
+# (kernel, lanes per column, threads per block, column heads, zero-step certificate):
+# the pipelined kernel with the FP32 certificate, without it (the exact test on the
+# FP64 sum alone), and the lanes-per-column kernel with 1 and 4 lanes
+CHOICES = [(0, 1, 448, 1, 1), (0, 1, 64, 0, 1), (0, 1, 448, 1, 0), (1, 1, 0, 1, -1), (1, 4, 0, 1, -1)]
 
 
 @pytest.mark.parametrize("choice", CHOICES)
