@@ -861,12 +861,12 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<
                 if (!zero_step) take_step(acc);
             };
             if constexpr (CERT) {
-                // FP64 form: the gathers bring only the high words of g, enough
-                // for the FP32 certificate of a zero LASSO step (ZeroCert).  A
-                // lane the certificate does not cover (x_i != 0, |grad| near
-                // lambda, the SVM dual) gathers the column again in FP64, from L2:
-                // keeping the FP64 values in registers across the certificate
-                // would spill.
+                // FP64 form with the FP32 certificate of a zero LASSO step
+                // (ZeroCert): the first chunk's gathers stay in registers as FP64,
+                // the tail's bring only the high words of g (FP64 values of both
+                // across the certificate would spill).  A lane the certificate
+                // does not cover (x_i != 0, |grad| near lambda, the SVM dual)
+                // reads the column's entries past the first chunk again, from L2.
                 XT gv[kE];
 #pragma unroll
                 for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
