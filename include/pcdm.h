@@ -88,8 +88,11 @@ typedef struct {
     int32_t sampling;            /* PCDM_SAMPLING_NICE (default), _INDEPENDENT or _BINOMIAL       */
     double p_b;                  /* binomial sampling: probability that a position is kept, (0, 1] */
     int32_t l2_persist;          /* 1: raise the CUDA context's L2 persisting-lines limit
-                                    (cudaLimitPersistingL2CacheSize) to the device maximum from
-                                    pcdm_create to pcdm_destroy, which restores the previous value.
+                                    (cudaLimitPersistingL2CacheSize) to the device maximum while
+                                    the handle lives.  The handles of a device share the limit:
+                                    the first l2_persist handle raises it, and destroying the last
+                                    one restores the value from before the first and resets the
+                                    persisting lines, whatever the order of create and destroy.
                                     The kernels mark the residual evict-last; the set-aside keeps
                                     more of it in L2.  The limit is context-wide: it holds for every
                                     kernel of the process while the handle lives.  Changing the
@@ -426,9 +429,9 @@ pcdm_status pcdm_selftest_barrier_timeout(uint64_t timeout_ns, void *cuda_stream
  * (4 MiB) inside the library, so m may be at most PCDM_NOALLOC_MAX_ROWS; larger
  * m returns PCDM_EINVAL before any device work.  A: col_ptr, row_idx on the
  * device (A->on_device must be 1; host arrays would need a staging buffer), the
- * values are not read.  The matrix is checked as pcdm_create checks it (col_ptr
- * monotone from 0 to nnz, rows in [0, m), strictly increasing in a column);
- * a violation returns PCDM_EINVAL.  The call clears the counters it uses, runs
+ * values are not read.  The matrix is checked as pcdm_create checks it (1 <= m,
+ * n < 2^31, nnz >= 0, col_ptr monotone from 0 to nnz, rows in [0, m), strictly
+ * increasing in a column); a violation returns PCDM_EINVAL.  The call clears the counters it uses, runs
  * on cuda_stream and synchronises it before writing *omega (host memory).
  *
  * The first call on a device looks up the array's device address (a one-time

@@ -23,6 +23,49 @@ constexpr int kMaxPoolDevices = 64;
 std::mutex g_pool_mu;
 cudaMemPool_t g_pools[kMaxPoolDevices] = {};
 uint64_t g_cache_limit = uint64_t(16) << 30;   // bytes of freed handle memory a pool keeps
+
+// The persisting-L2 limit is a property of the device's context, shared by every
+// handle on it.  It is raised when the first l2_persist handle of a device is
+// created and put back (with the persisting lines reset) when the last one is
+// destroyed, so that handles created and destroyed in any order neither drop
+// another live handle's set-aside nor leave the raised limit behind.
+std::mutex g_l2_mu;
+struct L2Users {
+    int count = 0;        // live l2_persist handles of the device
+    size_t before = 0;    // the limit before the first of them raised it
+};
+L2Users g_l2_users[kMaxPoolDevices];
+
+// Called with `device` current.
+cudaError_t l2_persist_acquire(int device, size_t max_bytes)
+{
+    if (device < 0 || device >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_l2_mu);
+    L2Users &u = g_l2_users[device];
+    if (u.count == 0) {
+        size_t before = 0;
+        cudaError_t e = cudaDeviceGetLimit(&before, cudaLimitPersistingL2CacheSize);
+        if (e == cudaSuccess) e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, max_bytes);
+        if (e != cudaSuccess) return e;
+        u.before = before;
+    }
+    u.count += 1;
+    return cudaSuccess;
+}
+
+void l2_persist_release(int device)
+{
+    if (device < 0 || device >= kMaxPoolDevices) return;
+    std::lock_guard<std::mutex> lock(g_l2_mu);
+    L2Users &u = g_l2_users[device];
+    if (u.count <= 0 || --u.count > 0) return;
+    int cur = -1;
+    const bool switch_dev = cudaGetDevice(&cur) == cudaSuccess && cur != device;
+    if (switch_dev) cudaSetDevice(device);
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, u.before);
+    cudaCtxResetPersistingL2Cache();
+    if (switch_dev) cudaSetDevice(cur);
+}
 }  // namespace
 
 cudaError_t pcdm_host::handle_pool(int device, cudaMemPool_t *pool)
@@ -60,8 +103,7 @@ void free_all(pcdm_handle h)
                     h->as_S, h->as_part, h->win, h->head};
     for (void *p : ptrs) hfree(h, p);
     if (h->l2_set) {
-        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, h->l2_prev);
-        cudaCtxResetPersistingL2Cache();
+        l2_persist_release(h->device);
         h->l2_set = false;
     }
     if (h->g64 && h->g64 != h->g) hfree(h, h->g64);
@@ -510,9 +552,8 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     if (o.l2_persist) {
         int maxp = 0;
         CKC(cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, h->device));
-        CKC(cudaDeviceGetLimit(&h->l2_prev, cudaLimitPersistingL2CacheSize));
         if (maxp > 0) {
-            CKC(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, size_t(maxp)));
+            CKC(l2_persist_acquire(h->device, size_t(maxp)));
             h->l2_set = true;
         }
     }
@@ -1240,7 +1281,8 @@ pcdm_status pcdm_omega_noalloc(const pcdm_csc *A, int64_t *omega, void *cuda_str
     // Every check that needs no device comes first; nothing below allocates.
     if (!A || !omega) return set_err(nullptr, PCDM_EINVAL, "A or omega is NULL");
     if (A->on_device != 1) return set_err(nullptr, PCDM_EINVAL, "A must be in device memory (on_device = 1)");
-    if (A->m < 0 || A->n < 0 || A->nnz < 0) return set_err(nullptr, PCDM_EINVAL, "negative m, n or nnz");
+    if (A->m < 1 || A->n < 1 || A->n > 2147483647LL || A->nnz < 0)
+        return set_err(nullptr, PCDM_EINVAL, "need 1 <= m, n < 2^31 and nnz >= 0");
     if (A->m > PCDM_NOALLOC_MAX_ROWS)
         return set_err(nullptr, PCDM_EINVAL, "m exceeds PCDM_NOALLOC_MAX_ROWS (" +
                                                  std::to_string(PCDM_NOALLOC_MAX_ROWS) + ")");
@@ -1253,7 +1295,7 @@ pcdm_status pcdm_omega_noalloc(const pcdm_csc *A, int64_t *omega, void *cuda_str
     e = noalloc_rows_scratch(dev, &cnt, &tail);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress of the row-count scratch");
     // counters and the flags / result words start at zero
-    if (A->m > 0) e = cudaMemsetAsync(cnt, 0, size_t(A->m) * sizeof(int), st);
+    e = cudaMemsetAsync(cnt, 0, size_t(A->m) * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(tail, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess) e = launch_rows_checked(A->col_ptr, A->row_idx, A->m, A->n, A->nnz, cnt, tail, st);
     if (e == cudaSuccess) e = launch_max_int(cnt, A->m, tail + 1, st);

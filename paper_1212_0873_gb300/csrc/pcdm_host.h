@@ -43,8 +43,7 @@ struct pcdm_ctx {
     int val_dtype = PCDM_F64, xg_dtype = PCDM_F64;
     double lambda = 0.0;
     int problem = 0;              // PCDM_PROBLEM_*: LASSO, SVM dual, logistic regression
-    bool l2_set = false;          // opts.l2_persist raised the context's persisting-L2 limit
-    size_t l2_prev = 0;           // the limit before, restored at destroy
+    bool l2_set = false;          // the handle counts among the device's l2_persist users
     pcdm_opts opts{};
     int W = 8;
     int sms = 0;

@@ -187,7 +187,8 @@ def test_omega_noalloc_host_checks(B):
     out = ctypes.c_int64(-1)
     ok = dict(m=10, n=4, nnz=0, col_ptr=1, row_idx=0, val=0, val_dtype=B.PCDM_F64, on_device=1)
     for case, change in [("host arrays", dict(on_device=0)), ("too many rows", dict(m=B.PCDM_NOALLOC_MAX_ROWS + 1)),
-                         ("negative n", dict(n=-1)), ("no col_ptr", dict(col_ptr=0)),
+                         ("negative n", dict(n=-1)), ("no rows", dict(m=0)), ("no columns", dict(n=0)),
+                         ("n of 2^31", dict(n=2**31)), ("negative nnz", dict(nnz=-1)), ("no col_ptr", dict(col_ptr=0)),
                          ("no row_idx", dict(nnz=5))]:
         csc = B.pcdm_csc(**dict(ok, **change))
         assert L.pcdm_omega_noalloc(ctypes.byref(csc), ctypes.byref(out), None) == B.PCDM_EINVAL, case

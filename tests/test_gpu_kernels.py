@@ -91,6 +91,30 @@ def test_l2_persist_option_is_scoped_to_the_handle():
     assert _cu_limit_persisting_l2() == before
 
 
+@pytest.mark.parametrize("first_destroyed", ["first_created", "last_created"])
+def test_l2_persist_limit_is_shared_by_the_handles_of_a_device(first_destroyed):
+    # the limit is the context's: it stays raised while any l2_persist handle lives,
+    # and goes back to the value from before the first one when the last one goes
+    import torch
+    torch.zeros(1, device="cuda")
+    before = _cu_limit_persisting_l2()
+    inst = instances.per_col_instance(2000, 1000, 20, nnz_star=50, val_dtype="f64", seed=1003)
+    a = Lasso.from_instance(inst, l2_persist=True)
+    raised = _cu_limit_persisting_l2()
+    assert raised >= before
+    b = Lasso.from_instance(inst, l2_persist=True)
+    plain = Lasso.from_instance(inst)
+    assert _cu_limit_persisting_l2() == raised
+    order = (a, b) if first_destroyed == "first_created" else (b, a)
+    order[0].close()
+    assert _cu_limit_persisting_l2() == raised       # the other handle still holds its set-aside
+    order[1].step(96, 3, 2)
+    plain.close()
+    assert _cu_limit_persisting_l2() == raised
+    order[1].close()
+    assert _cu_limit_persisting_l2() == before
+
+
 def test_handle_memory_comes_back_from_the_pool():
     # destroyed handles leave their memory in the library's pool; the next handle
     # reuses it, and pcdm_release_cached_memory returns it to the device
