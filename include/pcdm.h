@@ -99,7 +99,21 @@ typedef struct {
                                     limit costs milliseconds at create and destroy, so it pays off
                                     for handles that run many iterations.  0: leave it.
                                     Single-problem handles only (the batch and multi APIs ignore it). */
-    int32_t reserved2;           /* 0 */
+    int32_t deterministic_scatter;  /* 1: bitwise reproducible iterations (Algorithm 1, step 4, in a
+                                    fixed order of operations).  Each gradient sums its column in
+                                    storage order from 0, every product and addition rounded on its
+                                    own (no FMA); beta L_i is one product, and u = x_i - grad/(beta L_i),
+                                    t = lambda/(beta L_i) use correctly rounded divisions; x_i becomes
+                                    soft(u, t).  Each g_r then receives the iteration's nonzero steps
+                                    in increasing sampled position, g_r = g_r + a_ri h_j, with no
+                                    atomics, and the residual refresh sums each row from -b_r in
+                                    increasing column index.  In the FP64 form these are exactly the
+                                    operations of a plain sequential FP64 run of Algorithm 1 that
+                                    visits S_k[0], S_k[1], ... in turn.  Runs the two-kernel form
+                                    (fused, lanes_per_col and the tuning calls are ignored), LASSO
+                                    with the tau-nice sampling only (else EINVAL at create), and
+                                    keeps a row-major copy of A (8(m+1) + nnz(4 + value bytes)) and
+                                    8 n bytes of stamps.  0: atomics in arrival order.          */
 } pcdm_opts;
 
 /*

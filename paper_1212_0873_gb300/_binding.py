@@ -31,7 +31,7 @@ class pcdm_tuning(ctypes.Structure):
 class pcdm_opts(ctypes.Structure):
     _fields_ = [("xg_dtype", _i32), ("fused", _i32), ("refresh_every", _i64), ("check_every", _i64),
                 ("lanes_per_col", _i64), ("barrier_timeout_ns", _u64), ("profile", _i32), ("sampling", _i32),
-                ("p_b", _dbl), ("l2_persist", _i32), ("reserved2", _i32)]
+                ("p_b", _dbl), ("l2_persist", _i32), ("deterministic_scatter", _i32)]
 
 
 class pcdm_stats(ctypes.Structure):

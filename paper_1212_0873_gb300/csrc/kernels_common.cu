@@ -705,6 +705,47 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int64_t *col_
     if (blockIdx.x == 0 && threadIdx.x == 0) pbeg[n] = tile[ntiles];
 }
 
+// The same three passes over plain int counts (the row counts of the row-major copy).
+__global__ void __launch_bounds__(kScanThreads) k_count_scan_tiles(const int *cnt, int64_t m, int64_t *tile)
+{
+    const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanPer;
+    int64_t s = 0;
+    for (int q = 0; q < kScanPer; ++q)
+        if (base + q < m) s += cnt[base + q];
+    __shared__ int64_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) tile[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_count_scan_apply(const int *cnt, int64_t m, const int64_t *tile,
+                                                                   int64_t ntiles, int64_t *out)
+{
+    const int64_t base = int64_t(blockIdx.x) * kScanTile + int64_t(threadIdx.x) * kScanPer;
+    int64_t len[kScanPer];
+    int64_t s = 0;
+    for (int q = 0; q < kScanPer; ++q) {
+        len[q] = base + q < m ? cnt[base + q] : 0;
+        s += len[q];
+    }
+    __shared__ int64_t tot;
+    int64_t run = block_exclusive_scan(s, &tot) + tile[blockIdx.x];
+    for (int q = 0; q < kScanPer; ++q) {
+        if (base + q < m) out[base + q] = run;
+        run += len[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = tile[ntiles];
+}
+
+cudaError_t launch_count_scan(const int *cnt, int64_t m, int64_t *out, int64_t *tile, cudaStream_t st)
+{
+    const int64_t nt = scan_tile_count(m);
+    if (nt <= 0) return cudaSuccess;
+    k_count_scan_tiles<<<unsigned(nt), kScanThreads, 0, st>>>(cnt, m, tile);
+    k_scan_tile_prefix<<<1, kScanThreads, 0, st>>>(tile, nt);
+    k_count_scan_apply<<<unsigned(nt), kScanThreads, 0, st>>>(cnt, m, tile, nt, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_padded_scan(const int64_t *col_ptr, int64_t n, int granule, int64_t *pbeg, int64_t *tile,
                                cudaStream_t st)
 {

@@ -100,7 +100,7 @@ void free_all(pcdm_handle h)
     void *ptrs[] = {h->desc, h->prow, h->pval, h->b, h->L64, h->x, h->g, h->g2,
                     h->S[0], h->S[1], h->h, h->counters, h->bar, h->status, h->gap_part, h->gap_out,
                     h->as_sidx, h->as_c, h->as_sgn, h->as_u, h->as_dx, h->as_q, h->as_rowcnt, h->as_H,
-                    h->as_S, h->as_part, h->win, h->head};
+                    h->as_S, h->as_part, h->win, h->head, h->det_rptr, h->det_rcol, h->det_rval, h->det_mark};
     for (void *p : ptrs) hfree(h, p);
     if (h->l2_set) {
         l2_persist_release(h->device);
@@ -267,7 +267,21 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
         CK(h, take_event(h, &e1));
         CK(h, cudaEventRecord(e0, h->stream));
     }
-    if (h->opts.sampling != PCDM_SAMPLING_NICE) {
+    if (h->opts.deterministic_scatter) {
+        // the deterministic two-kernel form: gather, scatter, then S_{k+1}
+        CK(h, cudaMemsetAsync(h->det_mark, 0, size_t(h->n) * sizeof(unsigned long long), h->stream));
+        const double beta = beta_for(h, tau);
+        for (int64_t it = 0; it < iters; ++it) {
+            const int64_t kk = h->k + it;
+            CK(h, DetKernels<VT, XT>::gather(a, h->L64, beta, h->det_mark, kk, h->stream));
+            CK(h, DetKernels<VT, XT>::scatter(a, h->det_rptr, h->det_rcol, static_cast<const VT *>(h->det_rval),
+                                              h->det_mark, kk, h->stream));
+            CK(h, launch_sample(seed, kk + 1, h->n, tau, a.S[(kk + 1) & 1], h->stream));
+        }
+        h->g2_valid = false;
+        h->st_launches += iters;
+        h->st_kernels += 3 * iters + 1;
+    } else if (h->opts.sampling != PCDM_SAMPLING_NICE) {
         // the other samplings: draw, gather, scatter per iteration
         if (h->opts.sampling == PCDM_SAMPLING_INDEPENDENT) {
             if (!h->win) {
@@ -375,6 +389,15 @@ template <typename VT, typename XT>
 pcdm_status refresh_t(pcdm_handle h)
 {
     double *target = h->g64;
+    if (h->opts.deterministic_scatter) {
+        CK(h, DetKernels<VT, XT>::refresh(h->det_rptr, h->det_rcol, static_cast<const VT *>(h->det_rval),
+                                          static_cast<const double *>(h->x), h->b, h->m, target,
+                                          static_cast<XT *>(h->g), h->stream));
+        h->g2_valid = false;
+        h->st_refreshes += 1;
+        h->st_kernels += 1;
+        return PCDM_OK;
+    }
     CK(h, launch_neg_store<double>(target, h->b, h->m, h->stream));
     CK(h, Kernels<VT, XT>::refresh_cols(static_cast<const ColDesc<XT> *>(h->desc), h->prow,
                                         static_cast<const VT *>(h->pval), static_cast<const double *>(h->x), h->n,
@@ -520,6 +543,10 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
     if (o.sampling == PCDM_SAMPLING_BINOMIAL && !(o.p_b > 0.0 && o.p_b <= 1.0))
         return set_err(nullptr, PCDM_EINVAL, "p_b must be in (0, 1]");
     if (o.l2_persist != 0 && o.l2_persist != 1) return set_err(nullptr, PCDM_EINVAL, "l2_persist must be 0 or 1");
+    if (o.deterministic_scatter != 0 && o.deterministic_scatter != 1)
+        return set_err(nullptr, PCDM_EINVAL, "deterministic_scatter must be 0 or 1");
+    if (o.deterministic_scatter && (problem != PCDM_PROBLEM_LASSO || o.sampling != PCDM_SAMPLING_NICE))
+        return set_err(nullptr, PCDM_EINVAL, "deterministic_scatter needs LASSO with the tau-nice sampling");
 
     pcdm_ctx *h = new (std::nothrow) pcdm_ctx();
     if (!h) return set_err(nullptr, PCDM_ENOMEM, "host allocation failed");
@@ -717,6 +744,42 @@ pcdm_status create_impl(const pcdm_csc *A, const void *b, int32_t b_dtype, doubl
                                                      static_cast<bf16_t *>(h->pval), h->n, stg.y, st));
             break;
         }
+    }
+    if (o.deterministic_scatter) {
+        // row-major copy of A for the deterministic scatter and refresh
+        CKC(halloc(h, &h->det_rptr, h->m + 1));
+        CKC(halloc(h, &h->det_rcol, h->nnz > 0 ? h->nnz : 1));
+        CKC(halloc_bytes(h, &h->det_rval, (h->nnz > 0 ? h->nnz : 1) * vb));
+        CKC(halloc(h, &h->det_mark, h->n));
+        int64_t *tile = nullptr;
+        unsigned long long *cursor = nullptr;
+        CKC(halloc(h, &tile, scan_tile_count(h->m) + 1));
+        cudaError_t e = halloc(h, &cursor, h->m);
+        if (e == cudaSuccess) e = launch_count_scan(stg.rowcnt, h->m, h->det_rptr, tile, st);
+        if (e == cudaSuccess) {
+            switch (h->val_dtype) {
+            case PCDM_F64:
+                e = DetKernels<double, double>::build_rows(stg.col_ptr, stg.row_idx,
+                                                           static_cast<const double *>(stg.val), h->m, h->n,
+                                                           h->det_rptr, cursor, h->det_rcol,
+                                                           static_cast<double *>(h->det_rval), st);
+                break;
+            case PCDM_F32:
+                e = DetKernels<float, float>::build_rows(stg.col_ptr, stg.row_idx, static_cast<const float *>(stg.val),
+                                                         h->m, h->n, h->det_rptr, cursor, h->det_rcol,
+                                                         static_cast<float *>(h->det_rval), st);
+                break;
+            default:
+                e = DetKernels<bf16_t, float>::build_rows(stg.col_ptr, stg.row_idx,
+                                                          static_cast<const bf16_t *>(stg.val), h->m, h->n,
+                                                          h->det_rptr, cursor, h->det_rcol,
+                                                          static_cast<bf16_t *>(h->det_rval), st);
+                break;
+            }
+        }
+        hfree(h, tile);
+        hfree(h, cursor);
+        CKC(e);
     }
     CKC(cudaMemsetAsync(h->counters, 0, 3 * sizeof(unsigned long long), st));
     {
@@ -1357,6 +1420,8 @@ pcdm_status pcdm_step_async(pcdm_handle h, int64_t updates, uint64_t seed, int32
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
     if (h->problem != PCDM_PROBLEM_LASSO) return set_err(h, PCDM_EINVAL, "pcdm_step_async applies to LASSO handles only");
+    if (h->opts.deterministic_scatter)
+        return set_err(h, PCDM_EINVAL, "the asynchronous mode has no fixed order (deterministic_scatter handle)");
     if (updates < 0 || threads < 0) return set_err(h, PCDM_EINVAL, "updates and threads must be >= 0");
     if (updates == 0) return PCDM_OK;
     s = dispatch(h, [&](auto *vt, auto *xt) {
@@ -1374,6 +1439,8 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
     if (h->problem != PCDM_PROBLEM_LASSO) return set_err(h, PCDM_EINVAL, "pcdm_solve_async applies to LASSO handles only");
+    if (h->opts.deterministic_scatter)
+        return set_err(h, PCDM_EINVAL, "the asynchronous mode has no fixed order (deterministic_scatter handle)");
     if (max_updates < 0 || threads < 0 || !(rel_gap_tol >= 0.0))
         return set_err(h, PCDM_EINVAL, "bad max_updates, threads or tolerance");
     const int64_t epoch = h->n;   // updates between the first checks
@@ -1441,7 +1508,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     pcdm_status s = usable(h);
     if (s != PCDM_OK) return s;
     if (tau < 1 || tau > h->n || trial_iters < 1) return set_err(h, PCDM_EINVAL, "bad tau or trial_iters");
-    if (h->opts.sampling != PCDM_SAMPLING_NICE || !h->opts.fused)
+    if (h->opts.sampling != PCDM_SAMPLING_NICE || !h->opts.fused || h->opts.deterministic_scatter)
         return set_err(h, PCDM_EINVAL, "autotuning applies to the fused tau-nice iteration kernels");
     s = ensure_tau(h, tau);
     if (s != PCDM_OK) return s;

@@ -86,6 +86,12 @@ struct pcdm_ctx {
     int as_blocks = 0;
     unsigned long long *win = nullptr;   // n: first-pick keys of the tau-independent sampling
 
+    // deterministic two-kernel form (opts.deterministic_scatter)
+    int64_t *det_rptr = nullptr;  // m + 1: row starts of the row-major copy of A
+    int32_t *det_rcol = nullptr;  // nnz: its column indices, sorted within each row
+    void *det_rval = nullptr;     // nnz: its values (the stored dtype)
+    unsigned long long *det_mark = nullptr;   // n: stamps (lo32(k+1) << 32) | position of the nonzero steps
+
     int64_t omega = 0;
     int64_t k = 0;
     int64_t last_solve_iters = 0;   // iterations of the last pcdm_solve (0 after create / reset)

@@ -156,6 +156,28 @@ struct Kernels {
                                     const double *y, cudaStream_t st);
 };
 
+// Deterministic two-kernel form (det_kernels.cuh; pcdm_opts.deterministic_scatter):
+// fixed summation order and separately rounded products and sums.
+template <typename VT, typename XT>
+struct DetKernels {
+    // Row-major copy of A: rcol / rval at rptr (the exclusive scan of the row
+    // counts), each row sorted by column; cursor is m words of scratch.
+    static cudaError_t build_rows(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, int64_t m,
+                                  int64_t n, const int64_t *rptr, unsigned long long *cursor, int32_t *rcol, VT *rval,
+                                  cudaStream_t st);
+    // Gradients and steps of S_k (in S[k & 1]); stamps mark[i] of the nonzero steps.
+    static cudaError_t gather(const IterArgs<VT, XT> &a, const double *L64, double beta, unsigned long long *mark,
+                              int64_t k, cudaStream_t st);
+    // The nonzero steps of iteration k into g, row by row in increasing position.
+    static cudaError_t scatter(const IterArgs<VT, XT> &a, const int64_t *rptr, const int32_t *rcol, const VT *rval,
+                               const unsigned long long *mark, int64_t k, cudaStream_t st);
+    // g64 = A x - b by rows in increasing column (and g = g64 rounded when g is FP32).
+    static cudaError_t refresh(const int64_t *rptr, const int32_t *rcol, const VT *rval, const double *x,
+                               const double *b, int64_t m, double *g64, XT *g, cudaStream_t st);
+};
+// out[0..m) = exclusive prefix sums of cnt, out[m] = the total (tile: scan_tile_count(m) + 1 int64).
+cudaError_t launch_count_scan(const int *cnt, int64_t m, int64_t *out, int64_t *tile, cudaStream_t st);
+
 template <typename VT, typename XT>
 struct BatchArgs {
     const ColDesc<XT> *desc;

@@ -56,7 +56,7 @@ class Lasso:
 
     def __init__(self, m, n, col_ptr, row_idx, val, b, lam, *, xg_dtype=None, fused=True, refresh_every=0,
                  check_every=0, lanes_per_col=0, profile=False, barrier_timeout_ns=None, stream=None,
-                 sampling="nice", p_b=1.0, l2_persist=False):
+                 sampling="nice", p_b=1.0, l2_persist=False, deterministic_scatter=False):
         val_dtype = _val_code(val)
         if xg_dtype is None:
             xg_dtype = "f64" if val_dtype == "f64" else "f32"
@@ -80,6 +80,7 @@ class Lasso:
         opts.sampling = B.SAMPLING_CODES[sampling]
         opts.p_b = float(p_b)
         opts.l2_persist = 1 if l2_persist else 0
+        opts.deterministic_scatter = 1 if deterministic_scatter else 0
         if barrier_timeout_ns is not None:
             opts.barrier_timeout_ns = int(barrier_timeout_ns)
         b_dt = B.PCDM_F32 if (str(getattr(b, "dtype", "")) in ("float32", "torch.float32")) else B.PCDM_F64

@@ -52,6 +52,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(pcdm_csc), sizeof(pcdm_opts), sizeof(pcdm_stats), sizeof(pcdm_tuning));
   printf("%zu %zu %zu %zu\n", offsetof(pcdm_csc, val_dtype), offsetof(pcdm_opts, barrier_timeout_ns),
          offsetof(pcdm_stats, iter_kernel_ms), offsetof(pcdm_tuning, us_per_iteration));
+  printf("%zu\n", offsetof(pcdm_opts, deterministic_scatter));
   return 0;
 }
 """
@@ -70,6 +71,7 @@ int main(void) {
     assert sizes[5] == B.pcdm_opts.barrier_timeout_ns.offset
     assert sizes[6] == B.pcdm_stats.iter_kernel_ms.offset
     assert sizes[7] == B.pcdm_tuning.us_per_iteration.offset
+    assert sizes[8] == B.pcdm_opts.deterministic_scatter.offset
 
 
 def test_default_opts_and_status_strings(B):
@@ -91,7 +93,7 @@ def _csc(B, m=4, n=3, nnz=0, val_dtype=0):
 
 @pytest.mark.parametrize("case", ["null_A", "null_b", "m0", "n0", "neg_nnz", "huge_m", "lam_neg", "lam_nan",
                                   "lam_inf", "pair_f64_f32", "pair_bf16_f64", "bad_bdtype", "bad_lanes",
-                                  "neg_refresh", "null_rows"])
+                                  "neg_refresh", "null_rows", "det_flag_2", "det_independent"])
 def test_create_rejects_bad_arguments_before_any_cuda_call(B, case):
     import numpy as np
     b = np.zeros(4)
@@ -130,6 +132,11 @@ def test_create_rejects_bad_arguments_before_any_cuda_call(B, case):
         opts.refresh_every = -1
     elif case == "null_rows":
         A.nnz = 5
+    elif case == "det_flag_2":
+        opts.deterministic_scatter = 2
+    elif case == "det_independent":
+        opts.deterministic_scatter = 1
+        opts.sampling = B.SAMPLING_CODES["independent"]
     h = ctypes.c_void_p()
     st = B.lib().pcdm_create(ctypes.byref(a_arg) if a_arg is not None else None, b_arg, bdt, lam,
                              ctypes.byref(opts), None, ctypes.byref(h))
@@ -238,5 +245,14 @@ def test_create_problem_rejects_bad_arguments_before_device_work(B):
     opts.sampling = 1
     assert L.pcdm_create_problem(ctypes.byref(A), 1, y, 1.0, ctypes.byref(opts), None,
                                  ctypes.byref(h)) == B.PCDM_EINVAL
+    # the deterministic form is LASSO-only (a valid empty matrix, so that only the option is wrong)
+    col_ptr = (ctypes.c_int64 * 4)(0, 0, 0, 0)
+    A2 = B.pcdm_csc(4, 3, 0, ctypes.addressof(col_ptr), None, None, B.PCDM_F64, 0)
+    opts = B.pcdm_default_opts()
+    opts.deterministic_scatter = 1
+    assert L.pcdm_create_problem(ctypes.byref(A2), 1, y, 1.0, ctypes.byref(opts), None,
+                                 ctypes.byref(h)) == B.PCDM_EINVAL
+    msg = B.pcdm_last_error(None)
+    assert "deterministic" in (msg.decode() if isinstance(msg, bytes) else msg)
     assert not h.value
     assert L.pcdm_problem_kind(None, None) != 0
