@@ -106,6 +106,11 @@ def _declare(L):
         L.pcdm_oracle_run.argtypes = [_i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _dbl, _i64,
                                       _u64, _i64, _i64, _i64, _ptr, _ptr]
         L.pcdm_oracle_run.restype = ctypes.c_int
+        L.pcdm_oracle_run_threads.argtypes = [_i64, _i64, _ptr, _ptr, _ptr, _ptr, _ptr, _dbl, _dbl, _i64,
+                                              _u64, _i64, _i64, _i64, _ptr, _ptr, ctypes.c_int]
+        L.pcdm_oracle_run_threads.restype = ctypes.c_int
+        L.pcdm_oracle_sample_range.argtypes = [_u64, _i64, _i64, _i64, _i64, _ptr]
+        L.pcdm_oracle_sample_range.restype = ctypes.c_int
         _ci = ctypes.c_int
         L.pcdm_oracle_glm_lipschitz.argtypes = [_ci, _i64, _ptr, _ptr, _dbl, _ptr]
         L.pcdm_oracle_glm_lipschitz.restype = None
@@ -257,6 +262,17 @@ class State:
                                    _p(self.x), _p(self.g))
         if rc != 0:
             raise ValueError("oracle run failed")
+        self.k += int(iters)
+
+    def run_threads(self, tau, iters, seed, threads, refresh_every=0, beta=None):
+        """run() on `threads` host threads (the timing mode of the CPU baseline):
+        the same iterations, equal to run() bit for bit."""
+        b_ = self.beta(tau) if beta is None else float(beta)
+        rc = lib().pcdm_oracle_run_threads(*self.A.args(), _p(self.b), _p(self.L), self.lam, b_, int(tau),
+                                           int(seed) & (2**64 - 1), int(self.k), int(iters), int(refresh_every),
+                                           _p(self.x), _p(self.g), int(threads))
+        if rc != 0:
+            raise ValueError("oracle threaded run failed")
         self.k += int(iters)
 
     def run_sampling(self, kind, tau, iters, seed, p_b=1.0, refresh_every=0, beta=None):

@@ -11,7 +11,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "pcdm_oracle.c")              # LASSO, the samplers
 SRC_GLM = os.path.join(HERE, "pcdm_oracle_glm.c")      # SVM dual and logistic regression
-SOURCES = (SRC, SRC_GLM)
+SRC_THREADS = os.path.join(HERE, "pcdm_oracle_threads.c")   # threaded timing mode of the LASSO run
+SOURCES = (SRC, SRC_GLM, SRC_THREADS)
 OUT_DIR = os.path.join(HERE, "_build")
 OUT = os.path.join(OUT_DIR, "liboracle.so")
 
@@ -22,7 +23,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(OUT) and all(os.path.getmtime(OUT) >= os.path.getmtime(s) for s in SOURCES):
         return OUT
     tmp = OUT + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-pthread",
            "-Wall", "-Wextra", *SOURCES, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, OUT)

@@ -129,19 +129,27 @@ static uint32_t feistel_permute(uint32_t v, int hb, const uint32_t K[12])
     return (left << hb) | right;
 }
 
-/* tau-nice sample of iteration k: S[0..tau-1].  Returns 0, or -1 on bad sizes. */
-int pcdm_oracle_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S)
+/* Positions j0 .. j1-1 of the tau-nice sample of iteration k: S[j0..j1-1].
+ * Returns 0, or -1 on bad sizes. */
+int pcdm_oracle_sample_range(uint64_t seed, int64_t k, int64_t n, int64_t j0, int64_t j1, int32_t *S)
 {
-    if (n < 1 || n > 2147483647LL || tau < 0 || tau > n || k < 0) return -1;
+    if (n < 1 || n > 2147483647LL || j0 < 0 || j1 < j0 || j1 > n || k < 0) return -1;
     int hb = feistel_half_bits(n);
     uint32_t K[12];
     round_keys(seed, (uint64_t)k, K);
-    for (int64_t j = 0; j < tau; ++j) {
+    for (int64_t j = j0; j < j1; ++j) {
         uint32_t v = feistel_permute((uint32_t)j, hb, K);
         while ((int64_t)v >= n) v = feistel_permute(v, hb, K);
         S[j] = (int32_t)v;
     }
     return 0;
+}
+
+/* tau-nice sample of iteration k: S[0..tau-1].  Returns 0, or -1 on bad sizes. */
+int pcdm_oracle_sample(uint64_t seed, int64_t k, int64_t n, int64_t tau, int32_t *S)
+{
+    if (tau < 0 || tau > n) return -1;
+    return pcdm_oracle_sample_range(seed, k, n, 0, tau, S);
 }
 
 /* Samples of iterations k0 .. k0+K-1, row after row, into out[K*tau]. */
@@ -213,14 +221,16 @@ static double soft_threshold(double u, double t)
  * The new coordinate is stored as the soft-threshold value itself and the
  * residual moves by a_i * (x_new - x_old).
  * hbuf and xbuf are scratch arrays of length tau.
+ *
+ * pcdm_oracle_steps is the first half for positions t0 .. t1-1 (x_new and h
+ * into xbuf[t], hbuf[t]; it only reads x and g), pcdm_oracle_apply the second;
+ * pcdm_oracle_iteration is the one followed by the other over all positions.
  */
-void pcdm_oracle_iteration(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx,
-                           const double *val, const double *L, double lambda, double beta,
-                           int64_t tau, const int32_t *S, double *x, double *g,
-                           double *hbuf, double *xbuf)
+void pcdm_oracle_steps(const int64_t *col_ptr, const int32_t *row_idx, const double *val, const double *L,
+                       double lambda, double beta, int64_t t0, int64_t t1, const int32_t *S,
+                       double *x, double *g, double *hbuf, double *xbuf)
 {
-    (void)m; (void)n;
-    for (int64_t t = 0; t < tau; ++t) {
+    for (int64_t t = t0; t < t1; ++t) {
         int64_t i = S[t];
         double grad = 0.0;
         for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) grad += val[p] * g[row_idx[p]];
@@ -234,6 +244,12 @@ void pcdm_oracle_iteration(int64_t m, int64_t n, const int64_t *col_ptr, const i
         xbuf[t] = x_new;
         hbuf[t] = x_new - x[i];
     }
+}
+
+/* x_i = xbuf[t], then g += a_i h_t, for t = 0 .. tau-1 in turn. */
+void pcdm_oracle_apply(const int64_t *col_ptr, const int32_t *row_idx, const double *val, int64_t tau,
+                       const int32_t *S, double *x, double *g, const double *hbuf, const double *xbuf)
+{
     for (int64_t t = 0; t < tau; ++t) {
         int64_t i = S[t];
         x[i] = xbuf[t];
@@ -241,6 +257,16 @@ void pcdm_oracle_iteration(int64_t m, int64_t n, const int64_t *col_ptr, const i
         if (h == 0.0) continue;
         for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) g[row_idx[p]] += val[p] * h;
     }
+}
+
+void pcdm_oracle_iteration(int64_t m, int64_t n, const int64_t *col_ptr, const int32_t *row_idx,
+                           const double *val, const double *L, double lambda, double beta,
+                           int64_t tau, const int32_t *S, double *x, double *g,
+                           double *hbuf, double *xbuf)
+{
+    (void)m; (void)n;
+    pcdm_oracle_steps(col_ptr, row_idx, val, L, lambda, beta, 0, tau, S, x, g, hbuf, xbuf);
+    pcdm_oracle_apply(col_ptr, row_idx, val, tau, S, x, g, hbuf, xbuf);
 }
 
 /* g = A x - b. */

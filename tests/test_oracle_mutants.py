@@ -136,8 +136,8 @@ def test_pins_catch_mutant(name, workdir):
     so_path = os.path.join(workdir, name + ".so")
     with open(c_path, "w") as f:
         f.write(mutated)
-    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", c_path, oracle_build.SRC_GLM,
-                    "-o", so_path, "-lm"], check=True)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-pthread", c_path,
+                    oracle_build.SRC_GLM, oracle_build.SRC_THREADS, "-o", so_path, "-lm"], check=True)
     caught = []
     oracle.use_library(so_path)
     try:
@@ -161,8 +161,8 @@ def test_pins_catch_glm_mutant(name, workdir):
     so_path = os.path.join(workdir, "glm_" + name + ".so")
     with open(c_path, "w") as f:
         f.write(src.replace(old, new))
-    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", oracle_build.SRC, c_path,
-                    "-o", so_path, "-lm"], check=True)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-pthread", oracle_build.SRC,
+                    c_path, oracle_build.SRC_THREADS, "-o", so_path, "-lm"], check=True)
     caught = []
     oracle.use_library(so_path)
     try:
