@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--tuning", default=None,
                    help="kernel,lanes_per_col,threads_per_block,heads[,zero_cert] set by hand (pcdm_set_tuning) instead of "
                         "pcdm_autotune, e.g. 0,1,448,1 for the pipelined kernel with 448-thread blocks")
+    p.add_argument("--no-precisions", action="store_true",
+                   help="skip the other precision pairs and the errors against the oracle")
     p.add_argument("--no-gather-ceiling", action="store_true",
                    help="skip the random-gather ceiling measured beside the roofline")
     p.add_argument("--sweep", action="store_true", help="print the omega x tau x dtype table of the scale workload")
@@ -170,39 +172,30 @@ def traffic_per_update(a, tuning):
     return float(ent["dram_bytes_per_update"]), ent["tuning"]
 
 
-def gather_ceiling(m, elem_bytes, kernel_gathers_per_s, n_idx=1 << 24, reps=5):
+def gather_ceiling(m, elem_bytes, kernel_gathers_per_s):
     """Random-gather rates of this GPU as a second ceiling for the iteration
-    kernel, whose time goes to scattered gathers of g: torch.index_select of
-    elem_bytes-wide values at n_idx uniform random int32 indices, from a vector of
-    m entries (the size of one residual buffer, L2-resident) and from a 4 GiB one
-    (every gather a DRAM access).  Reported beside the kernel's own rate of
-    gathered nonzeros per second."""
+    kernel, whose time goes to scattered gathers of g: pcdm_gather_rate (a full
+    grid of independent coherent loads at hashed positions) from a vector of m
+    entries (the size of one residual buffer, L2-resident) and from a 4 GiB one
+    (every gather a DRAM access), beside the kernel's own rate of gathered
+    nonzeros per second."""
     import torch
+    from paper_1212_0873_gb300 import _binding as B
     dt = torch.float64 if elem_bytes == 8 else torch.float32
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(12345)
+    st = torch.cuda.current_stream().cuda_stream
     out = {}
     for name, size in (("l2_resident", int(m)), ("hbm", (4 << 30) // elem_bytes)):
         src = torch.ones(size, dtype=dt, device="cuda")
-        idx = torch.randint(0, size, (n_idx,), generator=gen, device="cuda", dtype=torch.int32)
-        dst = torch.empty(n_idx, dtype=dt, device="cuda")
-        for _ in range(2):
-            torch.index_select(src, 0, idx, out=dst)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            torch.index_select(src, 0, idx, out=dst)
-        e1.record()
-        e1.synchronize()
-        out["gathers_per_s_" + name] = n_idx * reps / (e0.elapsed_time(e1) / 1e3)
-        del src, idx, dst
+        out["gathers_per_s_" + name] = B.pcdm_gather_rate(src.data_ptr(), size, elem_bytes, st)
+        del src
     torch.cuda.empty_cache()
     out["kernel_gathers_per_s"] = kernel_gathers_per_s
-    out["kernel_frac_of_l2_resident"] = kernel_gathers_per_s / out["gathers_per_s_l2_resident"]
-    out["how"] = ("torch.index_select of %d-byte values at %d uniform random int32 indices from a vector of "
-                  "%d entries (one residual buffer) and from a 4 GiB vector; kernel: gathered nonzeros per "
-                  "second of the iteration kernel's launches" % (elem_bytes, n_idx, int(m)))
+    if kernel_gathers_per_s is not None:
+        out["kernel_frac_of_l2_resident"] = kernel_gathers_per_s / out["gathers_per_s_l2_resident"]
+        out["kernel_frac_of_hbm"] = kernel_gathers_per_s / out["gathers_per_s_hbm"]
+    out["how"] = ("pcdm_gather_rate: 2 x 1024 threads per SM, rounds of 16 independent %d-byte coherent loads at "
+                  "hashed positions, from a vector of %d entries (one residual buffer) and from a 4 GiB vector; "
+                  "kernel: gathered nonzeros per second of the iteration kernel's launches" % (elem_bytes, int(m)))
     return out
 
 
@@ -258,15 +251,25 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- the oracle arm
-def oracle_sample(inst, tau, seconds, max_iters):
-    """Time the FP64 oracle on the first iterations of the same solve (single thread)."""
+def host_threads():
+    """Host cores this process may run on (the CPU baseline's thread count)."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except Exception:
+        return max(1, os.cpu_count() or 1)
+
+
+def oracle_sample(inst, tau, seconds, max_iters, threads=1, refresh_every=0):
+    """Time the FP64 oracle on the first iterations of the same solve: its
+    threaded timing mode on `threads` host threads (equal to the single-threaded
+    run bit for bit)."""
     import oracle
     st = oracle.State(oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64), inst.b, inst.lam)
     done, t_used = 0, 0.0
     chunk = 1
     while t_used < seconds and done < max_iters:
         t0 = time.perf_counter()
-        st.run(tau, chunk, 0)
+        st.run_threads(tau, chunk, 0, threads, refresh_every=refresh_every)
         t_used += time.perf_counter() - t0
         done += chunk
         chunk = min(chunk * 2, max_iters - done) if done < max_iters else chunk
@@ -281,12 +284,13 @@ def run_reference(a, rank, world):
     import oracle
     inst = make_instance(a)
     st = oracle.State(oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64), inst.b, inst.lam)
-    iters_per_step = 2
+    threads = host_threads()
+    iters_per_step = 4
     for _ in range(a.warmup):
-        st.run(a.tau, iters_per_step, 0)
+        st.run_threads(a.tau, iters_per_step, 0, threads)
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        st.run(a.tau, iters_per_step, 0)
+        st.run_threads(a.tau, iters_per_step, 0, threads)
     dt = time.perf_counter() - t0
     value = a.steps * iters_per_step * a.tau / dt
     out = {
@@ -294,10 +298,11 @@ def run_reference(a, rank, world):
         "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "m": inst.m, "n": inst.n, "nnz": inst.nnz, "omega": a.omega,
-                   "tau": a.tau, "parallelism": "host, 1 thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d iterations of %d updates per step, continuing one PCDM1 run from x=0"
-                                   % (iters_per_step, a.tau)},
+                   "tau": a.tau, "parallelism": "host, %d threads" % threads},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d iterations of %d updates per step, continuing one PCDM1 run from x=0, the "
+                                   "oracle's threaded timing mode (FP64, bit-identical to its serial run) on %d "
+                                   "threads" % (iters_per_step, a.tau, threads)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -359,12 +364,20 @@ def run_batched_path(a):
             its += it
         return its
 
+    # the plain arm as the headline FP64 solve runs: the persisting-L2 window over its
+    # residual buffers and the kernel pcdm_autotune picks (tuned once on this A and tau,
+    # outside the timed region, and set on every later handle)
     plain_iters = 0
     t_plain = 0.0
-    with Lasso(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64, B[0].copy(), lmax[0]) as s:
+    with Lasso(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64, B[0].copy(), lmax[0], l2_persist=True) as s:
+        plain_tuning = s.autotune(tau, 20)
+        s.reset()
         plain_path(s, 0)                                  # warm-up
     for l in range(nrhs):
-        with Lasso(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64, B[l].copy(), lmax[l]) as s:
+        with Lasso(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64, B[l].copy(), lmax[l],
+                   l2_persist=True) as s:
+            s.set_tuning(plain_tuning["kernel"], plain_tuning["lanes_per_col"], plain_tuning["threads_per_block"],
+                         plain_tuning["heads"], plain_tuning["zero_cert"])
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -384,8 +397,9 @@ def run_batched_path(a):
         "max_rel_gap": worst,
         "plain_f64_time_s": t_plain,
         "plain_f64_iterations": plain_iters,
-        "plain": "the same 16 paths solved one problem at a time by the plain FP64 form (k_fused_pipe), "
-                 "values promoted exactly from the stored bf16",
+        "plain": "the same 16 paths solved one problem at a time by the plain FP64 form, values promoted "
+                 "exactly from the stored bf16, with the persisting-L2 window and the autotuner's kernel",
+        "plain_tuning": plain_tuning,
         "speedup_vs_plain_f64": t_plain / t_batched,
     }
 
@@ -658,6 +672,108 @@ def run_theory_vs_reality():
 
 
 # ----------------------------------------------------------------------------- the CUDA arm
+def kernel_name(a, tuning):
+    if a.unfused or (tuning and tuning["kernel"] == 2):
+        return "k_gather + k_scatter (two-kernel PCDM1 iterations)"
+    if tuning and tuning["kernel"] == 1:
+        return "k_fused (persistent PCDM1 iterations, %d lanes per column)" % tuning["lanes_per_col"]
+    if tuning and tuning["kernel"] == 3:
+        return "k_fused_pipe_rounds (persistent PCDM1 iterations, several positions per thread)"
+    return "k_fused_pipe (persistent PCDM1 iterations)"
+
+
+def kernel_roofline(a, st, tuning, dtype):
+    """Roofline of the iteration kernel from a handle's counters: algorithmic
+    bytes per launch (per gathered nonzero value + row index + g_r; per update
+    x_i read and write (FP64), 1/L_i and the column's start and length; per
+    scattered nonzero value + row index + read and write of g_r) over its
+    CUDA-event-timed average launch."""
+    sv, sg, sx = st["val_bytes"], st["xg_bytes"], 8
+    sidx, sL = 4, sg
+    alg_bytes = (st["gathered_nnz"] * (sv + sidx + sg) + st["updates"] * (2 * sx + sL + 8)
+                 + st["scattered_nnz"] * (sv + sidx + 2 * sg))
+    launches = max(st["iter_launches"], 1)
+    avg_launch_s = st["iter_kernel_ms"] / launches / 1e3
+    achieved = alg_bytes / launches / avg_launch_s / 1e9 if avg_launch_s > 0 else None
+    peak, peak_kind = measured_peaks()
+    b = argparse.Namespace(**dict(vars(a), dtype=dtype))
+    tpu, tpu_tuning = traffic_per_update(b, tuning)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (tpu * st["updates"] / launches) if tpu is not None else None,
+                "kernel": kernel_name(a, tuning), "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes / launches, "avg_launch_ms": avg_launch_s * 1e3,
+                "launches": st["iter_launches"], "traffic_taken_at": tpu_tuning}
+    return roofline, avg_launch_s, launches
+
+
+def rel_err(a_, b_):
+    b_ = np.asarray(b_, dtype=np.float64)
+    return float(np.max(np.abs(np.asarray(a_, dtype=np.float64) - b_))) / max(float(np.max(np.abs(b_))), 1e-300)
+
+
+def error_vs_oracle(a, inst, solver, refresh, x_final, gpu_rel_gap, threads, K=64):
+    """The result's error against the FP64 oracle: x and g after K iterations
+    from x = 0 (same seed and samples on both sides), and the final x of the
+    timed solve judged by the oracle's own residual and duality gap."""
+    import oracle
+    solver.reset()
+    solver.step(a.tau, K, 0)
+    xg, gg = solver.x(), solver.residual()
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    ref.run_threads(a.tau, K, 0, threads, refresh_every=refresh)
+    r = oracle.residual(A, inst.b, x_final)
+    rec = oracle.gap(A, inst.b, x_final, r, inst.lam)
+    return {"iterations": K, "x_rel_err_after_K": rel_err(xg, ref.x), "g_rel_err_after_K": rel_err(gg, ref.g),
+            "final_rel_gap_by_oracle": rec["gap"] / max(rec["primal"], 1e-300), "final_rel_gap_by_gpu": gpu_rel_gap,
+            "how": "max|v - v_oracle| / max|v_oracle| after K iterations of tau=%d from x=0 (seed 0, the same S_k; "
+                   "the oracle in FP64 on the stored values); the oracle's residual and duality gap of the timed "
+                   "solve's final x" % a.tau}
+
+
+def run_other_precision(a, dtype, threads, steps=5, warmup=3):
+    """The same workload with values stored in `dtype` (FP32 residual, FP64 x,
+    FP64 refresh every 64 iterations and FP64 gap): time to relative gap tol,
+    updates/s, the iteration kernel's roofline and the error against the oracle."""
+    import torch
+    from paper_1212_0873_gb300 import Lasso
+    b = argparse.Namespace(**dict(vars(a), dtype=dtype))
+    inst = make_instance(b)
+    refresh = 64
+    solver = Lasso.from_instance(inst, profile=True, refresh_every=refresh, check_every=a.check_every)
+    try:
+        tuning = solver.autotune(a.tau, 30) if not a.no_tune else None
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for _ in range(warmup):
+            solver.reset()
+            solver.solve(a.tau, 0, a.tol, a.max_iters)
+        solver.reset_stats()
+        ms, its, rel = [], [], None
+        for _ in range(steps):
+            flush.zero_()
+            solver.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ok, it, rel = solver.solve(a.tau, 0, a.tol, a.max_iters)
+            e1.record()
+            e1.synchronize()
+            if not ok:
+                raise RuntimeError("%s solve did not converge" % dtype)
+            ms.append(e0.elapsed_time(e1))
+            its.append(it)
+        st = solver.stats()
+        x_final = solver.x()
+        roof, _, _ = kernel_roofline(b, st, tuning, dtype)
+        err = error_vs_oracle(b, inst, solver, refresh, x_final, rel, threads)
+    finally:
+        solver.close()
+    return {"values": dtype, "residual": "f32", "refresh_every": refresh, "tuning": tuning,
+            "updates_per_s": st["updates"] / (sum(ms) / 1e3), "time_to_gap_s": sum(ms) / len(ms) / 1e3,
+            "iterations": its[-1], "us_per_iteration": 1e3 * st["iter_kernel_ms"] / max(st["iterations"], 1),
+            "roofline": roof, "error_vs_oracle": err, "steps": steps}
+
+
 def run_pcdm(a, rank, local, world):
     import torch
     from paper_1212_0873_gb300 import Lasso
@@ -718,31 +834,8 @@ def run_pcdm(a, rank, local, world):
     local_updates = st["updates"]
     value, max_seconds, _ = aggregate(local_updates, local_seconds, world)
 
-    # roofline of the fused iteration kernel
-    # algorithmic bytes: per gathered nonzero value + row index + g_r; per update
-    # x_i read and write (FP64), 1/L_i and the column's start and length; per
-    # scattered nonzero value + row index + read and write of g_r
-    sv, sg, sx = st["val_bytes"], st["xg_bytes"], 8
-    sidx, sL = 4, sg
-    alg_bytes = (st["gathered_nnz"] * (sv + sidx + sg) + st["updates"] * (2 * sx + sL + 8)
-                 + st["scattered_nnz"] * (sv + sidx + 2 * sg))
-    launches = max(st["iter_launches"], 1)
-    avg_launch_s = st["iter_kernel_ms"] / launches / 1e3
-    achieved = alg_bytes / launches / avg_launch_s / 1e9 if avg_launch_s > 0 else None
-    peak, peak_kind = measured_peaks()
-    tpu, tpu_tuning = traffic_per_update(a, tuning)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": (tpu * st["updates"] / launches) if tpu is not None else None,
-                "kernel": ("k_gather + k_scatter (two-kernel PCDM1 iterations)" if a.unfused or
-                           (tuning and tuning["kernel"] == 2) else
-                           "k_fused (persistent PCDM1 iterations, %d lanes per column)" % tuning["lanes_per_col"]
-                           if tuning and tuning["kernel"] == 1 else
-                           "k_fused_pipe_rounds (persistent PCDM1 iterations, several positions per thread)"
-                           if tuning and tuning["kernel"] == 3 else
-                           "k_fused_pipe (persistent PCDM1 iterations)"), "peak_source": peak_kind,
-                "alg_bytes_per_launch": alg_bytes / launches, "avg_launch_ms": avg_launch_s * 1e3,
-                "launches": st["iter_launches"], "traffic_taken_at": tpu_tuning}
+    roofline, avg_launch_s, launches = kernel_roofline(a, st, tuning, a.dtype)
+    sg = st["xg_bytes"]
     if avg_launch_s > 0 and not a.no_gather_ceiling:
         roofline["gather_ceiling"] = gather_ceiling(a.n, sg, st["gathered_nnz"] / launches / avg_launch_s)
 
@@ -788,11 +881,28 @@ def run_pcdm(a, rank, local, world):
                "ms_create_solve_finish": [round(1e3 * p / len(e2e_s), 2) for p in phases], "l2_persist": False}
 
     cpu = None
+    threads = host_threads()
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        v, done, used = oracle_sample(inst, a.tau, a.cpu_seconds, max(1, (a.n + a.tau - 1) // a.tau))
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d iterations (tau=%d, %d updates) of the same solve from x=0, single-threaded "
-                         "FP64 oracle, %.1f s" % (done, a.tau, done * a.tau, used)}
+        v, done, used = oracle_sample(inst, a.tau, a.cpu_seconds, max(1, (a.n + a.tau - 1) // a.tau), threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "first %d iterations (tau=%d, %d updates) of the same solve from x=0, the FP64 oracle's "
+                         "threaded timing mode (bit-identical to its serial run) on %d host threads, %.1f s"
+                         % (done, a.tau, done * a.tau, threads, used)}
+
+    # every precision pair on the same workload, each with its error against the oracle
+    precisions = None
+    if rank == 0 and world == 1 and not a.no_precisions:
+        x_final = solver.x()
+        head = {"values": a.dtype, "residual": "f64" if a.dtype == "f64" else "f32", "refresh_every": refresh,
+                "tuning": tuning, "updates_per_s": value, "time_to_gap_s": max_seconds / a.steps,
+                "iterations": iters[-1], "us_per_iteration": 1e3 * st["iter_kernel_ms"] / max(st["iterations"], 1),
+                "roofline": {k: roofline[k] for k in ("achieved", "peak", "frac", "traffic", "kernel")},
+                "error_vs_oracle": error_vs_oracle(a, inst, solver, refresh, x_final, rel, threads),
+                "steps": a.steps}
+        precisions = {a.dtype: head}
+        for dt in ("f64", "f32", "bf16"):
+            if dt != a.dtype:
+                precisions[dt] = run_other_precision(a, dt, threads)
 
     asyn = None
     if rank == 0 and world == 1 and not a.no_async:
@@ -835,7 +945,11 @@ def run_pcdm(a, rank, local, world):
             "e2e": e2e,
             "gpu_launches": st["kernel_launches"],
             "clocks": clk,
+            "precisions": precisions,
             "batched": batched,
+            "batched_time_s": batched["time_s"] if batched else None,
+            "plain_f64_time_s": batched["plain_f64_time_s"] if batched else None,
+            "batched_speedup_vs_plain_f64": batched["speedup_vs_plain_f64"] if batched else None,
             "asynchronous": asyn,
             "many_small_problems": multi,
             "differentiation": grad,

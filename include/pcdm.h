@@ -427,6 +427,21 @@ pcdm_status pcdm_sample_kind(int32_t kind, uint64_t seed, int64_t k, int64_t n, 
 pcdm_status pcdm_selftest_barrier_timeout(uint64_t timeout_ns, void *cuda_stream);
 
 /*
+ * Random-gather rate of the current GPU, a measurement helper with no
+ * counterpart in the paper: the iteration kernels spend their time on gathers
+ * of the residual at random rows, so this rate is their second ceiling beside
+ * the HBM copy bandwidth.  A full grid (two blocks of 1024 threads per SM)
+ * issues rounds of 16 independent coherent loads of elem_bytes (4 or 8) at
+ * hashed positions of src (device memory, n elements, 1 <= n < 2^32; every
+ * index is below n), twice untimed and five times between CUDA events on
+ * cuda_stream; *gathers_per_s (host) receives loads per second.  src is only
+ * read.  EINVAL for NULL pointers or bad sizes, ECUDA on a CUDA error.
+ * Synchronises the stream.
+ */
+pcdm_status pcdm_gather_rate(const void *src, int64_t n, int32_t elem_bytes, double *gathers_per_s,
+                             void *cuda_stream);
+
+/*
  * omega = the largest number of nonzeros in one row of A (the omega of the
  * tau-nice ESO parameter beta, Theorem ESO-nice, Sec. 6.3) for a CSC matrix already in
  * device memory, with no handle and WITHOUT ALLOCATING ANY MEMORY.  The paper

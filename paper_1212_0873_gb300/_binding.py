@@ -57,6 +57,7 @@ SIGNATURES = {
     "pcdm_solve": (_i32, [_ptr, _i64, _u64, _dbl, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "pcdm_next_check_interval": (_i64, [_i64, _i64, ctypes.c_double, _i64, ctypes.c_double, ctypes.c_double]),
     "pcdm_omega_noalloc": (_i32, [ctypes.POINTER(pcdm_csc), ctypes.POINTER(_i64), _ptr]),
+    "pcdm_gather_rate": (_i32, [_ptr, _i64, _i32, ctypes.POINTER(_dbl), _ptr]),
     "pcdm_batch_create": (_i32, [ctypes.POINTER(pcdm_csc), _i64, _ptr, _i32, _ptr, ctypes.POINTER(pcdm_opts), _ptr,
                                  _ptr]),
     "pcdm_batch_step": (_i32, [_ptr, _i64, _i64, _u64]),
@@ -268,6 +269,14 @@ def pcdm_sample(seed, k, n, tau, S_device_ptr, stream=0):
 def pcdm_selftest_barrier_timeout(timeout_ns, stream=0):
     """Returns the raw status (PCDM_ETIMEOUT is the expected outcome)."""
     return int(lib().pcdm_selftest_barrier_timeout(int(timeout_ns), _stream(stream)))
+
+
+def pcdm_gather_rate(src_device_ptr, n, elem_bytes, stream=0):
+    """Random gathers per second from a device vector of n elem_bytes-wide values."""
+    out = _dbl(0.0)
+    _check(lib().pcdm_gather_rate(_ptr(src_device_ptr), int(n), int(elem_bytes), ctypes.byref(out),
+                                  _stream(stream)), None)
+    return float(out.value)
 
 
 def pcdm_destroy(h):

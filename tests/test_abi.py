@@ -256,3 +256,14 @@ def test_create_problem_rejects_bad_arguments_before_device_work(B):
     assert "deterministic" in (msg.decode() if isinstance(msg, bytes) else msg)
     assert not h.value
     assert L.pcdm_problem_kind(None, None) != 0
+
+
+def test_gather_rate_rejects_bad_arguments(B):
+    L = B.lib()
+    out = ctypes.c_double(-1.0)
+    buf = ctypes.c_void_p(1 << 20)                  # never dereferenced: every case fails before device work
+    assert L.pcdm_gather_rate(None, 10, 8, ctypes.byref(out), None) == B.PCDM_EINVAL
+    assert L.pcdm_gather_rate(buf, 10, 8, None, None) == B.PCDM_EINVAL
+    for n, eb in ((0, 8), (-1, 4), (2**32, 4), (10, 2), (10, 16)):
+        assert L.pcdm_gather_rate(buf, n, eb, ctypes.byref(out), None) == B.PCDM_EINVAL, (n, eb)
+    assert out.value == -1.0
