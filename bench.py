@@ -883,11 +883,12 @@ def run_pcdm(a, rank, local, world):
     cpu = None
     threads = host_threads()
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        v, done, used = oracle_sample(inst, a.tau, a.cpu_seconds, max(1, (a.n + a.tau - 1) // a.tau), threads)
+        v, done, used = oracle_sample(inst, a.tau, a.cpu_seconds, max(1, iters[-1]), threads)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": "first %d iterations (tau=%d, %d updates) of the same solve from x=0, the FP64 oracle's "
+               "sample": "first %d iterations (tau=%d, %d updates; the GPU's solve takes %d) of the same solve from "
+                         "x=0, the FP64 oracle's "
                          "threaded timing mode (bit-identical to its serial run) on %d host threads, %.1f s"
-                         % (done, a.tau, done * a.tau, threads, used)}
+                         % (done, a.tau, done * a.tau, iters[-1], threads, used)}
 
     # every precision pair on the same workload, each with its error against the oracle
     precisions = None
