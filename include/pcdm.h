@@ -288,16 +288,19 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
  * the grid), each with and without the column heads (and, in the FP64 form of LASSO,
  * with and without zero_cert), its rounds form with blocks of 128 or 256 threads (several
  * positions per thread and iteration), the fused kernel with 1 .. 32 lanes per
- * column (its scatter reloads the column), and the two-kernel form with 1, 4 or
- * 16 lanes.  The fastest is kept for later pcdm_step /
+ * column (its scatter reloads the column), the two-kernel form with 1, 4 or
+ * 16 lanes, and the streaming kernel (4) with blocks of 128, 256 or 448 threads:
+ * one lane per column as the pipelined kernel, but the whole column reaches its
+ * thread chunk by chunk through TMA bulk copies into shared memory, two chunks
+ * ahead of the gathers (for long columns).  The fastest is kept for later pcdm_step /
  * pcdm_solve calls (for any tau; tune again for a very different one).
  * Needs the tau-nice sampling and opts.fused = 1.
  */
 typedef struct {
     int32_t kernel;             /* 0 pipelined, 1 fused with lanes_per_col lanes, 2 two-kernel form,
-                                   3 pipelined rounds */
+                                   3 pipelined rounds, 4 streaming */
     int32_t lanes_per_col;
-    int32_t threads_per_block;  /* pipelined kernel only */
+    int32_t threads_per_block;  /* pipelined, rounds and streaming kernels */
     int32_t heads;              /* pipelined kernels: 1 = fetch each sampled column's first chunk
                                    (16 row indices, then 16 values) with one bulk copy from a
                                    per-column head array, n * (64 + 16 sizeof(value)) bytes built
@@ -584,6 +587,20 @@ pcdm_status pcdm_batch_get_stats(pcdm_batch_handle h, pcdm_stats *out);
 pcdm_status pcdm_batch_reset_stats(pcdm_batch_handle h);
 
 void pcdm_batch_destroy(pcdm_batch_handle h);
+
+/* Autotuner of the batched iteration kernel (NEXT row 1 of the build's scope:
+ * the launch shape of k_batch_iter).  A group of bp lanes (one per right-hand
+ * side) owns a sampled column at a time; the grid decides how many columns a
+ * group takes per iteration (the tau-chunk) against how many groups share each
+ * SM.  Times trial_iters iterations for every grid of 1, 2, ... blocks per SM
+ * up to the co-resident limit (and the blocks tau needs), from the handle's
+ * current state, which is restored after every trial (X, G, the iteration
+ * counter and the statistics), and keeps the fastest for later steps and
+ * solves.  *blocks_per_sm and *us_per_iteration (either may be NULL) receive
+ * the choice and its time per iteration.  EINVAL for a bad tau or
+ * trial_iters; ENOMEM when the state copy does not fit. */
+pcdm_status pcdm_batch_autotune(pcdm_batch_handle h, int64_t tau, int64_t trial_iters, int32_t *blocks_per_sm,
+                                double *us_per_iteration);
 
 /* Last error of the batch handle; with NULL, that of a failed pcdm_batch_create
  * on this thread. */

@@ -72,6 +72,7 @@ SIGNATURES = {
     "pcdm_batch_reset_stats": (_i32, [_ptr]),
     "pcdm_batch_destroy": (None, [_ptr]),
     "pcdm_batch_last_error": (ctypes.c_char_p, [_ptr]),
+    "pcdm_batch_autotune": (_i32, [_ptr, _i64, _i64, ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
     "pcdm_set_b": (_i32, [_ptr, _ptr, _i32, _i32]),
     "pcdm_support_size": (_i32, [_ptr, _ptr]),
     "pcdm_polish": (_i32, [_ptr, _i64, _u64, _dbl, _i64, _ptr, _ptr]),
@@ -374,6 +375,12 @@ def pcdm_batch_get_stats(h):
 
 def pcdm_batch_reset_stats(h):
     _bcheck(lib().pcdm_batch_reset_stats(h), h)
+
+
+def pcdm_batch_autotune(h, tau, trial_iters):
+    bps, us = _i32(0), _dbl(0.0)
+    _bcheck(lib().pcdm_batch_autotune(h, int(tau), int(trial_iters), ctypes.byref(bps), ctypes.byref(us)), h)
+    return {"blocks_per_sm": int(bps.value), "us_per_iteration": float(us.value)}
 
 
 def pcdm_batch_destroy(h):

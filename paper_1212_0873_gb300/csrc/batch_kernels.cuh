@@ -196,19 +196,42 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_iter(const BatchArgs<VT, 
         if (!grid_sync(a.bar, target, a.status, a.timeout_ns)) return;
 
         // ---------------- phase 2: scatter of the listed columns' steps
+        // FP32 residuals: lane 4q adds the steps of problems 4q .. 4q+3 into the
+        // four consecutive entries of row r with one vector reduction (16-byte
+        // aligned: bp is a multiple of 4); FP64 residuals: one reduction per lane.
         const int64_t total = int64_t(ld_volatile_u32(cnt_k));
+        const uint64_t pl = l2_evict_last();
         for (int64_t sl = grp; sl < total; sl += ngrp) {
             const int32_t i = ldcg(a.list + sl);
             const XT h = ldcg(a.H + sl * BP + lane);
             const Col<XT> c = load_col(a.desc, i);
-            for (int cs = 0; cs < c.cnt; cs += kE) {
-                Chunk<kE, XT> t;
-                ld_chunk<kE>(t, a.prow, a.pval, c.pbeg + cs);
-                const int valid = c.cnt - cs;
-                if (h != XT(0)) {
+            if constexpr (sizeof(XT) == 4) {
+                const int q0 = lane & ~3;
+                const float h0 = __shfl_sync(gmask, h, q0 + 0, BP), h1 = __shfl_sync(gmask, h, q0 + 1, BP);
+                const float h2 = __shfl_sync(gmask, h, q0 + 2, BP), h3 = __shfl_sync(gmask, h, q0 + 3, BP);
+                const bool mine = (lane & 3) == 0 && (h0 != 0.f || h1 != 0.f || h2 != 0.f || h3 != 0.f);
+                for (int cs = 0; cs < c.cnt; cs += kE) {
+                    Chunk<kE, XT> t;
+                    ld_chunk<kE>(t, a.prow, a.pval, c.pbeg + cs);
+                    const int valid = c.cnt - cs;
+                    if (mine) {
 #pragma unroll
-                    for (int e = 0; e < kE; ++e)
-                        if (e < valid) red_add(a.G + int64_t(t.row[e]) * BP + lane, t.val[e] * h);
+                        for (int e = 0; e < kE; ++e)
+                            if (e < valid)
+                                red_add_v4(reinterpret_cast<float *>(a.G) + int64_t(t.row[e]) * BP + lane,
+                                           t.val[e] * h0, t.val[e] * h1, t.val[e] * h2, t.val[e] * h3, pl);
+                    }
+                }
+            } else {
+                for (int cs = 0; cs < c.cnt; cs += kE) {
+                    Chunk<kE, XT> t;
+                    ld_chunk<kE>(t, a.prow, a.pval, c.pbeg + cs);
+                    const int valid = c.cnt - cs;
+                    if (h != XT(0)) {
+#pragma unroll
+                        for (int e = 0; e < kE; ++e)
+                            if (e < valid) red_add(a.G + int64_t(t.row[e]) * BP + lane, t.val[e] * h, pl);
+                    }
                 }
             }
             if (lane == 0) cnt.scattered += (unsigned long long)c.cnt;

@@ -230,6 +230,25 @@ bool pipe_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads = 0
     return true;
 }
 
+// Shape of the streaming kernel for tau, if it applies: as the pipelined kernel,
+// one lane per column, every position owned by one thread of a co-resident grid.
+template <typename VT, typename XT>
+bool stream_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads)
+{
+    int64_t threads = want_threads > 0 ? want_threads : (tau + h->sms - 1) / h->sms;
+    threads = (threads + 31) / 32 * 32;
+    if (threads < 32) threads = 32;
+    if (threads > kPipeMaxBlock) return false;
+    int64_t blocks = (tau + threads - 1) / threads;
+    if (blocks < h->sms) blocks = tau < h->sms ? tau : h->sms;
+    const int cap = Kernels<VT, XT>::stream_max_blocks(int(threads));
+    if (cap <= 0 || blocks > cap) return false;
+    sh->W = 1;
+    sh->blocks = int(blocks);
+    sh->threads = int(threads);
+    return true;
+}
+
 // The per-column heads of the pipelined kernels, built on their first use.
 template <typename VT, typename XT>
 pcdm_status ensure_heads(pcdm_handle h, IterArgs<VT, XT> &a)
@@ -306,7 +325,9 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
     } else if (h->opts.fused && h->tune_kernel != 2) {
         FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
-        const bool pipe = (h->tune_kernel == 1 || h->tune_kernel == 3)
+        // the streaming kernel (kernel 4): by the tuning only
+        const bool stream = h->tune_kernel == 4 && stream_shape<VT, XT>(h, tau, &sh, h->tune_threads);
+        const bool pipe = (stream || h->tune_kernel == 1 || h->tune_kernel == 3 || h->tune_kernel == 4)
                               ? false
                               : pipe_shape<VT, XT>(h, tau, &sh, h->tune_kernel == 0 ? h->tune_threads : 0);
         // rounds: when chosen (pcdm_autotune / pcdm_set_tuning); on the workloads measured so far
@@ -328,7 +349,18 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
             pcdm_status hs = ensure_heads<VT, XT>(h, a);
             if (hs != PCDM_OK) return hs;
         }
-        if (rounds) {
+        if (stream) {
+            const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
+            if (!h->g2) {
+                CK(h, cudaStreamSynchronize(h->stream));
+                CK(h, halloc_bytes(h, &h->g2, int64_t(gbytes)));
+                a.g2 = static_cast<XT *>(h->g2);
+                h->g2_valid = false;
+            }
+            if (!h->g2_valid) CK(h, cudaMemcpyAsync(h->g2, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
+            CK(h, Kernels<VT, XT>::fused_stream(a, sh, h->k, iters, h->stream));
+            h->g2_valid = true;
+        } else if (rounds) {
             const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
             if (!h->g2) {
                 CK(h, cudaStreamSynchronize(h->stream));
@@ -1489,9 +1521,9 @@ pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
         return set_err(h, PCDM_EINVAL, "the SVM dual and logistic regression run in kernels 0, 1 and 2");
     const bool lanes_ok = t->lanes_per_col == 1 || t->lanes_per_col == 2 || t->lanes_per_col == 4 ||
                           t->lanes_per_col == 8 || t->lanes_per_col == 16 || t->lanes_per_col == 32;
-    if (t->kernel < 0 || t->kernel > 3 || !lanes_ok)
-        return set_err(h, PCDM_EINVAL, "kernel must be 0..3 and lanes_per_col a power of two up to 32");
-    if ((t->kernel == 0 && (t->threads_per_block < 32 || t->threads_per_block > kPipeMaxBlock)) ||
+    if (t->kernel < 0 || t->kernel > 4 || !lanes_ok)
+        return set_err(h, PCDM_EINVAL, "kernel must be 0..4 and lanes_per_col a power of two up to 32");
+    if (((t->kernel == 0 || t->kernel == 4) && (t->threads_per_block < 32 || t->threads_per_block > kPipeMaxBlock)) ||
         (t->kernel == 3 && (t->threads_per_block < 32 || t->threads_per_block > kPipeRoundsMaxBlock)) ||
         t->threads_per_block % 32 != 0)
         return set_err(h, PCDM_EINVAL, "threads_per_block must be a multiple of 32 within the kernel's limit");
@@ -1550,6 +1582,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     for (int W : {1, 2, 4, 8, 16, 32}) cands.push_back({1, W, 0, 1, -1});
     for (int W : {1, 4, 16}) cands.push_back({2, W, 0, 1, -1});
     for (int t : {128, 256}) cands.push_back({3, 1, t, 1, -1});
+    for (int t : {128, 256, 448}) cands.push_back({4, 1, t, 1, -1});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
@@ -1568,6 +1601,18 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
                 h->W = 1;
                 ok = pipe_shape<VT, XT>(h, tau, &sh, c.threads);
                 h->W = save_W;
+                return PCDM_OK;
+            });
+            if (!ok) continue;
+        }
+        if (c.kernel == 4) {
+            // the streaming kernel must hold tau positions at this block size
+            FusedShape sh;
+            bool ok = false;
+            dispatch(h, [&](auto *vt, auto *xt) {
+                using VT = std::remove_pointer_t<decltype(vt)>;
+                using XT = std::remove_pointer_t<decltype(xt)>;
+                ok = stream_shape<VT, XT>(h, tau, &sh, c.threads);
                 return PCDM_OK;
             });
             if (!ok) continue;

@@ -42,6 +42,7 @@ struct pcdm_batch_ctx {
     std::vector<int> active;
     int64_t k = 0;
     int64_t last_solve_iters = 0;   // iterations of the last pcdm_batch_solve (0 after create / reset)
+    int tune_blocks_per_sm = 0;     // grid of the iteration kernel chosen by pcdm_batch_autotune (0: built-in rule)
     bool failed = false;
     std::string err;
     int64_t st_iterations = 0, st_updates = 0, st_launches = 0, st_kernels = 0, st_refreshes = 0, st_gaps = 0;
@@ -260,6 +261,8 @@ pcdm_status bsegment_t(pcdm_batch_handle h, int64_t tau, uint64_t seed, int64_t 
     const int cap = BatchKernels<VT, XT>::iter_max_blocks(h->bp);
     if (cap <= 0) return berr(h, PCDM_ECUDA, "cooperative occupancy query failed");
     int64_t blocks = (tau * h->bp + kBatchBlock - 1) / kBatchBlock;
+    if (h->tune_blocks_per_sm > 0 && int64_t(h->tune_blocks_per_sm) * b->sms < blocks)
+        blocks = int64_t(h->tune_blocks_per_sm) * b->sms;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -439,6 +442,112 @@ void pcdm_batch_destroy(pcdm_batch_handle h)
 }
 
 const char *pcdm_batch_last_error(pcdm_batch_handle h) { return h ? h->err.c_str() : g_free_error.c_str(); }
+
+pcdm_status pcdm_batch_autotune(pcdm_batch_handle h, int64_t tau, int64_t trial_iters, int32_t *blocks_per_sm,
+                                double *us_per_iteration)
+{
+    pcdm_status s = busable(h);
+    if (s != PCDM_OK) return s;
+    const pcdm_handle b = h->base;
+    if (tau < 1 || tau > b->n || trial_iters < 1) return berr(h, PCDM_EINVAL, "bad tau or trial_iters");
+    s = ensure_btau(h, tau);
+    if (s != PCDM_OK) return s;
+    s = bsync(h);
+    if (s != PCDM_OK) return s;
+    int cap = 0;
+    bdispatch(h, [&](auto *vt, auto *xt) {
+        using VT = std::remove_pointer_t<decltype(vt)>;
+        using XT = std::remove_pointer_t<decltype(xt)>;
+        cap = BatchKernels<VT, XT>::iter_max_blocks(h->bp);
+        return PCDM_OK;
+    });
+    if (cap <= 0) return berr(h, PCDM_ECUDA, "cooperative occupancy query failed");
+    // the state the trials start from, restored after each one
+    const size_t xbytes = sizeof(double) * size_t(b->n) * size_t(h->bp);
+    const size_t gbytes = size_t(dtype_bytes(b->xg_dtype)) * size_t(b->m) * size_t(h->bp);
+    double *x0 = nullptr;
+    void *g0 = nullptr;
+    BCK(h, dalloc(&x0, int64_t(b->n) * h->bp));
+    cudaError_t e = dalloc_bytes(&g0, int64_t(gbytes));
+    if (e != cudaSuccess) {
+        cudaFree(x0);
+        return berr(h, PCDM_ENOMEM, "autotune state copy");
+    }
+    unsigned long long c0[3] = {0, 0, 0};
+    const int64_t k0 = h->k, st0[6] = {h->st_iterations, h->st_updates, h->st_launches, h->st_kernels,
+                                       h->st_refreshes, h->st_gaps};
+    const double ms0 = h->st_kernel_ms;
+    const int keep = h->tune_blocks_per_sm;
+    e = cudaMemcpy(c0, h->counters, sizeof(c0), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x0, h->X, xbytes, cudaMemcpyDeviceToDevice, bstream(h));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g0, h->G, gbytes, cudaMemcpyDeviceToDevice, bstream(h));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    // candidates: 1, 2, ... blocks per SM up to the co-resident limit and the blocks tau needs
+    const int64_t need = (tau * h->bp + kBatchBlock - 1) / kBatchBlock;
+    int best = 0;
+    double best_us = 0.0;
+    for (int per_sm = 1; e == cudaSuccess && s == PCDM_OK && per_sm * b->sms <= cap; ++per_sm) {
+        if (per_sm > 1 && int64_t(per_sm - 1) * b->sms >= need) break;
+        h->tune_blocks_per_sm = per_sm;
+        for (int rep = 0; rep < 2 && e == cudaSuccess && s == PCDM_OK; ++rep) {   // the first run warms up
+            e = cudaEventRecord(t0, bstream(h));
+            if (e != cudaSuccess) break;
+            s = bdispatch(h, [&](auto *vt, auto *xt) {
+                using VT = std::remove_pointer_t<decltype(vt)>;
+                using XT = std::remove_pointer_t<decltype(xt)>;
+                return bsegment_t<VT, XT>(h, tau, 0, trial_iters);
+            });
+            if (s != PCDM_OK) break;
+            e = cudaEventRecord(t1, bstream(h));
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e == cudaSuccess && rep == 1) {
+                const double us = 1e3 * double(ms) / double(trial_iters);
+                if (best == 0 || us < best_us) {
+                    best = per_sm;
+                    best_us = us;
+                }
+            }
+            h->k = k0;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->X, x0, xbytes, cudaMemcpyDeviceToDevice, bstream(h));
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->G, g0, gbytes, cudaMemcpyDeviceToDevice, bstream(h));
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->counters, c0, sizeof(c0), cudaMemcpyHostToDevice, bstream(h));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bstream(h));
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaFree(x0);
+    cudaFree(g0);
+    h->k = k0;
+    h->st_iterations = st0[0];
+    h->st_updates = st0[1];
+    h->st_launches = st0[2];
+    h->st_kernels = st0[3];
+    h->st_refreshes = st0[4];
+    h->st_gaps = st0[5];
+    h->st_kernel_ms = ms0;
+    for (auto &pr : h->ev_pending) {   // the trials' profile events are not the handle's work
+        h->ev_free.push_back(pr.first);
+        h->ev_free.push_back(pr.second);
+    }
+    h->ev_pending.clear();
+    if (s != PCDM_OK) {
+        h->tune_blocks_per_sm = keep;
+        return s;
+    }
+    if (e != cudaSuccess) {
+        h->tune_blocks_per_sm = keep;
+        return berr(h, PCDM_ECUDA, std::string("pcdm_batch_autotune: ") + cudaGetErrorString(e));
+    }
+    h->tune_blocks_per_sm = best;
+    if (blocks_per_sm) *blocks_per_sm = best;
+    if (us_per_iteration) *us_per_iteration = best_us;
+    return PCDM_OK;
+}
 
 pcdm_status pcdm_batch_step(pcdm_batch_handle h, int64_t tau, int64_t iters, uint64_t seed)
 {

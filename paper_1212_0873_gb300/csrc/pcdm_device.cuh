@@ -325,6 +325,14 @@ __device__ __forceinline__ void red_add(float *p, float v, uint64_t pol)
     asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
 }
 
+// g[0..3] += v[0..3] in one vector reduction (sm_90+); g 16-byte aligned.
+__device__ __forceinline__ void red_add_v4(float *p, float v0, float v1, float v2, float v3, uint64_t pol)
+{
+    asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v0), "f"(v1),
+                 "f"(v2), "f"(v3), "l"(pol)
+                 : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ T soft_threshold(T u, T t)
 {

@@ -97,7 +97,8 @@ struct pcdm_ctx {
     int64_t last_solve_iters = 0;   // iterations of the last pcdm_solve (0 after create / reset)
     uint64_t async_u = 0;           // next update number of the asynchronous mode
     // iteration kernel chosen by pcdm_autotune (-1: the built-in rule)
-    int tune_kernel = -1;           // 0 pipelined, 1 fused with tune_W lanes, 2 two-kernel form, 3 pipelined rounds
+    int tune_kernel = -1;           // 0 pipelined, 1 fused with tune_W lanes, 2 two-kernel form, 3 pipelined rounds,
+                                    // 4 streaming
     int tune_W = 0;
     int tune_threads = 0;           // block size of the pipelined kernel (0: built-in rule)
     int tune_heads = 1;             // pipelined kernels read the column heads (when they fit)

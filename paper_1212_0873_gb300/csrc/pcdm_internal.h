@@ -126,6 +126,11 @@ struct Kernels {
     static cudaError_t fused_pipe_rounds(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
                                          cudaStream_t st);
     static int pipe_rounds_max_blocks(int threads);
+    // Streaming persistent kernel for long columns (one lane per column, tau <= blocks * threads):
+    // every chunk of a column reaches its thread by TMA bulk copies (stream_kernels.cuh).
+    static cudaError_t fused_stream(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
+                                    cudaStream_t st);
+    static int stream_max_blocks(int threads);
     // Asynchronous updates u0 .. u0+count-1 (no barrier; atomics on x and g).
     static cudaError_t async(const IterArgs<VT, XT> &a, int blocks, uint64_t nthreads, uint64_t u0, uint64_t count,
                              cudaStream_t st);

@@ -217,11 +217,14 @@ __device__ __forceinline__ void ld_chunk_hint(Chunk<E, XT> &c, const int32_t *pr
     }
 }
 
+// Chunk load of the column kernels: A is read once per use, so it is marked
+// evict-first in L2, where it would otherwise push out the residual that every
+// gather reads (long columns stream about as many bytes of A per iteration as
+// L2 holds).
 template <int E, typename VT, typename XT>
 __device__ __forceinline__ void ld_chunk(Chunk<E, XT> &c, const int32_t *prow, const VT *pval, int64_t p)
 {
-    ld_rows<E>(c.row, prow + p);
-    ld_vals<E>(c.val, pval + p);
+    ld_chunk_hint<E>(c, prow, pval, p, l2_evict_first());
 }
 
 // The coordinate gradient of the smooth part is grad_i = sum_r a_ri phi(g_r).
@@ -240,13 +243,15 @@ __device__ __forceinline__ T grad_map(T v)
         return -1.0f / (1.0f + expf(v));
 }
 
-// sum_e val[e] * phi(v[row[e]]) over the first `valid` entries of the lane's run.
+// sum_e val[e] * phi(v[row[e]]) over the first `valid` entries of the lane's run
+// (the gathered vector marked evict-last in L2).
 template <int E, typename XT, typename GT, typename AT, int GM = 0>
 __device__ __forceinline__ AT chunk_dot(const Chunk<E, XT> &c, const GT *v, int valid)
 {
+    const uint64_t pl = l2_evict_last();
     GT gv[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) gv[e] = (e < valid) ? ldcg(v + c.row[e]) : GT(0);
+    for (int e = 0; e < E; ++e) gv[e] = (e < valid) ? ldcg_hint(v + c.row[e], pl) : GT(0);
     AT acc = AT(0);
 #pragma unroll
     for (int e = 0; e < E; ++e)
@@ -257,9 +262,10 @@ __device__ __forceinline__ AT chunk_dot(const Chunk<E, XT> &c, const GT *v, int 
 template <int E, typename XT>
 __device__ __forceinline__ void chunk_scatter(const Chunk<E, XT> &c, XT *g, XT h, int valid)
 {
+    const uint64_t pl = l2_evict_last();
 #pragma unroll
     for (int e = 0; e < E; ++e)
-        if (e < valid) red_add(g + c.row[e], c.val[e] * h);
+        if (e < valid) red_add(g + c.row[e], c.val[e] * h, pl);
 }
 
 template <int E, typename XT>
@@ -540,8 +546,9 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
             const double xi = ldcg(a.x + i0);
             XT gv[kE];
             const int valid0 = c0.cnt - lane * kE;
+            const uint64_t pl = l2_evict_last();
 #pragma unroll
-            for (int e = 0; e < kE; ++e) gv[e] = (e < valid0) ? ldcg(a.g + ch.row[e]) : XT(0);
+            for (int e = 0; e < kE; ++e) gv[e] = (e < valid0) ? ldcg_hint(a.g + ch.row[e], pl) : XT(0);
             i_next = sample_index(uint32_t(j0), key);
             c_next = load_col(a.desc, i_next);
             XT acc = XT(0);
@@ -1737,3 +1744,5 @@ cudaError_t Kernels<VT, XT>::gap_cols(const ColDesc<XT> *desc, const int32_t *pr
 }
 
 }  // namespace pcdm
+
+#include "stream_kernels.cuh"

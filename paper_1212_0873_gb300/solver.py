@@ -301,6 +301,10 @@ class BatchLasso:
         B.pcdm_batch_set_lambda(self._h, lams)
         self.lams = lams
 
+    def autotune(self, tau, trial_iters=20):
+        """Pick the grid of the batched iteration kernel for tau (pcdm_batch_autotune)."""
+        return B.pcdm_batch_autotune(self._h, tau, trial_iters)
+
     def reset(self):
         B.pcdm_batch_reset(self._h)
 

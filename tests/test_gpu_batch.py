@@ -159,3 +159,28 @@ def test_invalid_batches_are_rejected(case):
     with pytest.raises(PcdmError) as e:
         BatchLasso(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val, np.ascontiguousarray(Bm), lams)
     assert e.value.status == PCDM_EINVAL
+
+
+@pytest.mark.parametrize("val_dtype", ["f64", "bf16"])
+def test_batch_autotune_restores_the_state_and_keeps_parity(val_dtype):
+    # a larger instance, so that several grids are tried; the FP32 residuals use the
+    # four-problem vector reductions of the scatter (16 right-hand sides)
+    inst = instances.per_col_instance(400_000, 200_000, 15, nnz_star=1000, val_dtype=val_dtype, seed=1013)
+    Bm, lams = _rhs(inst, 16, 17, lam_fracs=np.geomspace(0.5, 0.05, 16))
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    tau, seed = 8192, 9
+    with BatchLasso(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val, Bm, lams) as bt:
+        bt.step(tau, 3, seed)
+        X3 = bt.x().copy()
+        st3 = bt.stats()
+        choice = bt.autotune(tau, 5)
+        assert choice["blocks_per_sm"] >= 1 and choice["us_per_iteration"] > 0
+        assert np.array_equal(bt.x(), X3)
+        st = bt.stats()
+        assert st["iterations"] == st3["iterations"] and st["gathered_nnz"] == st3["gathered_nnz"]
+        bt.step(tau, 9, seed)
+        X = bt.x()
+    for l in (0, 7, 15):
+        ref = oracle.State(A, Bm[l], lams[l])
+        ref.run(tau, 12, seed)
+        assert _rel(X[l], ref.x) <= TOL[val_dtype], l

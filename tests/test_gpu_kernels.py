@@ -1,5 +1,5 @@
 """Every iteration kernel (pipelined, fused with several lane widths, two-kernel,
-pipelined rounds; the pipelined ones with and without the column heads, the
+pipelined rounds, streaming; the pipelined ones with and without the column heads, the
 pipelined one also with and without the FP32 certificate of zero steps)
 selected by hand through pcdm_set_tuning follows the oracle;
 the rounds kernel also with several positions per thread (tau beyond the grid)."""
@@ -28,7 +28,8 @@ def _rel(a, b):
 
 # (kernel, lanes per column, threads per block, column heads[, zero-step certificate])
 CHOICES = [(0, 1, 64, 1), (0, 1, 448, 1), (0, 1, 128, 0), (0, 1, 64, 1, 1), (0, 1, 128, 0, 1), (0, 1, 448, 1, 0),
-           (1, 1, 0, 1), (1, 4, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1), (2, 16, 0, 1), (3, 1, 128, 1), (3, 1, 256, 0)]
+           (1, 1, 0, 1), (1, 4, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1), (2, 16, 0, 1), (3, 1, 128, 1), (3, 1, 256, 0),
+           (4, 1, 64, 1), (4, 1, 448, 1)]
 
 
 @pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])
@@ -65,6 +66,27 @@ def test_rounds_kernel_with_several_positions_per_thread(val_dtype, tol):
         ref.run(tau, 5, 8)
         assert _rel(s.x(), ref.x) <= tol
         ok, it, rel = s.solve(tau, 8, 1e-8 if val_dtype == "f64" else 1e-6, 100_000)
+        assert ok
+
+
+@pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])
+@pytest.mark.parametrize("per_col,threads", [(150, 448), (37, 128), (1, 64)])
+def test_streaming_kernel_on_long_and_short_columns(val_dtype, tol, per_col, threads):
+    # the streaming kernel copies every chunk of a column: 150 entries are ten chunks
+    # (the last one ragged); 37 three; 1 a single ragged chunk; ragged tau
+    inst = instances.per_col_instance(20_000, 4_000, per_col, nnz_star=200, val_dtype=val_dtype, seed=1021)
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    tau = min(2048 + 5, inst.n)
+    refresh = 0 if val_dtype == "f64" else 16
+    with Lasso.from_instance(inst, refresh_every=refresh) as s:
+        s.set_tuning(4, 1, threads, 1)
+        for upto in (1, 3, 30):
+            s.step(tau, upto - s.iteration, 6)
+            ref.run(tau, upto - ref.k, 6, refresh_every=refresh)
+            assert _rel(s.x(), ref.x) <= tol, upto
+            assert _rel(s.residual(), ref.g) <= tol, upto
+        ok, it, rel = s.solve(tau, 6, 1e-8 if val_dtype == "f64" else 1e-6, 100_000)
         assert ok
 
 
