@@ -14,8 +14,8 @@
 // occupy the load/store pipe that the scattered gathers of g saturate; for a
 // column of c entries the thread issues about c/kE pairs of bulk copies instead
 // of 3c/4 (FP64) vector loads spread over 32 cache lines per warp instruction.
-// The steps go through the block's queue as in the pipelined kernel; the scatter
-// of a moving coordinate (about 1% of LASSO's) rereads its column from memory.
+// The scatter of a moving coordinate (about 1% of LASSO's) rereads its column
+// from memory.
 #pragma once
 
 namespace pcdm {
@@ -48,14 +48,9 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_stream(const IterArg
     auto gbuf = [&](int64_t kk) { return (kk & 1) ? a.g2 : a.g; };
     auto chunks = [&](const Col<XT> &d) { return (d.cnt + kE - 1) / kE; };
 
-    __shared__ double s_qg[kPipeMaxBlock], s_qx[kPipeMaxBlock], s_ql[kPipeMaxBlock];
-    __shared__ XT s_qh[kPipeMaxBlock];
-    __shared__ int32_t s_qi[kPipeMaxBlock], s_qc[kPipeMaxBlock];
-    __shared__ unsigned s_qn;
     mbar_init(&mb[0], 1u);
     mbar_init(&mb[1], 1u);
     fence_mbarrier_init();
-    if (t == 0) s_qn = 0u;
     __syncthreads();
 
     // The stream of this thread's copies: the chunks of the current column, then
@@ -75,26 +70,28 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_stream(const IterArg
     int iss_c = 0, iss_n = 0;          // chunks of the current / next column issued
     uint32_t issued = 0, done = 0;     // items issued / read
     auto issue_one = [&]() -> bool {
-        const Col<XT> *d;
-        int q;
+        int64_t pbeg;
+        int cnt_c, q;
         if (iss_c < chunks(d_cur)) {
-            d = &d_cur;
+            pbeg = d_cur.pbeg;
+            cnt_c = d_cur.cnt;
             q = iss_c++;
         } else if (iss_n < chunks(d_nxt)) {
-            d = &d_nxt;
+            pbeg = d_nxt.pbeg;
+            cnt_c = d_nxt.cnt;
             q = iss_n++;
         } else {
             return false;
         }
         const int s = int(issued & 1u);
-        const int64_t pc = (int64_t(d->cnt) + G - 1) / G * G;
+        const int64_t pc = (int64_t(cnt_c) + G - 1) / G * G;
         const int64_t left = pc - int64_t(q) * kE;
         const uint32_t e = uint32_t(left < kE ? left : kE);
         const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
         fence_proxy_async_shared();   // this thread's reads of the slot come before the copy into it
         mbar_arrive_expect_tx(&mb[s], br + bv);
-        bulk_copy_g2s(slot(s), a.prow + d->pbeg + int64_t(q) * kE, br, &mb[s], pf);
-        bulk_copy_g2s(slot(s) + 64, a.pval + d->pbeg + int64_t(q) * kE, bv, &mb[s], pf);
+        bulk_copy_g2s(slot(s), a.prow + pbeg + int64_t(q) * kE, br, &mb[s], pf);
+        bulk_copy_g2s(slot(s) + 64, a.pval + pbeg + int64_t(q) * kE, bv, &mb[s], pf);
         issued += 1u;
         return true;
     };
@@ -128,11 +125,10 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_stream(const IterArg
             xi = ldcg_hint(a.x + i_cur, pf);
             XT acc = XT(0);
             const int nc = chunks(d_cur);
-            for (int q = 0; q < nc; ++q) {
-                if (!mbar_wait_bounded(&mb[done & 1u], (done >> 1) & 1u, a.status, a.timeout_ns)) {
-                    ok = false;
-                    break;
-                }
+            // Chunk q: wait for its copy, read its rows and values into registers,
+            // free the slot (the copy two items ahead may start), gather g at its rows.
+            auto load_gather = [&](int q, XT (&val)[kE], XT (&gv)[kE]) -> bool {
+                if (!mbar_wait_bounded(&mb[done & 1u], (done >> 1) & 1u, a.status, a.timeout_ns)) return false;
                 const unsigned char *sl = slot(int(done & 1u));
                 int32_t row[kE];
 #pragma unroll
@@ -143,7 +139,6 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_stream(const IterArg
                     row[4 * w + 2] = int32_t(r4.z);
                     row[4 * w + 3] = int32_t(r4.w);
                 }
-                XT val[kE];
 #pragma unroll
                 for (int w = 0; w < VW; ++w) {
                     XT vw[EPW];
@@ -154,19 +149,47 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_stream(const IterArg
                 done += 1u;
                 refill();
                 const int v = valid - q * kE;
-                XT gv[kE];
 #pragma unroll
                 for (int e = 0; e < kE; ++e) gv[e] = (e < v) ? ldcg_hint(gk + row[e], pl) : XT(0);
-                if (q == 0) {
-                    // the sample of k+2 (integer work) while the first gathers are in flight
-                    i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
-                    d_nn = load_col(a.desc, i_nn, pf);
-                }
+                return true;
+            };
+            auto dot = [&](int q, const XT (&val)[kE], const XT (&gv)[kE]) {
+                const int v = valid - q * kE;
 #pragma unroll
                 for (int e = 0; e < kE; ++e)
                     if (e < v) acc = fma(val[e], grad_map<GM>(gv[e]), acc);
+            };
+            if constexpr (sizeof(XT) == 4) {
+                // FP32 residual: the gathers of chunk q+1 are issued before the
+                // products of chunk q, two chunks of values and gathers in registers
+                XT va[kE], ga[kE], vb[kE], gb[kE];
+                if (nc > 0) ok = load_gather(0, va, ga);
+                if (ok) {
+                    i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
+                    d_nn = load_col(a.desc, i_nn, pf);
+                }
+                for (int q = 0; ok && q < nc; q += 2) {
+                    if (q + 1 < nc && !(ok = load_gather(q + 1, vb, gb))) break;
+                    dot(q, va, ga);
+                    if (q + 1 >= nc) break;
+                    if (q + 2 < nc && !(ok = load_gather(q + 2, va, ga))) break;
+                    dot(q + 1, vb, gb);
+                }
+            } else {
+                // FP64: one chunk at a time (two chunks of FP64 values and gathers
+                // would not fit the registers of a 448-thread block)
+                XT val[kE], gv[kE];
+                for (int q = 0; q < nc; ++q) {
+                    if (!(ok = load_gather(q, val, gv))) break;
+                    if (q == 0) {
+                        // the sample of k+2 (integer work) while the first gathers are in flight
+                        i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
+                        d_nn = load_col(a.desc, i_nn, pf);
+                    }
+                    dot(q, val, gv);
+                }
             }
-            if (nc == 0) {
+            if (nc == 0 && sizeof(XT) != 4) {
                 i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
                 d_nn = load_col(a.desc, i_nn, pf);
             }
@@ -189,37 +212,16 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_stream(const IterArg
             return;
         }
 
-        // ---------------- the steps of eq. (h(x)), compacted (as in k_fused_pipe)
-        {
-            const unsigned lane = unsigned(t) & 31u;
-            const unsigned vote = __ballot_sync(0xFFFFFFFFu, need_step);
-            unsigned base = 0u;
-            if (lane == 0 && vote != 0u) base = atomicAdd(&s_qn, unsigned(__popc(vote)));
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            const unsigned myq = base + unsigned(__popc(vote & ((1u << lane) - 1u)));
-            if (need_step) {
-                s_qg[myq] = step_grad;
-                s_qx[myq] = xi;
-                s_ql[myq] = double(d_cur.invL);
-                s_qi[myq] = i_cur;
-                s_qc[myq] = valid;
+        // ---------------- the step of eq. (h(x)) (FP64), x_i and the counters
+        if (need_step) {
+            const double xn = coord_step(a.problem, xi, step_grad, double(d_cur.invL), a.inv_beta, a.lambda, a.kappa);
+            const double h64 = xn - xi;
+            h = XT(h64);
+            if (h64 != 0.0) {   // most steps are zero: x_i unchanged
+                st_hint(a.x + i_cur, xn, pf);
+                cnt.nonzero += 1;
+                cnt.scattered += (unsigned long long)valid;
             }
-            __syncthreads();
-            const unsigned qn = s_qn;
-            for (unsigned q = unsigned(t); q < qn; q += unsigned(nt)) {
-                const double xq = s_qx[q];
-                const double xn = coord_step(a.problem, xq, s_qg[q], s_ql[q], a.inv_beta, a.lambda, a.kappa);
-                const double h64 = xn - xq;
-                s_qh[q] = XT(h64);
-                if (h64 != 0.0) {
-                    st_hint(a.x + s_qi[q], xn, pf);
-                    cnt.nonzero += 1;
-                    cnt.scattered += (unsigned long long)s_qc[q];
-                }
-            }
-            __syncthreads();
-            if (need_step) h = s_qh[myq];
-            if (t == 0) s_qn = 0u;
         }
 
         // ---------------- scatter of the steps of k-1 and k into the other buffer
