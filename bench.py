@@ -73,6 +73,7 @@ def parse():
     p.add_argument("--tuning", default=None,
                    help="kernel,lanes_per_col,threads_per_block,heads[,zero_cert] set by hand (pcdm_set_tuning) instead of "
                         "pcdm_autotune, e.g. 0,1,448,1 for the pipelined kernel with 448-thread blocks")
+    p.add_argument("--no-omega128", action="store_true", help="skip the omega = 128 FP64 solve (5.12e8 nonzeros)")
     p.add_argument("--no-precisions", action="store_true",
                    help="skip the other precision pairs and the errors against the oracle")
     p.add_argument("--no-gather-ceiling", action="store_true",
@@ -781,6 +782,43 @@ def run_other_precision(a, dtype, threads, steps=5, warmup=3):
             "roofline": roof, "error_vs_oracle": err, "steps": steps}
 
 
+def run_omega128(a, steps=3):
+    """The long-column end of the scale workload: m = n = 4e6 with omega = 128 nonzeros per row
+    (nnz = 5.12e8), FP64, tau = 65536, solved from x = 0 to relative gap tol; the kernel picked by
+    pcdm_autotune, with the persisting-L2 window, as the headline."""
+    import torch
+    from paper_1212_0873_gb300 import Lasso
+    b = argparse.Namespace(**dict(vars(a), omega=128, dtype="f64"))
+    t0 = time.perf_counter()
+    inst = make_instance(b)
+    t_gen = time.perf_counter() - t0
+    with Lasso.from_instance(inst, profile=True, refresh_every=0, l2_persist=True) as s:
+        tuning = s.autotune(a.tau, 20) if not a.no_tune else None
+        s.reset()
+        s.solve(a.tau, 0, a.tol, a.max_iters)              # warm-up
+        s.reset_stats()
+        ms, its = [], []
+        for _ in range(steps):
+            s.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ok, it, rel = s.solve(a.tau, 0, a.tol, a.max_iters)
+            e1.record()
+            e1.synchronize()
+            if not ok:
+                raise RuntimeError("omega = 128 solve did not converge")
+            ms.append(e0.elapsed_time(e1))
+            its.append(it)
+        st = s.stats()
+    roof, _, _ = kernel_roofline(b, st, tuning, "f64")
+    return {"workload": "square scale LASSO: m=n=%d, omega=128 per row (nnz=%d), tau=%d, f64 values, solve from x=0 "
+                        "to rel. duality gap %g" % (a.n, inst.nnz, a.tau, a.tol),
+            "updates_per_s": st["updates"] / (sum(ms) / 1e3), "time_to_gap_s": sum(ms) / len(ms) / 1e3,
+            "iterations": its[-1], "us_per_iteration": 1e3 * st["iter_kernel_ms"] / max(st["iterations"], 1),
+            "tuning": tuning, "roofline": {k: roof[k] for k in ("achieved", "peak", "frac", "kernel")},
+            "steps": steps, "instance_gen_s": t_gen}
+
+
 def run_pcdm(a, rank, local, world):
     import torch
     from paper_1212_0873_gb300 import Lasso
@@ -912,6 +950,9 @@ def run_pcdm(a, rank, local, world):
             if dt != a.dtype:
                 precisions[dt] = run_other_precision(a, dt, threads)
 
+    omega128 = None
+    if rank == 0 and world == 1 and not a.no_omega128:
+        omega128 = run_omega128(a)
     asyn = None
     if rank == 0 and world == 1 and not a.no_async:
         asyn = run_async(a, inst)
@@ -954,6 +995,7 @@ def run_pcdm(a, rank, local, world):
             "gpu_launches": st["kernel_launches"],
             "clocks": clk,
             "precisions": precisions,
+            "omega128": omega128,
             "batched": batched,
             "batched_time_s": batched["time_s"] if batched else None,
             "plain_f64_time_s": batched["plain_f64_time_s"] if batched else None,

@@ -159,3 +159,26 @@ def test_handle_memory_comes_back_from_the_pool():
     free1, _ = torch.cuda.mem_get_info()
     assert free1 >= free0 - (64 << 20)
     B.pcdm_set_memory_cache(16 << 30)
+
+
+@pytest.fixture(scope="module")
+def omega128_inst():
+    # 128 nonzeros in every row (the long-column end of the scale workload), smaller m = n
+    return instances.row_omega_instance(200_000, 200_000, 128, density=0.01, val_dtype="f64", seed=1031)
+
+
+@pytest.mark.parametrize("choice", [(1, 2, 0, 1), (2, 4, 0, 1), (4, 1, 448, 1), (0, 1, 448, 1)])
+def test_omega128_rows_follow_the_oracle(omega128_inst, choice):
+    inst = omega128_inst
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    assert ref.omega == 128
+    tau = 8192
+    with Lasso.from_instance(inst, l2_persist=True) as s:
+        assert s.omega == 128
+        s.set_tuning(*choice)
+        for upto in (1, 4, 12):
+            s.step(tau, upto - s.iteration, 4)
+            ref.run_threads(tau, upto - ref.k, 4, 8)
+            assert _rel(s.x(), ref.x) <= 1e-10, (choice, upto)
+            assert _rel(s.residual(), ref.g) <= 1e-10, (choice, upto)
