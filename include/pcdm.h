@@ -292,28 +292,39 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
  * 16 lanes, and the streaming kernel (4) with blocks of 128, 256 or 448 threads:
  * one lane per column as the pipelined kernel, but the whole column reaches its
  * thread chunk by chunk through TMA bulk copies into shared memory, two chunks
- * ahead of the gathers (for long columns).  The fastest is kept for later pcdm_step /
+ * ahead of the gathers (for long columns), and the warp-cooperative kernel (5) with
+ * blocks of 128, 256 or 512 threads: the 32 lanes of a warp share each of its columns
+ * (at most 32 positions per warp, so tau <= 32 * warps of the grid), one column after
+ * another with the next column's entries loading and its gathers in flight while the
+ * current column's products are taken; the partial sums of four (FP64) or eight
+ * columns are reduced over the warp together and the owner lanes take their steps
+ * side by side (for long columns; the FP64 form of LASSO certifies zero steps in FP32
+ * as zero_cert describes, unless zero_cert = 0).
+ * The fastest is kept for later pcdm_step /
  * pcdm_solve calls (for any tau; tune again for a very different one).
  * Needs the tau-nice sampling and opts.fused = 1.
  */
 typedef struct {
     int32_t kernel;             /* 0 pipelined, 1 fused with lanes_per_col lanes, 2 two-kernel form,
-                                   3 pipelined rounds, 4 streaming */
+                                   3 pipelined rounds, 4 streaming, 5 warp-cooperative */
     int32_t lanes_per_col;
-    int32_t threads_per_block;  /* pipelined, rounds and streaming kernels */
+    int32_t threads_per_block;  /* pipelined, rounds, streaming and warp-cooperative kernels */
     int32_t heads;              /* pipelined kernels: 1 = fetch each sampled column's first chunk
                                    (16 row indices, then 16 values) with one bulk copy from a
                                    per-column head array, n * (64 + 16 sizeof(value)) bytes built
                                    on first use when free device memory holds four times that;
                                    0 = two copies from the padded CSC arrays */
-    int32_t zero_cert;          /* pipelined kernel, FP64 form, LASSO: 1 = before the FP64 sum
+    int32_t zero_cert;          /* pipelined and warp-cooperative kernels, FP64 form, LASSO:
+                                   1 = before the FP64 sum
                                    a_i^T g, bound it in FP32 from the high words of the operands
                                    and take the step as 0 when the bound shows |a_i^T g| <= lambda
                                    at x_i = 0 (the same step the FP64 sum gives: eq. (h(x)) with
                                    x_i = 0 is 0 exactly when |grad_i| <= lambda); a warp whose
                                    lanes are all certified issues no FP64 instruction;
                                    0 = the FP64 sum for every column; -1 (pcdm_set_tuning only) =
-                                   the built-in rule, on when nnz <= 8 n.  The FP32 and BF16
+                                   the built-in rule: for kernel 0 on when nnz <= 8 n, for
+                                   kernel 5 always on (its lanes share a column: the bound
+                                   covers the warp's summation order).  The FP32 and BF16
                                    forms always compare their FP32 gradient with lambda rounded
                                    down, an exact test, and ignore this field. */
     double us_per_iteration;    /* measured */
@@ -323,9 +334,9 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
 
 /* Choose the iteration kernel by hand (the fields of pcdm_tuning; us_per_iteration
  * is ignored; heads 0 or 1; zero_cert -1, 0 or 1; threads_per_block a multiple of 32,
- * up to 448 for kernel 0 and 256 for kernel 3), or return to the built-in rule with
- * t = NULL.  A pipelined kernel that cannot hold tau at that block size falls back to
- * the fused one. */
+ * up to 448 for kernels 0 and 4, 256 for kernel 3 and 512 for kernel 5), or return to
+ * the built-in rule with t = NULL.  A pipelined, streaming or warp-cooperative kernel
+ * that cannot hold tau at that block size falls back to the fused one. */
 pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t);
 
 /* Recompute g = A x - b in FP64 (stored in g's dtype). */

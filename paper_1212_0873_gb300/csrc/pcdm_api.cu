@@ -249,6 +249,27 @@ bool stream_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads)
     return true;
 }
 
+// Shape of the warp-cooperative kernel for tau, if it applies: blocks of
+// `want_threads` (default kWarpMaxBlock) threads, as many co-resident blocks as
+// give every warp a position, at most 32 positions per warp.
+template <typename VT, typename XT>
+bool warp_shape(pcdm_handle h, int64_t tau, FusedShape *sh, int want_threads)
+{
+    const int threads = want_threads > 0 ? want_threads : kWarpMaxBlock;
+    if (threads % 32 != 0 || threads > kWarpMaxBlock) return false;
+    const int wpb = threads / 32;
+    const int cap = Kernels<VT, XT>::warp_max_blocks(threads);
+    if (cap <= 0) return false;
+    int64_t blocks = (tau + wpb - 1) / wpb;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (tau > 32 * int64_t(wpb) * blocks) return false;
+    sh->W = 32;
+    sh->blocks = int(blocks);
+    sh->threads = threads;
+    return true;
+}
+
 // The per-column heads of the pipelined kernels, built on their first use.
 template <typename VT, typename XT>
 pcdm_status ensure_heads(pcdm_handle h, IterArgs<VT, XT> &a)
@@ -325,9 +346,11 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
     } else if (h->opts.fused && h->tune_kernel != 2) {
         FusedShape sh;
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
-        // the streaming kernel (kernel 4): by the tuning only
+        // the streaming (4) and warp-cooperative (5) kernels: by the tuning only
+        const bool warp = h->tune_kernel == 5 && warp_shape<VT, XT>(h, tau, &sh, h->tune_threads);
         const bool stream = h->tune_kernel == 4 && stream_shape<VT, XT>(h, tau, &sh, h->tune_threads);
-        const bool pipe = (stream || h->tune_kernel == 1 || h->tune_kernel == 3 || h->tune_kernel == 4)
+        const bool pipe = (warp || stream || h->tune_kernel == 1 || h->tune_kernel == 3 || h->tune_kernel == 4 ||
+                           h->tune_kernel == 5)
                               ? false
                               : pipe_shape<VT, XT>(h, tau, &sh, h->tune_kernel == 0 ? h->tune_threads : 0);
         // rounds: when chosen (pcdm_autotune / pcdm_set_tuning); on the workloads measured so far
@@ -349,7 +372,19 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
             pcdm_status hs = ensure_heads<VT, XT>(h, a);
             if (hs != PCDM_OK) return hs;
         }
-        if (stream) {
+        if (warp) {
+            const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
+            if (!h->g2) {
+                CK(h, cudaStreamSynchronize(h->stream));
+                CK(h, halloc_bytes(h, &h->g2, int64_t(gbytes)));
+                a.g2 = static_cast<XT *>(h->g2);
+                h->g2_valid = false;
+            }
+            if (!h->g2_valid) CK(h, cudaMemcpyAsync(h->g2, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
+            // the FP32 zero-step certificate (FP64 form of LASSO) unless the tuning turns it off
+            CK(h, Kernels<VT, XT>::fused_warp(a, sh, h->k, iters, h->tune_zc != 0, h->stream));
+            h->g2_valid = true;
+        } else if (stream) {
             const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
             if (!h->g2) {
                 CK(h, cudaStreamSynchronize(h->stream));
@@ -1521,9 +1556,10 @@ pcdm_status pcdm_set_tuning(pcdm_handle h, const pcdm_tuning *t)
         return set_err(h, PCDM_EINVAL, "the SVM dual and logistic regression run in kernels 0, 1 and 2");
     const bool lanes_ok = t->lanes_per_col == 1 || t->lanes_per_col == 2 || t->lanes_per_col == 4 ||
                           t->lanes_per_col == 8 || t->lanes_per_col == 16 || t->lanes_per_col == 32;
-    if (t->kernel < 0 || t->kernel > 4 || !lanes_ok)
-        return set_err(h, PCDM_EINVAL, "kernel must be 0..4 and lanes_per_col a power of two up to 32");
+    if (t->kernel < 0 || t->kernel > 5 || !lanes_ok)
+        return set_err(h, PCDM_EINVAL, "kernel must be 0..5 and lanes_per_col a power of two up to 32");
     if (((t->kernel == 0 || t->kernel == 4) && (t->threads_per_block < 32 || t->threads_per_block > kPipeMaxBlock)) ||
+        (t->kernel == 5 && (t->threads_per_block < 32 || t->threads_per_block > kWarpMaxBlock)) ||
         (t->kernel == 3 && (t->threads_per_block < 32 || t->threads_per_block > kPipeRoundsMaxBlock)) ||
         t->threads_per_block % 32 != 0)
         return set_err(h, PCDM_EINVAL, "threads_per_block must be a multiple of 32 within the kernel's limit");
@@ -1583,6 +1619,7 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
     for (int W : {1, 4, 16}) cands.push_back({2, W, 0, 1, -1});
     for (int t : {128, 256}) cands.push_back({3, 1, t, 1, -1});
     for (int t : {128, 256, 448}) cands.push_back({4, 1, t, 1, -1});
+    for (int t : {128, 256, 512}) cands.push_back({5, 1, t, 1, -1});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
@@ -1613,6 +1650,18 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
                 using VT = std::remove_pointer_t<decltype(vt)>;
                 using XT = std::remove_pointer_t<decltype(xt)>;
                 ok = stream_shape<VT, XT>(h, tau, &sh, c.threads);
+                return PCDM_OK;
+            });
+            if (!ok) continue;
+        }
+        if (c.kernel == 5) {
+            // the warp-cooperative kernel must hold tau positions at this block size
+            FusedShape sh;
+            bool ok = false;
+            dispatch(h, [&](auto *vt, auto *xt) {
+                using VT = std::remove_pointer_t<decltype(vt)>;
+                using XT = std::remove_pointer_t<decltype(xt)>;
+                ok = warp_shape<VT, XT>(h, tau, &sh, c.threads);
                 return PCDM_OK;
             });
             if (!ok) continue;
@@ -1674,7 +1723,8 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
         best->lanes_per_col = bestc.W;
         best->threads_per_block = bestc.threads;
         best->heads = bestc.heads && !h->head_off ? 1 : 0;
-        best->zero_cert = bestc.kernel == 0 && zc_choice ? bestc.zc : 0;
+        // the warp-cooperative kernel runs with the certificate (tune_zc -1) wherever it applies
+        best->zero_cert = !zc_choice ? 0 : bestc.kernel == 0 ? bestc.zc : bestc.kernel == 5 ? 1 : 0;
         best->us_per_iteration = best_us;
     }
     return PCDM_OK;

@@ -98,9 +98,9 @@ struct pcdm_ctx {
     uint64_t async_u = 0;           // next update number of the asynchronous mode
     // iteration kernel chosen by pcdm_autotune (-1: the built-in rule)
     int tune_kernel = -1;           // 0 pipelined, 1 fused with tune_W lanes, 2 two-kernel form, 3 pipelined rounds,
-                                    // 4 streaming
+                                    // 4 streaming, 5 warp-cooperative
     int tune_W = 0;
-    int tune_threads = 0;           // block size of the pipelined kernel (0: built-in rule)
+    int tune_threads = 0;           // block size of the pipelined, streaming, warp kernels (0: built-in rule)
     int tune_heads = 1;             // pipelined kernels read the column heads (when they fit)
     int tune_zc = -1;               // FP32 certificate of zero steps in the FP64 pipelined kernel (-1: built-in rule)
     bool head_off = false;          // the column heads did not fit in device memory

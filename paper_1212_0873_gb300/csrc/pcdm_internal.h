@@ -31,6 +31,18 @@ constexpr int kPipeMaxBlock = 448;   // block limit of the pipelined kernel (its
 constexpr int kPipeRoundsMaxBlock = 256;   // block limit of the pipelined rounds kernel (up to 255 registers)
 constexpr int64_t kSlack = 1024;     // trailing entries of prow / pval
 constexpr int kLaneRun = 16;         // entries a lane reads per chunk (16-byte vector loads)
+// The warp-cooperative kernel (warp_kernels.cuh): the first warp_rounds<XT>()
+// runs of 64 entries of a column are held in registers (longer columns loop
+// over the rest: 256 entries with an FP32 residual, 192 with FP64, whose
+// registers run out first); columns are prefetched into L2 kWarpAhead
+// positions ahead of their loads; blocks of up to kWarpMaxBlock threads.
+template <typename XT>
+__host__ __device__ constexpr int warp_rounds()
+{
+    return sizeof(XT) == 8 ? 2 : 3;
+}
+constexpr int kWarpAhead = 4;
+constexpr int kWarpMaxBlock = 512;
 
 template <typename XT>
 struct ColDesc;
@@ -131,6 +143,11 @@ struct Kernels {
     static cudaError_t fused_stream(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
                                     cudaStream_t st);
     static int stream_max_blocks(int threads);
+    // Warp-cooperative persistent kernel for long columns (a warp shares each of its
+    // columns, at most 32 positions per warp: tau <= 32 * warps of the grid; warp_kernels.cuh).
+    static cudaError_t fused_warp(const IterArgs<VT, XT> &a, const FusedShape &sh, int64_t k0, int64_t iters,
+                                  bool zero_cert, cudaStream_t st);
+    static int warp_max_blocks(int threads);
     // Asynchronous updates u0 .. u0+count-1 (no barrier; atomics on x and g).
     static cudaError_t async(const IterArgs<VT, XT> &a, int blocks, uint64_t nthreads, uint64_t u0, uint64_t count,
                              cudaStream_t st);

@@ -1746,3 +1746,4 @@ cudaError_t Kernels<VT, XT>::gap_cols(const ColDesc<XT> *desc, const int32_t *pr
 }  // namespace pcdm
 
 #include "stream_kernels.cuh"
+#include "warp_kernels.cuh"

@@ -132,7 +132,7 @@ class Lasso:
 
     def set_tuning(self, kernel=None, lanes_per_col=1, threads_per_block=0, heads=1, zero_cert=-1):
         """Choose the iteration kernel (0 pipelined, 1 fused, 2 two-kernel, 3 pipelined
-        rounds) by hand, whether the pipelined kernels read the column heads, and
+        rounds, 4 streaming, 5 warp-cooperative) by hand, whether the pipelined kernels read the column heads, and
         whether the FP64 pipelined kernel certifies zero steps in FP32 first (-1: the
         built-in rule); None returns to the built-in rule."""
         B.pcdm_set_tuning(self._h, kernel, lanes_per_col, threads_per_block, heads, zero_cert)

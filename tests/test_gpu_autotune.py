@@ -34,7 +34,7 @@ def test_autotune_keeps_state_and_parity(val_dtype, tol):
         ref.run(512, 7, 3)
         x_before, g_before, st_before = s.x(), s.residual(), s.stats()
         best = s.autotune(512, trial_iters=10)
-        assert best["kernel"] in (0, 1, 2, 3) and best["us_per_iteration"] > 0
+        assert best["kernel"] in (0, 1, 2, 3, 4, 5) and best["us_per_iteration"] > 0
         assert best["heads"] in (0, 1)
         assert best["zero_cert"] in (0, 1) and (val_dtype == "f64" or best["zero_cert"] == 0)
         assert best["lanes_per_col"] in (1, 2, 4, 8, 16, 32)

@@ -52,7 +52,7 @@ def _gpu_residual_as_oracle(inst, g):
 
 
 # (kernel, lanes per column, threads per block, heads)
-CHOICES = [(0, 1, 64, 1), (0, 1, 160, 0), (1, 1, 0, 1), (1, 8, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1), (2, 4, 0, 1), (4, 1, 64, 1)]
+CHOICES = [(0, 1, 64, 1), (0, 1, 160, 0), (1, 1, 0, 1), (1, 8, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1), (2, 4, 0, 1), (4, 1, 64, 1), (5, 1, 64, 1)]
 
 
 @pytest.mark.parametrize("problem", sorted(PROBLEMS))

@@ -1,8 +1,9 @@
 """Every iteration kernel (pipelined, fused with several lane widths, two-kernel,
-pipelined rounds, streaming; the pipelined ones with and without the column heads, the
-pipelined one also with and without the FP32 certificate of zero steps)
-selected by hand through pcdm_set_tuning follows the oracle;
-the rounds kernel also with several positions per thread (tau beyond the grid)."""
+pipelined rounds, streaming, warp-cooperative; the pipelined ones with and without the
+column heads, the pipelined one also with and without the FP32 certificate of zero
+steps) selected by hand through pcdm_set_tuning follows the oracle; the rounds kernel
+also with several positions per thread (tau beyond the grid), the warp-cooperative one
+also with many positions per warp, empty columns and columns of several items."""
 import numpy as np
 import pytest
 
@@ -29,7 +30,7 @@ def _rel(a, b):
 # (kernel, lanes per column, threads per block, column heads[, zero-step certificate])
 CHOICES = [(0, 1, 64, 1), (0, 1, 448, 1), (0, 1, 128, 0), (0, 1, 64, 1, 1), (0, 1, 128, 0, 1), (0, 1, 448, 1, 0),
            (1, 1, 0, 1), (1, 4, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1), (2, 16, 0, 1), (3, 1, 128, 1), (3, 1, 256, 0),
-           (4, 1, 64, 1), (4, 1, 448, 1)]
+           (4, 1, 64, 1), (4, 1, 448, 1), (5, 1, 32, 1), (5, 1, 512, 1), (5, 1, 128, 1, 0)]
 
 
 @pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])
@@ -88,6 +89,55 @@ def test_streaming_kernel_on_long_and_short_columns(val_dtype, tol, per_col, thr
             assert _rel(s.residual(), ref.g) <= tol, upto
         ok, it, rel = s.solve(tau, 6, 1e-8 if val_dtype == "f64" else 1e-6, 100_000)
         assert ok
+
+
+@pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])
+@pytest.mark.parametrize("per_col,threads", [(600, 512), (150, 128), (37, 32), (1, 64)])
+def test_warp_kernel_on_long_and_short_columns(val_dtype, tol, per_col, threads):
+    # the warp-cooperative kernel copies runs of up to 256 entries: 600 entries are three
+    # items (the last one ragged), 150 and 37 one, 1 a single padded entry; ragged tau
+    # (m grows with the column length: the generator draws each column's distinct rows)
+    m = 400_000 if per_col > 200 else 20_000
+    inst = instances.per_col_instance(m, 4_000, per_col, nnz_star=200, val_dtype=val_dtype, seed=1021)
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    tau = min(2048 + 5, inst.n)
+    refresh = 0 if val_dtype == "f64" else 16
+    with Lasso.from_instance(inst, refresh_every=refresh) as s:
+        s.set_tuning(5, 1, threads, 1)
+        for upto in (1, 3, 30):
+            s.step(tau, upto - s.iteration, 6)
+            ref.run(tau, upto - ref.k, 6, refresh_every=refresh)
+            assert _rel(s.x(), ref.x) <= tol, upto
+            assert _rel(s.residual(), ref.g) <= tol, upto
+        ok, it, rel = s.solve(tau, 6, 1e-8 if val_dtype == "f64" else 1e-6, 100_000)
+        assert ok
+
+
+def _warps_of_grid(threads):
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count * (threads // 32)
+
+
+@pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("bf16", 1e-5)])
+def test_warp_kernel_with_many_positions_per_warp(val_dtype, tol):
+    # about 28 positions per warp (blocks of 512 threads, one per SM): several groups of
+    # eight columns per warp reduction, the last one ragged; about a quarter of the
+    # columns empty (Poisson column counts of mean 1.5)
+    warps = _warps_of_grid(512)
+    n = 30 * warps
+    inst = instances.row_omega_instance(n // 2, n, 3, density=0.01, val_dtype=val_dtype, seed=1051)
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    assert np.sum(np.diff(inst.col_ptr) == 0) > n // 8
+    tau = 28 * warps + 7
+    with Lasso.from_instance(inst) as s:
+        s.set_tuning(5, 1, 512, 1)
+        for upto in (1, 2, 7):
+            s.step(tau, upto - s.iteration, 9)
+            ref.run_threads(tau, upto - ref.k, 9, 8)
+            assert _rel(s.x(), ref.x) <= tol, upto
+            assert _rel(s.residual(), ref.g) <= tol, upto
 
 
 def _cu_limit_persisting_l2():
@@ -167,7 +217,8 @@ def omega128_inst():
     return instances.row_omega_instance(200_000, 200_000, 128, density=0.01, val_dtype="f64", seed=1031)
 
 
-@pytest.mark.parametrize("choice", [(1, 2, 0, 1), (2, 4, 0, 1), (4, 1, 448, 1), (0, 1, 448, 1)])
+@pytest.mark.parametrize("choice", [(1, 2, 0, 1), (2, 4, 0, 1), (4, 1, 448, 1), (0, 1, 448, 1), (5, 1, 512, 1),
+                                    (5, 1, 256, 1, 0)])
 def test_omega128_rows_follow_the_oracle(omega128_inst, choice):
     inst = omega128_inst
     A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)

@@ -1,9 +1,9 @@
 """The zero-step shortcuts of the iteration kernels change no result.
 
 At x_i = 0 the LASSO step is zero exactly when |grad_i| <= lambda.  The
-pipelined kernel can decide that in FP32 before any FP64 work (FP64 form: a sum
-over FP32 images of the operands with an error bound); both it and the
-lanes-per-column kernel test the finished gradient exactly (FP32 and BF16 forms:
+pipelined and warp-cooperative kernels can decide that in FP32 before any FP64
+work (FP64 form: a sum over FP32 images of the operands with an error bound);
+they and the lanes-per-column kernel test the finished gradient exactly (FP32 and BF16 forms:
 the FP32 gradient against lambda rounded down; FP64 form: the bit patterns
 compared as integers) and run no FP64 instruction for a lane that passes.  A
 wrong certificate zeroes a step that should be nonzero, so these instances put
@@ -82,8 +82,10 @@ def _rel(a, b):
 SCALES = [(1.0, 1.0), (2.0 ** -100, 2.0 ** 100), (2.0 ** -130, 2.0 ** 20), (1.0, 2.0 ** 130), (2.0 ** -70, 2.0 ** -70)]
 # (kernel, lanes per column, threads per block, column heads, zero-step certificate):
 # the pipelined kernel with the FP32 certificate, without it (the exact test on the
-# FP64 sum alone), and the lanes-per-column kernel with 1 and 4 lanes
-CHOICES = [(0, 1, 448, 1, 1), (0, 1, 64, 0, 1), (0, 1, 448, 1, 0), (1, 1, 0, 1, -1), (1, 4, 0, 1, -1)]
+# FP64 sum alone), the lanes-per-column kernel with 1 and 4 lanes, and the
+# warp-cooperative kernel with its certificate (the built-in rule) and without it
+CHOICES = [(0, 1, 448, 1, 1), (0, 1, 64, 0, 1), (0, 1, 448, 1, 0), (1, 1, 0, 1, -1), (1, 4, 0, 1, -1),
+           (5, 1, 128, 1, -1), (5, 1, 32, 1, 0)]
 
 
 @pytest.mark.parametrize("choice", CHOICES)

@@ -1,8 +1,9 @@
 """The error bound of the FP32 zero-step certificate, restated exactly on the CPU.
 
-The pipelined kernel's FP64 form may decide a LASSO step at x_i = 0 without
-FP64 work: it sums FP32 images of the operands (made from their high words
-with integer operations) and certifies |a_i^T g| <= lambda when
+The FP64 forms of the pipelined and warp-cooperative kernels may decide a
+LASSO step at x_i = 0 without FP64 work: they sum FP32 images of the operands
+(made from their high words with integer operations) and certify
+|a_i^T g| <= lambda when
 
     |acc32| + (c + 40) 2^-24 sabs32 + c 2^-123 mx + 2^-120  <=  lambda rounded down to FP32,
 
@@ -11,8 +12,10 @@ mx: the largest image magnitude; c <= 1024 products).  This test restates that
 arithmetic with exact rationals and correctly rounded FP32 operations, and
 checks on random and adversarial columns that a certificate is only ever
 issued when the FP64 sum the kernel would otherwise compute (in any order, with
-or without FMA) is at most lambda in magnitude: the only property the kernel
-relies on.  The GPU side of the same claim is tests/test_gpu_zero_cert.py.
+or without FMA) is at most lambda in magnitude: the only property the kernels
+rely on.  The warp-cooperative kernel sums in another order (per lane, then a
+five-level tree) and takes the bound with c + 5 for c: certify_warp restates
+it.  The GPU side of the same claim is tests/test_gpu_zero_cert.py.
 """
 import math
 import struct
@@ -175,3 +178,71 @@ def test_images_and_rounding_helpers():
     for x in rng.standard_normal(200) * 10.0 ** rng.integers(-30, 30, 200):
         assert round_f32(Fraction(float(x))) == float(np.float32(x))
     assert round_f32(Fraction(1) + Fraction(1, 2 ** 30), up=True) == float(np.nextafter(np.float32(1), np.float32(2)))
+
+
+def certify_warp(v, g, lam):
+    """The warp-cooperative kernel's certificate: lane l sums the products of
+    entries 64r + 2l and 64r + 2l + 1 (r = 0, 1, ...) with FP32 FMAs in that
+    order, the 32 lane sums are added by the five levels of the warp reduction
+    (partners at distance 16, 8, 4, 2, 1), the maxima likewise, and the bound
+    is taken with c + 5 in place of c."""
+    c = len(v)
+    if c + 5 > 1024:
+        return False
+    acc, sabs, mx = [0.0] * 32, [0.0] * 32, [0.0] * 32
+    for e in range(c):
+        l = (e % 64) // 2
+        vi, gi = f32_image(hi_word(v[e])), f32_image(hi_word(g[e]))
+        acc[l] = fma32(vi, gi, acc[l])
+        sabs[l] = fma32(abs(vi), abs(gi), sabs[l])
+        mx[l] = max(mx[l], abs(vi), abs(gi))
+    for d in (16, 8, 4, 2, 1):
+        acc = [fma32(1.0, acc[l], acc[l ^ d]) for l in range(32)]
+        sabs = [fma32(1.0, sabs[l], sabs[l ^ d]) for l in range(32)]
+        mx = [max(mx[l], mx[l ^ d]) for l in range(32)]
+    acc, sabs, mx = acc[0], sabs[0], mx[0]
+    if any(math.isnan(t) or math.isinf(t) for t in (acc, sabs, mx)):
+        return False
+    lamf = round_f32(Fraction(lam))
+    if math.isinf(lamf) or Fraction(lamf) > Fraction(lam):
+        lamf = float(np.nextafter(np.float32(lamf), np.float32(0)))
+    cc = c + 5
+    lhs = round_f32(Fraction(abs(acc)) + Fraction(2) ** -120, up=True)
+    lhs = fma32(mx, cc * 2.0 ** -123, lhs, up=True)
+    lhs = fma32(sabs, (cc + 40) * 2.0 ** -24, lhs, up=True)
+    return lhs <= lamf
+
+
+def fp64_warp_sum(v, g):
+    """The FP64 sum the warp-cooperative kernel falls back to: lane l takes the
+    entries l, l + 32, ... with FMAs, then the five-level reduction."""
+    acc = [0.0] * 32
+    for e, (a, b) in enumerate(zip(v, g)):
+        acc[e % 32] = float(Fraction(a) * Fraction(b) + Fraction(acc[e % 32]))
+    for d in (16, 8, 4, 2, 1):
+        acc = [acc[l] + acc[l ^ d] for l in range(32)]
+    return acc[0]
+
+
+@pytest.mark.parametrize("kind", ["normal", "spread", "cancel", "tiny", "huge", "lowbits"])
+def test_warp_order_certificate_only_when_the_fp64_sum_is_within_lambda(kind):
+    # columns up to a few hundred entries: several products per lane, then the tree
+    rng = np.random.default_rng((hash(kind) + 7) % (2 ** 32))
+    issued = 0
+    for trial in range(40):
+        c = int(rng.choice([1, 3, 31, 32, 33, 64, 100, 128, 150, 300]))
+        v, g = _column(rng, c, kind)
+        D = math.fsum(float(Fraction(a) * Fraction(b)) for a, b in zip(v, g))
+        base = abs(D) if D != 0 else 2.0 ** -100
+        for rel in (-2.0 ** -10, -2.0 ** -20, 0.0, 2.0 ** -20, 2.0 ** -10, 1.0):
+            lam = base * (1.0 + rel)
+            if not (lam > 0 and math.isfinite(lam)):
+                continue
+            if certify_warp(v, g, lam):
+                issued += 1
+                for s in list(fp64_sums(v, g)) + [fp64_warp_sum(v, g)]:
+                    assert abs(s) <= lam, (kind, c, rel, s, lam)
+    if kind in ("normal", "lowbits", "spread"):
+        assert issued > 0
+    if kind == "huge":
+        assert issued == 0
