@@ -303,8 +303,21 @@ __global__ void __launch_bounds__(kWarpMaxBlock, 1) k_fused_warp(const IterArgs<
             const int64_t pb = __shfl_sync(FULL, c_d.pbeg, t);
             const int cc = __shfl_sync(FULL, c_d.cnt, t);
             XT p = XT(0);
-            for (int e = lane; e < cc; e += 32)
-                p = fma(XT(ldv(a.pval + pb + e)), ldcg_hint(gk + __ldg(a.prow + pb + e), pl), p);
+            for (int cs = 0; cs < cc; cs += 32 * kWarpBatch) {
+                // a batch of entries: every load, then every gather, then the products
+                int32_t rr[kWarpBatch];
+                XT vv[kWarpBatch], gg[kWarpBatch];
+#pragma unroll
+                for (int q = 0; q < kWarpBatch; ++q) {
+                    const int e = cs + lane + 32 * q;
+                    rr[q] = e < cc ? __ldg(a.prow + pb + e) : 0;
+                    vv[q] = e < cc ? XT(ldv(a.pval + pb + e)) : XT(0);
+                }
+#pragma unroll
+                for (int q = 0; q < kWarpBatch; ++q) gg[q] = cs + lane + 32 * q < cc ? ldcg_hint(gk + rr[q], pl) : XT(0);
+#pragma unroll
+                for (int q = 0; q < kWarpBatch; ++q) p = fma(vv[q], gg[q], p);
+            }
             p = warp_sum(p);
             if (lane == t) grad = p;
         }
@@ -318,7 +331,20 @@ __global__ void __launch_bounds__(kWarpMaxBlock, 1) k_fused_warp(const IterArgs<
             const int64_t pb = __shfl_sync(FULL, d.pbeg, t);
             const int cc = __shfl_sync(FULL, d.cnt, t);
             const XT hh = __shfl_sync(FULL, hv, t);
-            for (int e = lane; e < cc; e += 32) red_add(gdst + __ldg(a.prow + pb + e), XT(ldv(a.pval + pb + e)) * hh, pl);
+            for (int cs = 0; cs < cc; cs += 32 * kWarpBatch) {
+                // a batch of entries: every load, then the atomic adds
+                int32_t rr[kWarpBatch];
+                XT vv[kWarpBatch];
+#pragma unroll
+                for (int q = 0; q < kWarpBatch; ++q) {
+                    const int e = cs + lane + 32 * q;
+                    rr[q] = e < cc ? __ldg(a.prow + pb + e) : 0;
+                    vv[q] = e < cc ? XT(ldv(a.pval + pb + e)) : XT(0);
+                }
+#pragma unroll
+                for (int q = 0; q < kWarpBatch; ++q)
+                    if (cs + lane + 32 * q < cc) red_add(gdst + rr[q], vv[q] * hh, pl);
+            }
         }
     };
 
