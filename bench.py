@@ -824,7 +824,9 @@ def run_omega128(a, steps=3):
                         "to rel. duality gap %g" % (a.n, inst.nnz, a.tau, a.tol),
             "updates_per_s": st["updates"] / (sum(ms) / 1e3), "time_to_gap_s": sum(ms) / len(ms) / 1e3,
             "iterations": its[-1], "us_per_iteration": 1e3 * st["iter_kernel_ms"] / max(st["iterations"], 1),
-            "tuning": tuning, "roofline": {k: roof[k] for k in ("achieved", "peak", "frac", "kernel")},
+            "tuning": tuning,
+            "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                                              "alg_bytes_per_launch", "avg_launch_ms", "traffic_taken_at")},
             "steps": steps, "instance_gen_s": t_gen}
 
 
