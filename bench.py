@@ -169,8 +169,12 @@ def traffic_per_update(a, tuning):
         return None, None
     if any(ent.get("tuning", {}).get(f, 0) != tuning.get(f, 0) for f in ("kernel", "lanes_per_col", "heads")):
         return None, None
-    # the zero-step certificate changes the kernel's loads (taken without it unless recorded)
-    if int(ent.get("tuning", {}).get("zero_cert", 0)) != (1 if tuning.get("zero_cert", 0) == 1 else 0):
+    # the zero-step certificate changes the kernel's loads (taken without it unless recorded; the
+    # warp-cooperative kernel's -1 is its adaptive rule)
+    want = int(tuning.get("zero_cert", 0))
+    if tuning.get("kernel") != 5 and want < 0:
+        want = 0
+    if int(ent.get("tuning", {}).get("zero_cert", 0)) != want:
         return None, None
     return float(ent["dram_bytes_per_update"]), ent["tuning"]
 

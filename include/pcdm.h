@@ -299,7 +299,7 @@ pcdm_status pcdm_solve_async(pcdm_handle h, uint64_t seed, double rel_gap_tol, i
  * current column's products are taken; the partial sums of four (FP64) or eight
  * columns are reduced over the warp together and the owner lanes take their steps
  * side by side (for long columns; the FP64 form of LASSO certifies zero steps in FP32
- * as zero_cert describes, unless zero_cert = 0).
+ * as zero_cert describes).
  * The fastest is kept for later pcdm_step /
  * pcdm_solve calls (for any tau; tune again for a very different one).
  * Needs the tau-nice sampling and opts.fused = 1.
@@ -321,10 +321,14 @@ typedef struct {
                                    at x_i = 0 (the same step the FP64 sum gives: eq. (h(x)) with
                                    x_i = 0 is 0 exactly when |grad_i| <= lambda); a warp whose
                                    lanes are all certified issues no FP64 instruction;
-                                   0 = the FP64 sum for every column; -1 (pcdm_set_tuning only) =
-                                   the built-in rule: for kernel 0 on when nnz <= 8 n, for
-                                   kernel 5 always on (its lanes share a column: the bound
-                                   covers the warp's summation order).  The FP32 and BF16
+                                   0 = the FP64 sum for every column; -1 (pcdm_set_tuning, and
+                                   pcdm_autotune's report for kernel 5) =
+                                   the built-in rule: for kernel 0 on when nnz <= 8 n; for
+                                   kernel 5 (whose bound covers the warp's summation order)
+                                   on while at most a quarter of the sampled coordinates
+                                   move, which pcdm_solve measures between its gap checks
+                                   (off after create and reset, when x = 0; on after
+                                   set_x).  The FP32 and BF16
                                    forms always compare their FP32 gradient with lambda rounded
                                    down, an exact test, and ignore this field. */
     double us_per_iteration;    /* measured */

@@ -381,8 +381,10 @@ pcdm_status run_segment(pcdm_handle h, int64_t tau, uint64_t seed, int64_t iters
                 h->g2_valid = false;
             }
             if (!h->g2_valid) CK(h, cudaMemcpyAsync(h->g2, h->g, gbytes, cudaMemcpyDeviceToDevice, h->stream));
-            // the FP32 zero-step certificate (FP64 form of LASSO) unless the tuning turns it off
-            CK(h, Kernels<VT, XT>::fused_warp(a, sh, h->k, iters, h->tune_zc != 0, h->stream));
+            // the FP32 zero-step certificate (FP64 form of LASSO): by the tuning, else while few
+            // coordinates move (warp_cert)
+            const bool wzc = h->tune_zc == 1 || (h->tune_zc < 0 && h->warp_cert);
+            CK(h, Kernels<VT, XT>::fused_warp(a, sh, h->k, iters, wzc, h->stream));
             h->g2_valid = true;
         } else if (stream) {
             const size_t gbytes = size_t(h->m) * size_t(dtype_bytes(h->xg_dtype));
@@ -537,6 +539,7 @@ pcdm_status reset_state(pcdm_handle h)
     h->st_kernels += 1;   // the g = -b kernel
     h->k = 0;
     h->sample_valid = false;
+    h->warp_cert = false;
     return PCDM_OK;
 }
 
@@ -987,6 +990,17 @@ pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap
     int64_t done = 0;
     s = do_gap(h, rec);
     if (s != PCDM_OK) return s;
+    // the share of moving coordinates over each stretch between checks decides the
+    // warp-cooperative kernel's certificate (counters read after the gap's synchronisation)
+    unsigned long long *hc = reinterpret_cast<unsigned long long *>(h->host_buf + 12);
+    auto moving = [&](unsigned long long *nonzero) -> pcdm_status {
+        CK(h, cudaMemcpyAsync(hc, h->counters, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        *nonzero = hc[2];
+        return PCDM_OK;
+    };
+    unsigned long long nz0 = 0, nz1 = 0;
+    if ((s = moving(&nz0)) != PCDM_OK) return s;
     double rel = rec[2] / (rec[0] > 1e-300 ? rec[0] : 1e-300);
     while (rel > rel_gap_tol && done < max_iters) {
         const int64_t chunk = every < max_iters - done ? every : max_iters - done;
@@ -996,6 +1010,9 @@ pcdm_status pcdm_solve(pcdm_handle h, int64_t tau, uint64_t seed, double rel_gap
         done += chunk;
         s = do_gap(h, rec);
         if (s != PCDM_OK) return s;
+        if ((s = moving(&nz1)) != PCDM_OK) return s;
+        h->warp_cert = 4 * (nz1 - nz0) <= (unsigned long long)(chunk * tau);
+        nz0 = nz1;
         rel = rec[2] / (rec[0] > 1e-300 ? rec[0] : 1e-300);
         if (!fixed) every = pcdm_next_check_interval(epoch, done - chunk, rel_prev, done, rel, rel_gap_tol);
     }
@@ -1022,6 +1039,7 @@ pcdm_status pcdm_set_x(pcdm_handle h, const void *x_in, int32_t on_device)
     if (!x_in) return set_err(h, PCDM_EINVAL, "x_in is NULL");
     CK(h, cudaMemcpyAsync(h->x, x_in, size_t(h->n) * sizeof(double), copy_kind(on_device, 1), h->stream));
     h->sample_valid = false;
+    h->warp_cert = true;   // a warm start: most coordinates are expected to stay
     s = do_refresh(h);
     if (s != PCDM_OK) return s;
     return sync_check(h);
@@ -1723,8 +1741,8 @@ pcdm_status pcdm_autotune(pcdm_handle h, int64_t tau, int64_t trial_iters, pcdm_
         best->lanes_per_col = bestc.W;
         best->threads_per_block = bestc.threads;
         best->heads = bestc.heads && !h->head_off ? 1 : 0;
-        // the warp-cooperative kernel runs with the certificate (tune_zc -1) wherever it applies
-        best->zero_cert = !zc_choice ? 0 : bestc.kernel == 0 ? bestc.zc : bestc.kernel == 5 ? 1 : 0;
+        // the warp-cooperative kernel's certificate follows the share of moving coordinates (tune_zc -1)
+        best->zero_cert = !zc_choice ? 0 : bestc.kernel == 0 ? bestc.zc : bestc.kernel == 5 ? -1 : 0;
         best->us_per_iteration = best_us;
     }
     return PCDM_OK;

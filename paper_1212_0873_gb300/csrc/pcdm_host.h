@@ -103,6 +103,10 @@ struct pcdm_ctx {
     int tune_threads = 0;           // block size of the pipelined, streaming, warp kernels (0: built-in rule)
     int tune_heads = 1;             // pipelined kernels read the column heads (when they fit)
     int tune_zc = -1;               // FP32 certificate of zero steps in the FP64 pipelined kernel (-1: built-in rule)
+    // The warp-cooperative kernel's FP32 certificate under tune_zc = -1: on when the last stretch of a
+    // solve stepped at most a quarter of its sampled coordinates (pcdm_solve measures it between gap
+    // checks); off after create and reset (from x = 0 most coordinates move), on after set_x
+    bool warp_cert = false;
     bool head_off = false;          // the column heads did not fit in device memory
     bool rounds_last = false;       // the last segment ran the pipelined rounds kernel (S_{k} not left drawn)
     bool sample_valid = false;

@@ -36,7 +36,9 @@ def test_autotune_keeps_state_and_parity(val_dtype, tol):
         best = s.autotune(512, trial_iters=10)
         assert best["kernel"] in (0, 1, 2, 3, 4, 5) and best["us_per_iteration"] > 0
         assert best["heads"] in (0, 1)
-        assert best["zero_cert"] in (0, 1) and (val_dtype == "f64" or best["zero_cert"] == 0)
+        # kernel 5 reports -1: its certificate follows the share of moving coordinates
+        assert best["zero_cert"] in ((-1,) if best["kernel"] == 5 and val_dtype == "f64" else (0, 1))
+        assert val_dtype == "f64" or best["zero_cert"] == 0
         assert best["lanes_per_col"] in (1, 2, 4, 8, 16, 32)
         assert np.array_equal(s.x(), x_before) and np.array_equal(s.residual(), g_before)
         assert s.iteration == 7

@@ -30,7 +30,7 @@ def _rel(a, b):
 # (kernel, lanes per column, threads per block, column heads[, zero-step certificate])
 CHOICES = [(0, 1, 64, 1), (0, 1, 448, 1), (0, 1, 128, 0), (0, 1, 64, 1, 1), (0, 1, 128, 0, 1), (0, 1, 448, 1, 0),
            (1, 1, 0, 1), (1, 4, 0, 1), (1, 32, 0, 1), (2, 1, 0, 1), (2, 16, 0, 1), (3, 1, 128, 1), (3, 1, 256, 0),
-           (4, 1, 64, 1), (4, 1, 448, 1), (5, 1, 32, 1), (5, 1, 512, 1), (5, 1, 128, 1, 0)]
+           (4, 1, 64, 1), (4, 1, 448, 1), (5, 1, 32, 1), (5, 1, 512, 1, 1), (5, 1, 128, 1, 0)]
 
 
 @pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])
@@ -119,11 +119,12 @@ def _warps_of_grid(threads):
     return torch.cuda.get_device_properties(0).multi_processor_count * (threads // 32)
 
 
-@pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("bf16", 1e-5)])
-def test_warp_kernel_with_many_positions_per_warp(val_dtype, tol):
+@pytest.mark.parametrize("val_dtype,tol,zc", [("f64", 1e-10, 1), ("f64", 1e-10, 0), ("bf16", 1e-5, -1)])
+def test_warp_kernel_with_many_positions_per_warp(val_dtype, tol, zc):
     # about 28 positions per warp (blocks of 512 threads, one per SM): several groups of
-    # eight columns per warp reduction, the last one ragged; about a quarter of the
-    # columns empty (Poisson column counts of mean 1.5)
+    # four (FP64) or eight columns per warp reduction, the last one ragged; about a
+    # quarter of the columns empty (Poisson column counts of mean 1.5); FP64 with and
+    # without the FP32 certificate
     warps = _warps_of_grid(512)
     n = 30 * warps
     inst = instances.row_omega_instance(n // 2, n, 3, density=0.01, val_dtype=val_dtype, seed=1051)
@@ -132,7 +133,7 @@ def test_warp_kernel_with_many_positions_per_warp(val_dtype, tol):
     assert np.sum(np.diff(inst.col_ptr) == 0) > n // 8
     tau = 28 * warps + 7
     with Lasso.from_instance(inst) as s:
-        s.set_tuning(5, 1, 512, 1)
+        s.set_tuning(5, 1, 512, 1, zc)
         for upto in (1, 2, 7):
             s.step(tau, upto - s.iteration, 9)
             ref.run_threads(tau, upto - ref.k, 9, 8)
@@ -217,7 +218,7 @@ def omega128_inst():
     return instances.row_omega_instance(200_000, 200_000, 128, density=0.01, val_dtype="f64", seed=1031)
 
 
-@pytest.mark.parametrize("choice", [(1, 2, 0, 1), (2, 4, 0, 1), (4, 1, 448, 1), (0, 1, 448, 1), (5, 1, 512, 1),
+@pytest.mark.parametrize("choice", [(1, 2, 0, 1), (2, 4, 0, 1), (4, 1, 448, 1), (0, 1, 448, 1), (5, 1, 512, 1, 1),
                                     (5, 1, 256, 1, 0)])
 def test_omega128_rows_follow_the_oracle(omega128_inst, choice):
     inst = omega128_inst
