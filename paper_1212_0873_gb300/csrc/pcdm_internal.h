@@ -42,7 +42,6 @@ __host__ __device__ constexpr int warp_rounds()
     return sizeof(XT) == 8 ? 2 : 3;
 }
 constexpr int kWarpAhead = 4;
-constexpr int kWarpBatch = 2;   // rounds of 32 entries per batch of the rereading passes (FP64 sums, scatters)
 constexpr int kWarpMaxBlock = 512;
 
 template <typename XT>

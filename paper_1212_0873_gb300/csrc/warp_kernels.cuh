@@ -72,6 +72,20 @@ __device__ __forceinline__ T transposed_sum8(const T (&p)[8], int lane)
     return s;
 }
 
+// The same for two partials: lanes 16c .. 16c+15 return the total of partial c.
+template <typename T>
+__device__ __forceinline__ T transposed_sum2(const T (&p)[2], int lane)
+{
+    const unsigned full = 0xFFFFFFFFu;
+    const bool b4 = (lane & 16) != 0;
+    T s = (b4 ? p[1] : p[0]) + __shfl_xor_sync(full, b4 ? p[0] : p[1], 16);
+    s += __shfl_xor_sync(full, s, 8);
+    s += __shfl_xor_sync(full, s, 4);
+    s += __shfl_xor_sync(full, s, 2);
+    s += __shfl_xor_sync(full, s, 1);
+    return s;
+}
+
 // Transposed reduction of four per-lane values with max (the certificate's
 // largest operand image): lanes 8c .. 8c+7 return the maximum of value c.
 __device__ __forceinline__ float transposed_max4(const float (&p)[4], int lane)
@@ -294,56 +308,105 @@ __global__ void __launch_bounds__(kWarpMaxBlock, 1) k_fused_warp(const IterArgs<
         }
         ++closed;
     };
-    // FP64 gradient of each column in mask m (CERT: the columns the certificate
-    // did not decide), read again from memory; the sum goes to the owner lane.
+    // The rereading passes take QS columns of a lane mask at a time (the q-th
+    // lowest set lane in slot q; an empty slot has no entries), QB runs of 32
+    // entries of each per batch, so that their loads and gathers are in flight
+    // together: two columns with an FP32 residual, one (two runs per batch) in
+    // FP64, whose registers would otherwise spill.
+    constexpr int QS = sizeof(XT) == 8 ? 1 : 2;
+    constexpr int QB = sizeof(XT) == 8 ? 2 : 1;
+    auto take = [&](unsigned &m, const Col<XT> &d, int (&tq)[QS], int64_t (&pbq)[QS], int (&ccq)[QS]) {
+#pragma unroll
+        for (int q = 0; q < QS; ++q) {
+            const bool any = m != 0u;
+            const int t = any ? __ffs(int(m)) - 1 : 0;
+            if (any) m &= m - 1u;
+            tq[q] = any ? t : -1;
+            pbq[q] = __shfl_sync(FULL, d.pbeg, t);
+            const int cc = __shfl_sync(FULL, d.cnt, t);
+            ccq[q] = any ? cc : 0;
+        }
+    };
+    // FP64 gradient of each column in mask m (the columns the certificate did
+    // not decide), read again from memory; the sum goes to the owner lane.
     auto fp64_grads = [&](unsigned m, const XT *gk) {
         while (m) {
-            const int t = __ffs(int(m)) - 1;
-            m &= m - 1u;
-            const int64_t pb = __shfl_sync(FULL, c_d.pbeg, t);
-            const int cc = __shfl_sync(FULL, c_d.cnt, t);
-            XT p = XT(0);
-            for (int cs = 0; cs < cc; cs += 32 * kWarpBatch) {
-                // a batch of entries: every load, then every gather, then the products
-                int32_t rr[kWarpBatch];
-                XT vv[kWarpBatch], gg[kWarpBatch];
+            int tq[QS], ccq[QS];
+            int64_t pbq[QS];
+            take(m, c_d, tq, pbq, ccq);
+            int ccmax = 0;
 #pragma unroll
-                for (int q = 0; q < kWarpBatch; ++q) {
-                    const int e = cs + lane + 32 * q;
-                    rr[q] = e < cc ? __ldg(a.prow + pb + e) : 0;
-                    vv[q] = e < cc ? XT(ldv(a.pval + pb + e)) : XT(0);
-                }
+            for (int q = 0; q < QS; ++q) ccmax = max(ccmax, ccq[q]);
+            XT p[QS];
 #pragma unroll
-                for (int q = 0; q < kWarpBatch; ++q) gg[q] = cs + lane + 32 * q < cc ? ldcg_hint(gk + rr[q], pl) : XT(0);
+            for (int q = 0; q < QS; ++q) p[q] = XT(0);
+            for (int cs = 0; cs < ccmax; cs += 32 * QB) {
+                // a batch: every load, then every gather, then the products
+                int32_t rr[QS][QB];
+                XT vv[QS][QB], gg[QS][QB];
 #pragma unroll
-                for (int q = 0; q < kWarpBatch; ++q) p = fma(vv[q], gg[q], p);
+                for (int q = 0; q < QS; ++q)
+#pragma unroll
+                    for (int b = 0; b < QB; ++b) {
+                        const int e = cs + lane + 32 * b;
+                        rr[q][b] = e < ccq[q] ? __ldg(a.prow + pbq[q] + e) : 0;
+                        vv[q][b] = e < ccq[q] ? XT(ldv(a.pval + pbq[q] + e)) : XT(0);
+                    }
+#pragma unroll
+                for (int q = 0; q < QS; ++q)
+#pragma unroll
+                    for (int b = 0; b < QB; ++b)
+                        gg[q][b] = cs + lane + 32 * b < ccq[q] ? ldcg_hint(gk + rr[q][b], pl) : XT(0);
+#pragma unroll
+                for (int q = 0; q < QS; ++q)
+#pragma unroll
+                    for (int b = 0; b < QB; ++b) p[q] = fma(vv[q][b], gg[q][b], p[q]);
             }
-            p = warp_sum(p);
-            if (lane == t) grad = p;
+            if constexpr (QS == 1) {
+                const XT v = warp_sum(p[0]);
+                if (lane == tq[0]) grad = v;
+            } else {
+                // the two sums over the warp at once: slot q's total in lanes 16q .. 16q+15
+                const XT tot = transposed_sum2(p, lane);
+#pragma unroll
+                for (int q = 0; q < QS; ++q) {
+                    const XT v = __shfl_sync(FULL, tot, 16 * q);
+                    if (lane == tq[q]) grad = v;
+                }
+            }
         }
     };
     // The warp adds A_i h_i of its moving coordinates (d, hv of lane t) into gdst.
     auto scatter_owned = [&](const Col<XT> &d, XT hv, XT *gdst) {
         unsigned m = __ballot_sync(FULL, mine && !is_zero_bits(hv));
         while (m) {
-            const int t = __ffs(int(m)) - 1;
-            m &= m - 1u;
-            const int64_t pb = __shfl_sync(FULL, d.pbeg, t);
-            const int cc = __shfl_sync(FULL, d.cnt, t);
-            const XT hh = __shfl_sync(FULL, hv, t);
-            for (int cs = 0; cs < cc; cs += 32 * kWarpBatch) {
-                // a batch of entries: every load, then the atomic adds
-                int32_t rr[kWarpBatch];
-                XT vv[kWarpBatch];
+            int tq[QS], ccq[QS];
+            int64_t pbq[QS];
+            take(m, d, tq, pbq, ccq);
+            XT hq[QS];
+            int ccmax = 0;
 #pragma unroll
-                for (int q = 0; q < kWarpBatch; ++q) {
-                    const int e = cs + lane + 32 * q;
-                    rr[q] = e < cc ? __ldg(a.prow + pb + e) : 0;
-                    vv[q] = e < cc ? XT(ldv(a.pval + pb + e)) : XT(0);
-                }
+            for (int q = 0; q < QS; ++q) {
+                hq[q] = __shfl_sync(FULL, hv, tq[q] < 0 ? 0 : tq[q]);
+                ccmax = max(ccmax, ccq[q]);
+            }
+            for (int cs = 0; cs < ccmax; cs += 32 * QB) {
+                // a batch: every load, then the atomic adds
+                int32_t rr[QS][QB];
+                XT vv[QS][QB];
 #pragma unroll
-                for (int q = 0; q < kWarpBatch; ++q)
-                    if (cs + lane + 32 * q < cc) red_add(gdst + rr[q], vv[q] * hh, pl);
+                for (int q = 0; q < QS; ++q)
+#pragma unroll
+                    for (int b = 0; b < QB; ++b) {
+                        const int e = cs + lane + 32 * b;
+                        rr[q][b] = e < ccq[q] ? __ldg(a.prow + pbq[q] + e) : 0;
+                        vv[q][b] = e < ccq[q] ? XT(ldv(a.pval + pbq[q] + e)) : XT(0);
+                    }
+#pragma unroll
+                for (int q = 0; q < QS; ++q)
+#pragma unroll
+                    for (int b = 0; b < QB; ++b)
+                        if (cs + lane + 32 * b < ccq[q]) red_add(gdst + rr[q][b], vv[q][b] * hq[q], pl);
             }
         }
     };
