@@ -692,7 +692,7 @@ def kernel_name(a, tuning):
     if tuning and tuning["kernel"] == 4:
         return "k_fused_stream (persistent PCDM1 iterations, columns streamed by TMA)"
     if tuning and tuning["kernel"] == 5:
-        return "k_fused_warp (persistent PCDM1 iterations, a warp per column, columns streamed by TMA)"
+        return "k_fused_warp (persistent PCDM1 iterations, a warp per column)"
     return "k_fused_pipe (persistent PCDM1 iterations)"
 
 
