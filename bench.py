@@ -79,6 +79,7 @@ def parse():
     p.add_argument("--no-gather-ceiling", action="store_true",
                    help="skip the random-gather ceiling measured beside the roofline")
     p.add_argument("--sweep", action="store_true", help="print the omega x tau x dtype table of the scale workload")
+    p.add_argument("--sweep-omega", default="2,16,128", help="the omega values of --sweep (comma-separated)")
     p.add_argument("--huge", action="store_true", help="time the 4e9-nonzero configuration (about 140 GB of HBM)")
     p.add_argument("--huge-m", type=int, default=1_000_000_000, help="rows of the huge configuration (scaled runs)")
     p.add_argument("--huge-n", type=int, default=500_000_000, help="columns of the huge configuration")
@@ -1100,7 +1101,7 @@ def run_sweep(a):
     import torch
     from paper_1212_0873_gb300 import Lasso, instances
     torch.cuda.set_device(0)
-    for omega in (2, 16, 128):
+    for omega in [int(v) for v in a.sweep_omega.split(",")]:
         for dtype in ("f64", "f32"):
             inst = instances.row_omega_instance(a.n, a.n, omega, density=0.01, noise=0.01, lam_frac=0.05,
                                                 val_dtype=dtype, seed=1002)
