@@ -987,6 +987,349 @@ __device__ __forceinline__ void mem_scatter(const IterArgs<VT, XT> &a, const Col
     }
 }
 
+// Shared-memory slot of one thread of the pipelined kernel: the column's first
+// kE row indices and values (the head's layout), then its next kE/2 row indices
+// and values, padded to an odd number of 16-byte words (with it, the 128-bit
+// loads of 8 consecutive threads hit distinct banks).
+template <typename VT>
+__host__ __device__ constexpr int pipe_tail_off()
+{
+    return 64 + kLaneRun * int(sizeof(VT));   // the tail's row indices; its values 2 kLaneRun bytes on
+}
+template <typename VT>
+__host__ __device__ constexpr int pipe_slot_raw()
+{
+    return pipe_tail_off<VT>() + 2 * kLaneRun + (kLaneRun / 2) * int(sizeof(VT));
+}
+template <typename VT>
+__host__ __device__ constexpr int pipe_slot_bytes1()
+{
+    return (pipe_slot_raw<VT>() / 16) % 2 == 0 ? pipe_slot_raw<VT>() + 16 : pipe_slot_raw<VT>();
+}
+template <typename VT>
+__host__ __device__ constexpr size_t pipe_smem_bytes1(int threads)
+{
+    return size_t(threads) * size_t(pipe_slot_bytes1<VT>()) + 16;
+}
+
+// Row indices and values of a slot: the first kE entries, then the next kE/2.
+template <typename VT, typename XT>
+__device__ __forceinline__ void slot_rows(const unsigned char *slot, int32_t (&row)[kE], int32_t (&tr)[kE / 2])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 r4 = reinterpret_cast<const uint4 *>(slot)[q];
+        row[4 * q + 0] = int32_t(r4.x);
+        row[4 * q + 1] = int32_t(r4.y);
+        row[4 * q + 2] = int32_t(r4.z);
+        row[4 * q + 3] = int32_t(r4.w);
+    }
+#pragma unroll
+    for (int q = 0; q < kE / 8; ++q) {
+        const uint4 r4 = reinterpret_cast<const uint4 *>(slot + pipe_tail_off<VT>())[q];
+        tr[4 * q + 0] = int32_t(r4.x);
+        tr[4 * q + 1] = int32_t(r4.y);
+        tr[4 * q + 2] = int32_t(r4.z);
+        tr[4 * q + 3] = int32_t(r4.w);
+    }
+}
+
+// Scatter of one column whose first kE + kE/2 entries sit in a slot (the rest
+// from memory) into g: g_r += a_ri * h.
+template <typename VT, typename XT>
+__device__ __forceinline__ void slot_scatter1(const IterArgs<VT, XT> &a, const unsigned char *slot, const Col<XT> &d,
+                                              XT h, XT *g, uint64_t pf, uint64_t pl)
+{
+    constexpr int VW = pipe_value_words<VT>();
+    constexpr int VWT = VW / 2;
+    constexpr int EPW = 16 / int(sizeof(VT));
+    constexpr int kT = kE / 2;
+    int32_t row[kE], tr[kT];
+    slot_rows<VT, XT>(slot, row, tr);
+#pragma unroll
+    for (int w = 0; w < VW; ++w) {
+        XT vw[EPW];
+        decode_word<VT, XT>(reinterpret_cast<const uint4 *>(slot + 64)[w], vw);
+#pragma unroll
+        for (int o = 0; o < EPW; ++o)
+            if (w * EPW + o < d.cnt) red_add(g + row[w * EPW + o], vw[o] * h, pl);
+    }
+    if (d.cnt > kE) {
+#pragma unroll
+        for (int w = 0; w < VWT; ++w) {
+            XT vw[EPW];
+            decode_word<VT, XT>(reinterpret_cast<const uint4 *>(slot + pipe_tail_off<VT>() + 4 * kT)[w], vw);
+#pragma unroll
+            for (int o = 0; o < EPW; ++o)
+                if (kE + w * EPW + o < d.cnt) red_add(g + tr[w * EPW + o], vw[o] * h, pl);
+        }
+    }
+    for (int cs = kE + kT; cs < d.cnt; cs += kE) {
+        Chunk<kE, XT> t;
+        ld_chunk_hint<kE>(t, a.prow, a.pval, d.pbeg + cs, pf);
+        chunk_scatter_hint<kE>(t, g, h, d.cnt - cs, pl);
+    }
+}
+
+// The pipelined kernel's FP64 form ("wide" slots): one slot per thread holds the
+// column's first kE + kE/2 entries (the head by one bulk copy, the next kE/2 by
+// two more for a longer column), so the gathers of entries kE .. kE + kE/2 - 1
+// need no dependent load; the slot is refilled after the grid barrier's arrive
+// (its scatter done), and the previous iteration's step is scattered from
+// memory.  In FP64, whose phase before the scatter is the longest, this cut the
+// iteration at the bench workload from 18.6 to 17.0 us; the FP32 and BF16 forms,
+// where the block's wait for every thread's copies then costs more than the tail
+// loads did, keep the double-buffered kernel above.
+template <typename VT, typename XT, int GM = 0, bool ZC = false>
+__global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe_wide(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int VW = pipe_value_words<VT>();
+    constexpr int VWT = VW / 2;
+    constexpr int SB = pipe_slot_bytes1<VT>();
+    constexpr int TO = pipe_tail_off<VT>();
+    constexpr int G = pad_granule<VT>();
+    constexpr int kT = kE / 2;   // entries [kE, kE + kT) sit in the slot as well
+    const int nt = blockDim.x, t = threadIdx.x;
+    // Sampled position j belongs to block j mod gridDim.x, thread j / gridDim.x:
+    // with one block per SM the positions spread over every SM even when tau
+    // does not fill the last block.
+    const int64_t j0 = int64_t(t) * gridDim.x + blockIdx.x;
+    const bool own = j0 < a.tau;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + size_t(nt) * SB);
+    Counters cnt;
+    const uint64_t pf = l2_evict_first();   // A, descriptors, x: touched once per iteration
+    const uint64_t pl = l2_evict_last();    // the residual buffers: gathered at random rows
+    const float lamf = __double2float_rd(a.lambda);   // the largest float <= lambda (ZeroCert)
+    constexpr bool CERT = sizeof(XT) == 8 && GM == 0 && ZC;   // the FP64 form tries the FP32 certificate
+    unsigned char *my = smem + size_t(t) * SB;
+    // the residual buffer that holds g_k at iteration k
+    auto gbuf = [&](int64_t kk) { return (kk & 1) ? a.g2 : a.g; };
+    // This thread's share of filling the slots: arrive on the mbarrier and, for a
+    // non-empty column, bulk-copy its first kE entries (one copy from the column's
+    // head when the heads exist, else rows and values) and, for a longer column,
+    // its next kE/2 entries (rows and values).
+    auto fill = [&](const Col<XT> &d, int32_t ci, bool mine) {
+        if (mine && d.cnt > 0) {
+            const int64_t pc = (int64_t(d.cnt) + G - 1) / G * G;
+            const uint32_t e = uint32_t(pc < kE ? pc : kE);
+            const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
+            const uint32_t e2 = pc > kE ? uint32_t(pc - kE < kT ? pc - kE : kT) : 0u;
+            const uint32_t br2 = e2 * 4u, bv2 = e2 * uint32_t(sizeof(VT));
+            mbar_arrive_expect_tx(mbar, (a.head ? 64u + bv : br + bv) + br2 + bv2);
+            if (a.head) {
+                bulk_copy_g2s(my, a.head + int64_t(ci) * head_stride<VT>(), 64u + bv, mbar, pf);
+            } else {
+                bulk_copy_g2s(my, a.prow + d.pbeg, br, mbar, pf);
+                bulk_copy_g2s(my + 64, a.pval + d.pbeg, bv, mbar, pf);
+            }
+            if (e2 > 0) {
+                bulk_copy_g2s(my + TO, a.prow + d.pbeg + kE, br2, mbar, pf);
+                bulk_copy_g2s(my + TO + 4 * kT, a.pval + d.pbeg + kE, bv2, mbar, pf);
+            }
+        } else {
+            mbar_arrive(mbar);
+        }
+    };
+    // The slots of iteration it are the mbarrier's it-th completion.
+    auto wait_buf = [&](int64_t it) { return mbar_wait_bounded(mbar, uint32_t(it) & 1u, a.status, a.timeout_ns); };
+
+    if (t == 0) {
+        mbar_init(mbar, uint32_t(nt));
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+
+    // Prologue: i_{k0} (drawn by the caller) and its entries; i_{k0+1} and its descriptor.
+    int32_t i_cur = 0, i_nxt = 0;
+    Col<XT> d_cur, d_nxt, d_prev;
+    d_cur.pbeg = d_nxt.pbeg = d_prev.pbeg = 0;
+    d_cur.cnt = d_nxt.cnt = d_prev.cnt = 0;
+    d_cur.invL = d_nxt.invL = d_prev.invL = XT(0);
+    XT h_prev = XT(0);   // the step of the previous iteration's column (still owed to one buffer)
+    if (own) {
+        i_cur = ldcg(sample_buf(a, k0) + j0);
+        d_cur = load_col(a.desc, i_cur, pf);
+        i_nxt = sample_index(uint32_t(j0), make_sample_key(a.seed, k0 + 1, a.n));
+        d_nxt = load_col(a.desc, i_nxt, pf);
+    }
+    fill(d_cur, i_cur, own);
+
+    constexpr int EPW = 16 / int(sizeof(VT));
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t k = k0 + it;
+        // this iteration's entries (filled during the previous iteration)
+        if (!wait_buf(it)) return;
+        const XT *gk = gbuf(k);
+        XT *gn = gbuf(k + 1);
+
+        // ---------------- gather, step, x update (reads g_k)
+        // The loads go first (x_i, the gathers of g at the slot's rows); the
+        // sample of k+2 (integer work only) is drawn while they are in flight.
+        XT h = XT(0);
+        double xi = 0.0;
+        int32_t i_nn = 0;
+        Col<XT> d_nn = d_nxt;
+        const int valid = own ? d_cur.cnt : 0;
+        if (own) {
+            xi = ldcg_hint(a.x + i_cur, pf);
+            int32_t row[kE], tr[kT];
+            slot_rows<VT, XT>(my, row, tr);
+            // the step from the gradient (FP64), x_i and the counters
+            auto take_step = [&](XT grad) {
+                const double xn =
+                    coord_step(a.problem, xi, double(grad), double(d_cur.invL), a.inv_beta, a.lambda, a.kappa);
+                const double h64 = xn - xi;
+                h = XT(h64);
+                if (h64 != 0.0) {   // most steps are zero: x_i unchanged
+                    st_hint(a.x + i_cur, xn, pf);
+                    cnt.nonzero += 1;
+                    cnt.scattered += (unsigned long long)valid;
+                }
+            };
+            // the products of the slot's entries with gathered values gv (first chunk) and gt (next kT)
+            auto slot_dot = [&](const XT (&gv)[kE], const XT (&gt)[kT]) {
+                XT acc = XT(0);
+#pragma unroll
+                for (int w = 0; w < VW; ++w) {
+                    XT vw[EPW];
+                    decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
+#pragma unroll
+                    for (int q = 0; q < EPW; ++q)
+                        if (w * EPW + q < valid) acc = fma(vw[q], grad_map<GM>(gv[w * EPW + q]), acc);
+                }
+                if (valid > kE) {
+#pragma unroll
+                    for (int w = 0; w < VWT; ++w) {
+                        XT vw[EPW];
+                        decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + TO + 4 * kT)[w], vw);
+#pragma unroll
+                        for (int q = 0; q < EPW; ++q)
+                            if (kE + w * EPW + q < valid) acc = fma(vw[q], grad_map<GM>(gt[w * EPW + q]), acc);
+                    }
+                }
+                return acc;
+            };
+            if constexpr (CERT) {
+                // FP64 form with the FP32 certificate of a zero LASSO step (ZeroCert):
+                // the slot's gathers stay in registers as FP64; entries past the slot
+                // bring only the high words of g.  A lane the certificate does not
+                // cover reads those entries again, from L2.
+                XT gv[kE], gt[kT];
+#pragma unroll
+                for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
+#pragma unroll
+                for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg_hint(gk + tr[e], pl) : XT(0);
+                i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
+                d_nn = load_col(a.desc, i_nn, pf);
+                bool zero_step = false;
+                if (a.problem == 0 && is_zero_bits(xi)) {
+                    ZeroCert zc;
+#pragma unroll
+                    for (int w = 0; w < VW; ++w) {
+                        const uint4 u = reinterpret_cast<const uint4 *>(my + 64)[w];
+                        if (2 * w < valid) zc.add(u.y, hi_word(gv[2 * w]));
+                        if (2 * w + 1 < valid) zc.add(u.w, hi_word(gv[2 * w + 1]));
+                    }
+                    if (valid > kE) {
+#pragma unroll
+                        for (int w = 0; w < VWT; ++w) {
+                            const uint4 u = reinterpret_cast<const uint4 *>(my + TO + 4 * kT)[w];
+                            if (kE + 2 * w < valid) zc.add(u.y, hi_word(gt[2 * w]));
+                            if (kE + 2 * w + 1 < valid) zc.add(u.w, hi_word(gt[2 * w + 1]));
+                        }
+                    }
+                    for (int cs = kE + kT; cs < valid; cs += kT) {
+                        Chunk<kT, XT> tc;
+                        ld_chunk_hint<kT>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
+                        uint32_t gc[kT];
+#pragma unroll
+                        for (int e = 0; e < kT; ++e) gc[e] = (cs + e < valid) ? ldcg_hi_hint(gk + tc.row[e], pl) : 0u;
+#pragma unroll
+                        for (int e = 0; e < kT; ++e)
+                            if (cs + e < valid) zc.add(hi_word(tc.val[e]), gc[e]);
+                    }
+                    zero_step = zc.below(valid, lamf);
+                }
+                if (!zero_step) {
+                    // FP64 sum over the whole column: the slot's entries from registers,
+                    // the rest from memory
+                    XT acc = slot_dot(gv, gt);
+                    for (int cs = kE + kT; cs < valid; cs += kE) {
+                        Chunk<kE, XT> tc;
+                        ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
+                        acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
+                    }
+                    // the exact test on the FP64 sum (the bound may not have decided it)
+                    if (!(a.problem == 0 && is_zero_bits(xi) && abs_le_bits(acc, a.lambda))) take_step(acc);
+                }
+            } else {
+                XT gv[kE], gt[kT];
+#pragma unroll
+                for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
+#pragma unroll
+                for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg_hint(gk + tr[e], pl) : XT(0);
+                i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
+                d_nn = load_col(a.desc, i_nn, pf);
+                XT acc = slot_dot(gv, gt);
+                for (int cs = kE + kT; cs < valid; cs += kE) {
+                    Chunk<kE, XT> tc;
+                    ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
+                    acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
+                }
+                // At x_i = 0 the LASSO step is 0 when |grad| <= lambda: tested in FP32
+                // against lambda rounded down (FP32 and BF16 forms) or on the FP64
+                // bit patterns as integers (FP64 form), with no FP64 instruction
+                bool zero_step = false;
+                if constexpr (GM == 0) {
+                    if constexpr (sizeof(XT) == 4)
+                        zero_step = a.problem == 0 && is_zero_bits(xi) && fabsf(float(acc)) <= lamf;
+                    else
+                        zero_step = a.problem == 0 && is_zero_bits(xi) && abs_le_bits(double(acc), a.lambda);
+                }
+                if (!zero_step) take_step(acc);
+            }
+            cnt.gathered += (unsigned long long)valid;
+        }
+
+        // ---------------- scatter into the other buffer (g_{k-1} -> g_{k+1})
+        // No barrier is needed before it: every gather of iteration k reads g_k,
+        // which nobody writes during iteration k.  The other buffer holds g_{k-1}
+        // and receives the steps of iterations k-1 and k.  The previous column's
+        // entries were replaced in the slot: it is scattered from memory.
+        if (own && !is_zero_bits(h_prev)) mem_scatter<VT, XT>(a, d_prev, h_prev, gn, pf, pl);
+        if (own && !is_zero_bits(h)) slot_scatter1<VT, XT>(a, my, d_cur, h, gn, pf, pl);
+        h_prev = h;
+        d_prev = d_cur;
+
+        // ---------------- the only grid barrier of the iteration: g_{k+1} complete
+        // Split: the release-arrive publishes x and the scatter; the bulk copies of
+        // the next columns (reads of A only, nothing to publish) are issued after
+        // it, into the slot this thread has finished reading, and overlap the wait.
+        const unsigned long long target = (unsigned long long)(it + 1) * gridDim.x;
+        grid_arrive(a.bar);
+        fence_proxy_async_shared();
+        fill(d_nxt, i_nxt, own);
+        if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) {
+            wait_buf(it + 1);   // the copies just issued land before the block leaves
+            return;
+        }
+        i_cur = i_nxt;
+        d_cur = d_nxt;
+        i_nxt = i_nn;
+        d_nxt = d_nn;
+    }
+    // Both buffers equal again: the last iteration's steps go into the buffer
+    // that holds g_{k0+iters-1}.
+    if (iters > 0 && own && !is_zero_bits(h_prev))
+        mem_scatter<VT, XT>(a, d_prev, h_prev, gbuf(k0 + iters - 1), pf, pl);
+    // the last fill (the entries of i_{k0+iters}) lands before the block leaves
+    wait_buf(iters);
+    // S_{k0+iters} for the caller (the sample of the next launch).
+    if (own) sample_buf(a, k0 + iters)[j0] = i_cur;
+    flush_counters(cnt, a.counters);
+}
+
 // ---------------------------------------------------------------------------
 // Pipelined kernel for tau larger than the grid: thread t of T owns positions
 // t, t + T, ..., t + (R-1) T of every iteration ("rounds").  Its work items
@@ -1591,12 +1934,25 @@ int Kernels<VT, XT>::pipe_max_blocks(int threads)
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    const size_t bytes = pipe_smem_bytes<VT>(threads);
+    // FP64: the wide-slot kernel (one slot per thread), else the double-buffered one;
     // the same grid serves every variant (gradient maps, zero-step certificate):
     // the smallest co-resident grid of them
-    const void *fns[3] = {(const void *)k_fused_pipe<VT, XT, 0, false>, (const void *)k_fused_pipe<VT, XT, 1, false>,
-                          (const void *)k_fused_pipe<VT, XT, 0, true>};
-    const int nf = sizeof(XT) == 8 ? 3 : 2;
+    size_t bytes;
+    const void *fns[3];
+    int nf;
+    if constexpr (sizeof(XT) == 8) {
+        bytes = pipe_smem_bytes1<VT>(threads);
+        fns[0] = (const void *)k_fused_pipe_wide<VT, XT, 0, false>;
+        fns[1] = (const void *)k_fused_pipe_wide<VT, XT, 1, false>;
+        fns[2] = (const void *)k_fused_pipe_wide<VT, XT, 0, true>;
+        nf = 3;
+    } else {
+        bytes = pipe_smem_bytes<VT>(threads);
+        fns[0] = (const void *)k_fused_pipe<VT, XT, 0, false>;
+        fns[1] = (const void *)k_fused_pipe<VT, XT, 1, false>;
+        fns[2] = nullptr;
+        nf = 2;
+    }
     int best = -1;
     for (int f = 0; f < nf; ++f) {
         if (cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess)
@@ -1614,12 +1970,20 @@ cudaError_t Kernels<VT, XT>::fused_pipe(const IterArgs<VT, XT> &a, const FusedSh
     if (iters <= 0 || a.tau <= 0) return cudaSuccess;
     IterArgs<VT, XT> args = a;
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
-    // the certificate applies to the FP64 form of LASSO (the FP32 forms test |grad| <= lambda exactly anyway)
-    const void *fn = a.problem == 2 ? (const void *)k_fused_pipe<VT, XT, 1, false>
-                     : (sizeof(XT) == 8 && zero_cert && a.problem == 0) ? (const void *)k_fused_pipe<VT, XT, 0, true>
-                                                                       : (const void *)k_fused_pipe<VT, XT, 0, false>;
-    return cudaLaunchCooperativeKernel(fn, dim3(unsigned(sh.blocks)), dim3(unsigned(sh.threads)), params,
-                                       pipe_smem_bytes<VT>(sh.threads), st);
+    // the certificate applies to the FP64 form of LASSO (the FP32 forms test |grad| <= lambda exactly anyway);
+    // FP64 runs the wide-slot kernel
+    const void *fn;
+    size_t bytes;
+    if constexpr (sizeof(XT) == 8) {
+        fn = a.problem == 2 ? (const void *)k_fused_pipe_wide<VT, XT, 1, false>
+             : (zero_cert && a.problem == 0) ? (const void *)k_fused_pipe_wide<VT, XT, 0, true>
+                                             : (const void *)k_fused_pipe_wide<VT, XT, 0, false>;
+        bytes = pipe_smem_bytes1<VT>(sh.threads);
+    } else {
+        fn = a.problem == 2 ? (const void *)k_fused_pipe<VT, XT, 1, false> : (const void *)k_fused_pipe<VT, XT, 0, false>;
+        bytes = pipe_smem_bytes<VT>(sh.threads);
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(unsigned(sh.blocks)), dim3(unsigned(sh.threads)), params, bytes, st);
 }
 
 template <typename VT, typename XT>
