@@ -1071,15 +1071,14 @@ __device__ __forceinline__ void slot_scatter1(const IterArgs<VT, XT> &a, const u
     }
 }
 
-// The pipelined kernel's FP64 form ("wide" slots): one slot per thread holds the
-// column's first kE + kE/2 entries (the head by one bulk copy, the next kE/2 by
-// two more for a longer column), so the gathers of entries kE .. kE + kE/2 - 1
-// need no dependent load; the slot is refilled after the grid barrier's arrive
-// (its scatter done), and the previous iteration's step is scattered from
-// memory.  In FP64, whose phase before the scatter is the longest, this cut the
-// iteration at the bench workload from 18.6 to 17.0 us; the FP32 and BF16 forms,
-// where the block's wait for every thread's copies then costs more than the tail
-// loads did, keep the double-buffered kernel above.
+// The pipelined kernel's FP64 and FP32 forms ("wide" slots): one slot per thread
+// holds the column's first kE + kE/2 entries (one bulk copy of the column's head,
+// or two to four from the CSC arrays without heads), so the gathers of entries
+// kE .. kE + kE/2 - 1 need no dependent load; the slot is refilled after the grid
+// barrier's arrive (its scatter done), and the previous iteration's step is
+// scattered from memory.  At the bench workload this cut the FP64 iteration from
+// 18.6 to 16.5 us and the FP32 one from 12.7 to 12.4 us; the BF16 form (12.3 us
+// double-buffered, 12.5 wide) keeps the double-buffered kernel above.
 template <typename VT, typename XT, int GM = 0, bool ZC = false>
 __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe_wide(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
 {
@@ -1116,16 +1115,19 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe_wide(const Iter
             const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
             const uint32_t e2 = pc > kE ? uint32_t(pc - kE < kT ? pc - kE : kT) : 0u;
             const uint32_t br2 = e2 * 4u, bv2 = e2 * uint32_t(sizeof(VT));
-            mbar_arrive_expect_tx(mbar, (a.head ? 64u + bv : br + bv) + br2 + bv2);
             if (a.head) {
-                bulk_copy_g2s(my, a.head + int64_t(ci) * head_stride<VT>(), 64u + bv, mbar, pf);
+                // the head's layout is the slot's: one copy, up to the last tail value needed
+                const uint32_t bytes = e2 > 0 ? uint32_t(TO + 4 * kT) + bv2 : 64u + bv;
+                mbar_arrive_expect_tx(mbar, bytes);
+                bulk_copy_g2s(my, a.head + int64_t(ci) * head_stride<VT>(), bytes, mbar, pf);
             } else {
+                mbar_arrive_expect_tx(mbar, br + bv + br2 + bv2);
                 bulk_copy_g2s(my, a.prow + d.pbeg, br, mbar, pf);
                 bulk_copy_g2s(my + 64, a.pval + d.pbeg, bv, mbar, pf);
-            }
-            if (e2 > 0) {
-                bulk_copy_g2s(my + TO, a.prow + d.pbeg + kE, br2, mbar, pf);
-                bulk_copy_g2s(my + TO + 4 * kT, a.pval + d.pbeg + kE, bv2, mbar, pf);
+                if (e2 > 0) {
+                    bulk_copy_g2s(my + TO, a.prow + d.pbeg + kE, br2, mbar, pf);
+                    bulk_copy_g2s(my + TO + 4 * kT, a.pval + d.pbeg + kE, bv2, mbar, pf);
+                }
             }
         } else {
             mbar_arrive(mbar);
@@ -1646,15 +1648,19 @@ __global__ void __launch_bounds__(kBlock) k_build_heads(const ColDesc<XT> *__res
                                                         const int32_t *__restrict__ prow, const VT *__restrict__ pval,
                                                         int64_t n, unsigned char *__restrict__ head)
 {
+    constexpr int EH = kE + kE / 2;   // entries of a head
     const int64_t stride = int64_t(gridDim.x) * kBlock;
-    for (int64_t t = int64_t(blockIdx.x) * kBlock + threadIdx.x; t < n * kE; t += stride) {
-        const int64_t i = t / kE;
-        const int e = int(t % kE);
+    for (int64_t t = int64_t(blockIdx.x) * kBlock + threadIdx.x; t < n * EH; t += stride) {
+        const int64_t i = t / EH;
+        const int e = int(t % EH);
         const Col<XT> c = load_col(desc, int32_t(i));
-        unsigned char *h = head + i * head_stride<VT>();
+        // entries 0 .. kE-1: rows at 0, values at 4 kE; entries kE .. EH-1: rows, then values, after them
+        unsigned char *h = head + i * head_stride<VT>() + (e < kE ? 0 : 4 * kE + kE * int(sizeof(VT)));
+        const int q = e < kE ? e : e - kE;
+        const int voff = e < kE ? 4 * kE : 4 * (kE / 2);
         const bool in = e < c.cnt;
-        reinterpret_cast<int32_t *>(h)[e] = in ? prow[c.pbeg + e] : 0;
-        reinterpret_cast<VT *>(h + 4 * kE)[e] = in ? pval[c.pbeg + e] : VT{};
+        reinterpret_cast<int32_t *>(h)[q] = in ? prow[c.pbeg + e] : 0;
+        reinterpret_cast<VT *>(h + voff)[q] = in ? pval[c.pbeg + e] : VT{};
     }
 }
 
@@ -1934,18 +1940,18 @@ int Kernels<VT, XT>::pipe_max_blocks(int threads)
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    // FP64: the wide-slot kernel (one slot per thread), else the double-buffered one;
-    // the same grid serves every variant (gradient maps, zero-step certificate):
-    // the smallest co-resident grid of them
+    // FP64 and FP32 values: the wide-slot kernel (one slot per thread), BF16 the
+    // double-buffered one; the same grid serves every variant (gradient maps,
+    // zero-step certificate): the smallest co-resident grid of them
     size_t bytes;
     const void *fns[3];
     int nf;
-    if constexpr (sizeof(XT) == 8) {
+    if constexpr (sizeof(VT) >= 4) {
         bytes = pipe_smem_bytes1<VT>(threads);
         fns[0] = (const void *)k_fused_pipe_wide<VT, XT, 0, false>;
         fns[1] = (const void *)k_fused_pipe_wide<VT, XT, 1, false>;
         fns[2] = (const void *)k_fused_pipe_wide<VT, XT, 0, true>;
-        nf = 3;
+        nf = sizeof(XT) == 8 ? 3 : 2;
     } else {
         bytes = pipe_smem_bytes<VT>(threads);
         fns[0] = (const void *)k_fused_pipe<VT, XT, 0, false>;
@@ -1971,13 +1977,13 @@ cudaError_t Kernels<VT, XT>::fused_pipe(const IterArgs<VT, XT> &a, const FusedSh
     IterArgs<VT, XT> args = a;
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
     // the certificate applies to the FP64 form of LASSO (the FP32 forms test |grad| <= lambda exactly anyway);
-    // FP64 runs the wide-slot kernel
+    // FP64 and FP32 values run the wide-slot kernel
     const void *fn;
     size_t bytes;
-    if constexpr (sizeof(XT) == 8) {
+    if constexpr (sizeof(VT) >= 4) {
         fn = a.problem == 2 ? (const void *)k_fused_pipe_wide<VT, XT, 1, false>
-             : (zero_cert && a.problem == 0) ? (const void *)k_fused_pipe_wide<VT, XT, 0, true>
-                                             : (const void *)k_fused_pipe_wide<VT, XT, 0, false>;
+             : (sizeof(XT) == 8 && zero_cert && a.problem == 0) ? (const void *)k_fused_pipe_wide<VT, XT, 0, true>
+                                                               : (const void *)k_fused_pipe_wide<VT, XT, 0, false>;
         bytes = pipe_smem_bytes1<VT>(sh.threads);
     } else {
         fn = a.problem == 2 ? (const void *)k_fused_pipe<VT, XT, 1, false> : (const void *)k_fused_pipe<VT, XT, 0, false>;
@@ -2020,7 +2026,8 @@ cudaError_t Kernels<VT, XT>::build_heads(const ColDesc<XT> *desc, const int32_t 
                                          unsigned char *head, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_build_heads<VT, XT><<<blocks_for_threads(n * kE, 152 * 64), kBlock, 0, st>>>(desc, prow, pval, n, head);
+    k_build_heads<VT, XT><<<blocks_for_threads(n * (kE + kE / 2), 152 * 64), kBlock, 0, st>>>(desc, prow, pval, n,
+                                                                                              head);
     return cudaGetLastError();
 }
 
