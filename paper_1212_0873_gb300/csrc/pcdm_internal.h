@@ -104,13 +104,21 @@ struct IterArgs {
     double kappa;
 };
 
+// Entries of one column head: kLaneRun (the first chunk), and for the 4- and
+// 8-byte values, whose pipelined kernel has wide slots, kLaneRun/2 more.
+template <typename VT>
+__host__ __device__ constexpr int head_entries()
+{
+    return sizeof(VT) >= 4 ? kLaneRun + kLaneRun / 2 : kLaneRun;
+}
+
 // Bytes of one column head: kLaneRun row indices, then kLaneRun values (the first
-// chunk), then the next kLaneRun/2 row indices and values (read by the FP64
-// pipelined kernel's wide slots, with the rest in one bulk copy).
+// chunk), then (wide heads) the next kLaneRun/2 row indices and values, so that
+// the wide slot's 24 entries come in one bulk copy.
 template <typename VT>
 __host__ __device__ constexpr int64_t head_stride()
 {
-    return 4 * kLaneRun + kLaneRun * int64_t(sizeof(VT)) + 2 * kLaneRun + (kLaneRun / 2) * int64_t(sizeof(VT));
+    return int64_t(head_entries<VT>()) * (4 + int64_t(sizeof(VT)));
 }
 
 // Launch shape of the fused kernel.
@@ -158,8 +166,8 @@ struct Kernels {
     static cudaError_t setup_cols(const int64_t *col_ptr, const int32_t *row_idx, const VT *val, int64_t m,
                                   int64_t n, double *L, int *rowcnt, int *flags, cudaStream_t st);
     // Padded layout: copy the columns into prow/pval at pbeg (entries) and write desc.
-    // head + i * head_stride<VT>(): the first chunk of column i (rows, then values), then its next
-    // kLaneRun/2 entries (rows, then values), zero-padded.
+    // head + i * head_stride<VT>(): the first chunk of column i (rows, then values), then (wide
+    // heads) its next kLaneRun/2 entries (rows, then values), zero-padded.
     static cudaError_t build_heads(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, int64_t n,
                                    unsigned char *head, cudaStream_t st);
     static cudaError_t build_layout(const int64_t *col_ptr, const int32_t *row_idx, const VT *val,

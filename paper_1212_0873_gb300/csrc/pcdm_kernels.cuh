@@ -1089,6 +1089,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe_wide(const Iter
     constexpr int TO = pipe_tail_off<VT>();
     constexpr int G = pad_granule<VT>();
     constexpr int kT = kE / 2;   // entries [kE, kE + kT) sit in the slot as well
+    static_assert(head_entries<VT>() == kE + kT, "the wide slot is filled from a wide head");
     const int nt = blockDim.x, t = threadIdx.x;
     // Sampled position j belongs to block j mod gridDim.x, thread j / gridDim.x:
     // with one block per SM the positions spread over every SM even when tau
@@ -1648,7 +1649,7 @@ __global__ void __launch_bounds__(kBlock) k_build_heads(const ColDesc<XT> *__res
                                                         const int32_t *__restrict__ prow, const VT *__restrict__ pval,
                                                         int64_t n, unsigned char *__restrict__ head)
 {
-    constexpr int EH = kE + kE / 2;   // entries of a head
+    constexpr int EH = head_entries<VT>();
     const int64_t stride = int64_t(gridDim.x) * kBlock;
     for (int64_t t = int64_t(blockIdx.x) * kBlock + threadIdx.x; t < n * EH; t += stride) {
         const int64_t i = t / EH;
@@ -2026,8 +2027,8 @@ cudaError_t Kernels<VT, XT>::build_heads(const ColDesc<XT> *desc, const int32_t 
                                          unsigned char *head, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_build_heads<VT, XT><<<blocks_for_threads(n * (kE + kE / 2), 152 * 64), kBlock, 0, st>>>(desc, prow, pval, n,
-                                                                                              head);
+    k_build_heads<VT, XT><<<blocks_for_threads(n * head_entries<VT>(), 152 * 64), kBlock, 0, st>>>(desc, prow, pval,
+                                                                                                   n, head);
     return cudaGetLastError();
 }
 
