@@ -104,17 +104,27 @@ struct IterArgs {
     double kappa;
 };
 
+// Entries of a wide slot after its first chunk (the pipelined kernel's FP64 and
+// FP32 forms): 8 for FP64 (32 cost the FP64 pipe more predicated products than the
+// dependent loads they saved: 18.1 against 16.4 us per iteration at the bench
+// workload), 16 for FP32 (11.8 against 12.3 us).
+template <typename VT>
+__host__ __device__ constexpr int wide_tail()
+{
+    return sizeof(VT) == 4 ? kLaneRun : kLaneRun / 2;
+}
+
 // Entries of one column head: kLaneRun (the first chunk), and for the 4- and
-// 8-byte values, whose pipelined kernel has wide slots, kLaneRun/2 more.
+// 8-byte values, whose pipelined kernel has wide slots, wide_tail more.
 template <typename VT>
 __host__ __device__ constexpr int head_entries()
 {
-    return sizeof(VT) >= 4 ? kLaneRun + kLaneRun / 2 : kLaneRun;
+    return sizeof(VT) >= 4 ? kLaneRun + wide_tail<VT>() : kLaneRun;
 }
 
 // Bytes of one column head: kLaneRun row indices, then kLaneRun values (the first
-// chunk), then (wide heads) the next kLaneRun/2 row indices and values, so that
-// the wide slot's 24 entries come in one bulk copy.
+// chunk), then (wide heads) the next wide_tail row indices and values, so that
+// the wide slot's entries come in one bulk copy.
 template <typename VT>
 __host__ __device__ constexpr int64_t head_stride()
 {
@@ -167,7 +177,7 @@ struct Kernels {
                                   int64_t n, double *L, int *rowcnt, int *flags, cudaStream_t st);
     // Padded layout: copy the columns into prow/pval at pbeg (entries) and write desc.
     // head + i * head_stride<VT>(): the first chunk of column i (rows, then values), then (wide
-    // heads) its next kLaneRun/2 entries (rows, then values), zero-padded.
+    // heads) its next wide_tail entries (rows, then values), zero-padded.
     static cudaError_t build_heads(const ColDesc<XT> *desc, const int32_t *prow, const VT *pval, int64_t n,
                                    unsigned char *head, cudaStream_t st);
     static cudaError_t build_layout(const int64_t *col_ptr, const int32_t *row_idx, const VT *val,

@@ -988,7 +988,7 @@ __device__ __forceinline__ void mem_scatter(const IterArgs<VT, XT> &a, const Col
 }
 
 // Shared-memory slot of one thread of the pipelined kernel: the column's first
-// kE row indices and values (the head's layout), then its next kE/2 row indices
+// kE row indices and values (the head's layout), then its next wide_tail row indices
 // and values, padded to an odd number of 16-byte words (with it, the 128-bit
 // loads of 8 consecutive threads hit distinct banks).
 template <typename VT>
@@ -999,7 +999,7 @@ __host__ __device__ constexpr int pipe_tail_off()
 template <typename VT>
 __host__ __device__ constexpr int pipe_slot_raw()
 {
-    return pipe_tail_off<VT>() + 2 * kLaneRun + (kLaneRun / 2) * int(sizeof(VT));
+    return pipe_tail_off<VT>() + wide_tail<VT>() * (4 + int(sizeof(VT)));
 }
 template <typename VT>
 __host__ __device__ constexpr int pipe_slot_bytes1()
@@ -1012,9 +1012,9 @@ __host__ __device__ constexpr size_t pipe_smem_bytes1(int threads)
     return size_t(threads) * size_t(pipe_slot_bytes1<VT>()) + 16;
 }
 
-// Row indices and values of a slot: the first kE entries, then the next kE/2.
+// Row indices of a wide slot: the first kE entries, then the next wide_tail.
 template <typename VT, typename XT>
-__device__ __forceinline__ void slot_rows(const unsigned char *slot, int32_t (&row)[kE], int32_t (&tr)[kE / 2])
+__device__ __forceinline__ void slot_rows(const unsigned char *slot, int32_t (&row)[kE], int32_t (&tr)[wide_tail<VT>()])
 {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -1025,7 +1025,7 @@ __device__ __forceinline__ void slot_rows(const unsigned char *slot, int32_t (&r
         row[4 * q + 3] = int32_t(r4.w);
     }
 #pragma unroll
-    for (int q = 0; q < kE / 8; ++q) {
+    for (int q = 0; q < wide_tail<VT>() / 4; ++q) {
         const uint4 r4 = reinterpret_cast<const uint4 *>(slot + pipe_tail_off<VT>())[q];
         tr[4 * q + 0] = int32_t(r4.x);
         tr[4 * q + 1] = int32_t(r4.y);
@@ -1034,16 +1034,16 @@ __device__ __forceinline__ void slot_rows(const unsigned char *slot, int32_t (&r
     }
 }
 
-// Scatter of one column whose first kE + kE/2 entries sit in a slot (the rest
+// Scatter of one column whose first kE + wide_tail entries sit in a slot (the rest
 // from memory) into g: g_r += a_ri * h.
 template <typename VT, typename XT>
 __device__ __forceinline__ void slot_scatter1(const IterArgs<VT, XT> &a, const unsigned char *slot, const Col<XT> &d,
                                               XT h, XT *g, uint64_t pf, uint64_t pl)
 {
     constexpr int VW = pipe_value_words<VT>();
-    constexpr int VWT = VW / 2;
+    constexpr int kT = wide_tail<VT>();
+    constexpr int VWT = kT * int(sizeof(VT)) / 16;
     constexpr int EPW = 16 / int(sizeof(VT));
-    constexpr int kT = kE / 2;
     int32_t row[kE], tr[kT];
     slot_rows<VT, XT>(slot, row, tr);
 #pragma unroll
@@ -1072,23 +1072,24 @@ __device__ __forceinline__ void slot_scatter1(const IterArgs<VT, XT> &a, const u
 }
 
 // The pipelined kernel's FP64 and FP32 forms ("wide" slots): one slot per thread
-// holds the column's first kE + kE/2 entries (one bulk copy of the column's head,
-// or two to four from the CSC arrays without heads), so the gathers of entries
-// kE .. kE + kE/2 - 1 need no dependent load; the slot is refilled after the grid
+// holds the column's first kE + wide_tail entries (one bulk copy of the column's
+// head, or two to four from the CSC arrays without heads), so the gathers of
+// entries kE .. kE + wide_tail - 1 need no dependent load; the slot is refilled after the grid
 // barrier's arrive (its scatter done), and the previous iteration's step is
 // scattered from memory.  At the bench workload this cut the FP64 iteration from
-// 18.6 to 16.5 us and the FP32 one from 12.7 to 12.4 us; the BF16 form (12.3 us
-// double-buffered, 12.5 wide) keeps the double-buffered kernel above.
+// 18.6 to 16.4 us (24 entries) and the FP32 one from 12.7 to 11.8 us (32 entries);
+// the BF16 form (12.3 us double-buffered, 12.5 wide) keeps the double-buffered
+// kernel above.
 template <typename VT, typename XT, int GM = 0, bool ZC = false>
 __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe_wide(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int VW = pipe_value_words<VT>();
-    constexpr int VWT = VW / 2;
     constexpr int SB = pipe_slot_bytes1<VT>();
     constexpr int TO = pipe_tail_off<VT>();
     constexpr int G = pad_granule<VT>();
-    constexpr int kT = kE / 2;   // entries [kE, kE + kT) sit in the slot as well
+    constexpr int kT = wide_tail<VT>();   // entries [kE, kE + kT) sit in the slot as well
+    constexpr int VWT = kT * int(sizeof(VT)) / 16;
     static_assert(head_entries<VT>() == kE + kT, "the wide slot is filled from a wide head");
     const int nt = blockDim.x, t = threadIdx.x;
     // Sampled position j belongs to block j mod gridDim.x, thread j / gridDim.x:
@@ -1108,7 +1109,7 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe_wide(const Iter
     // This thread's share of filling the slots: arrive on the mbarrier and, for a
     // non-empty column, bulk-copy its first kE entries (one copy from the column's
     // head when the heads exist, else rows and values) and, for a longer column,
-    // its next kE/2 entries (rows and values).
+    // its next wide_tail entries (rows and values).
     auto fill = [&](const Col<XT> &d, int32_t ci, bool mine) {
         if (mine && d.cnt > 0) {
             const int64_t pc = (int64_t(d.cnt) + G - 1) / G * G;
@@ -1658,7 +1659,7 @@ __global__ void __launch_bounds__(kBlock) k_build_heads(const ColDesc<XT> *__res
         // entries 0 .. kE-1: rows at 0, values at 4 kE; entries kE .. EH-1: rows, then values, after them
         unsigned char *h = head + i * head_stride<VT>() + (e < kE ? 0 : 4 * kE + kE * int(sizeof(VT)));
         const int q = e < kE ? e : e - kE;
-        const int voff = e < kE ? 4 * kE : 4 * (kE / 2);
+        const int voff = e < kE ? 4 * kE : 4 * wide_tail<VT>();
         const bool in = e < c.cnt;
         reinterpret_cast<int32_t *>(h)[q] = in ? prow[c.pbeg + e] : 0;
         reinterpret_cast<VT *>(h + voff)[q] = in ? pval[c.pbeg + e] : VT{};
