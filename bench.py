@@ -694,9 +694,7 @@ def kernel_name(a, tuning):
         return "k_fused_stream (persistent PCDM1 iterations, columns streamed by TMA)"
     if tuning and tuning["kernel"] == 5:
         return "k_fused_warp (persistent PCDM1 iterations, a warp per column)"
-    if a.dtype in ("f64", "f32"):
-        return "k_fused_pipe_wide (persistent PCDM1 iterations, pipelined, wide slots)"
-    return "k_fused_pipe (persistent PCDM1 iterations)"
+    return "k_fused_pipe_wide (persistent PCDM1 iterations, pipelined, wide slots)"
 
 
 def kernel_roofline(a, st, tuning, dtype):

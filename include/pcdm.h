@@ -309,11 +309,13 @@ typedef struct {
                                    3 pipelined rounds, 4 streaming, 5 warp-cooperative */
     int32_t lanes_per_col;
     int32_t threads_per_block;  /* pipelined, rounds, streaming and warp-cooperative kernels */
-    int32_t heads;              /* pipelined kernels: 1 = fetch each sampled column's first chunk
-                                   (16 row indices, then 16 values) with one bulk copy from a
-                                   per-column head array, n * (64 + 16 sizeof(value)) bytes built
-                                   on first use when free device memory holds four times that;
-                                   0 = two copies from the padded CSC arrays */
+    int32_t heads;              /* pipelined kernels: 1 = fetch each sampled column's first E
+                                   entries (16 row indices, 16 values, then E - 16 row indices
+                                   and as many values) with one bulk copy from a per-column
+                                   head array, n * E * (4 + sizeof(value)) bytes (E = 24 for
+                                   FP64 values, 32 for FP32 and BF16) built on first use when
+                                   free device memory holds four times that; 0 = two to four
+                                   copies from the padded CSC arrays */
     int32_t zero_cert;          /* pipelined and warp-cooperative kernels, FP64 form, LASSO:
                                    1 = before the FP64 sum
                                    a_i^T g, bound it in FP32 from the high words of the operands

@@ -104,22 +104,22 @@ struct IterArgs {
     double kappa;
 };
 
-// Entries of a wide slot after its first chunk (the pipelined kernel's FP64 and
-// FP32 forms): 8 for FP64 (32 cost the FP64 pipe more predicated products than the
-// dependent loads they saved: 18.1 against 16.4 us per iteration at the bench
-// workload), 16 for FP32 (11.8 against 12.3 us).
+// Entries of a wide slot after its first chunk (the pipelined kernel): 8 for
+// FP64 (32 cost the FP64 pipe more predicated products than the dependent loads
+// they saved: 18.1 against 16.4 us per iteration at the bench workload), 16 for
+// FP32 (11.8 against 12.3 us) and BF16 values.
 template <typename VT>
 __host__ __device__ constexpr int wide_tail()
 {
-    return sizeof(VT) == 4 ? kLaneRun : kLaneRun / 2;
+    return sizeof(VT) == 8 ? kLaneRun / 2 : kLaneRun;
 }
 
-// Entries of one column head: kLaneRun (the first chunk), and for the 4- and
-// 8-byte values, whose pipelined kernel has wide slots, wide_tail more.
+// Entries of one column head: kLaneRun (the first chunk), then wide_tail more,
+// the pipelined kernel's wide slot.
 template <typename VT>
 __host__ __device__ constexpr int head_entries()
 {
-    return sizeof(VT) >= 4 ? kLaneRun + wide_tail<VT>() : kLaneRun;
+    return kLaneRun + wide_tail<VT>();
 }
 
 // Bytes of one column head: kLaneRun row indices, then kLaneRun values (the first

@@ -625,16 +625,16 @@ __global__ void __launch_bounds__(fused_max_block(W), 1) k_fused(const IterArgs<
 // the update stays Jacobi, and only the barrier that publishes g_{k+1} remains.
 // Both buffers hold the same residual at every launch boundary.
 // Thread j keeps i_k and i_{k+1} with their descriptors in registers; the first
-// kE entries of column i_k sit in the thread's slot of shared-memory buffer
-// (it & 1), brought in by TMA bulk copies during the previous iteration
-// (completion on an mbarrier).  Per iteration k:
-//   gather   the gathers of g_k at the chunk's rows (and the start of the
-//            column's tail) are issued; the sample i_{k+2} is drawn (integer
-//            work) while they are in flight and its descriptor load is issued;
-//            then gradient, step, x;
-//   scatter  steps of k-1 and k into the other buffer;
-//   barrier  release-arrive; then TMA copies of the first chunk of column i_{k+1}
-//            into the other slot; then wait
+// entries of column i_k sit in the thread's shared-memory slot, brought in by a
+// TMA bulk copy issued during the previous iteration (completion on an
+// mbarrier).  Per iteration k (k_fused_pipe_wide, after the helpers below):
+//   gather   the gathers of g_k at the slot's rows are issued; the sample
+//            i_{k+2} is drawn (integer work) while they are in flight and its
+//            descriptor load is issued; then gradient, step, x;
+//   scatter  the step of k-1 (from memory) and of k (from the slot) into the
+//            other buffer;
+//   barrier  release-arrive; then the bulk copy of column i_{k+1}'s first
+//            entries into the slot; then wait
 // On GB300 the scattered gathers saturate each SM's load/store pipe, so the
 // bulk copies run on the TMA engine and the sampling is integer work only.
 // Values of one 16-byte word of a shared chunk (16 / sizeof(VT) entries).
@@ -709,270 +709,6 @@ __device__ __forceinline__ void slot_scatter(const IterArgs<VT, XT> &a, const un
         ld_chunk_hint<kE>(t, a.prow, a.pval, d.pbeg + cs, pf);
         chunk_scatter_hint<kE>(t, g, h, d.cnt - cs, pl);
     }
-}
-
-template <typename VT, typename XT, int GM = 0, bool ZC = false>
-__global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int VW = pipe_value_words<VT>();
-    constexpr int SB = pipe_slot_bytes<VT>();
-    constexpr int G = pad_granule<VT>();
-    const int nt = blockDim.x, t = threadIdx.x;
-    // Sampled position j belongs to block j mod gridDim.x, thread j / gridDim.x:
-    // with one block per SM the positions spread over every SM even when tau
-    // does not fill the last block.
-    const int64_t j0 = int64_t(t) * gridDim.x + blockIdx.x;
-    const bool own = j0 < a.tau;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + size_t(2) * nt * SB);
-    Counters cnt;
-    const uint64_t pf = l2_evict_first();   // A, descriptors, x: touched once per iteration
-    const uint64_t pl = l2_evict_last();    // the residual buffers: gathered at random rows
-    const float lamf = __double2float_rd(a.lambda);   // the largest float <= lambda (ZeroCert)
-    constexpr bool CERT = sizeof(XT) == 8 && GM == 0 && ZC;   // the FP64 form tries the FP32 certificate
-
-    auto slot = [&](int b) { return smem + (size_t(b) * nt + t) * SB; };
-    // the residual buffer that holds g_k at iteration k
-    auto gbuf = [&](int64_t kk) { return (kk & 1) ? a.g2 : a.g; };
-    // This thread's share of filling buffer b: arrive on mbar[b] and, for a
-    // non-empty column, bulk-copy its first chunk (rows, then values): one copy
-    // from the column's head when the heads exist, else two.
-    auto fill = [&](int b, const Col<XT> &d, int32_t ci, bool mine) {
-        if (mine && d.cnt > 0) {
-            const int64_t pc = (int64_t(d.cnt) + G - 1) / G * G;
-            const uint32_t e = uint32_t(pc < kE ? pc : kE);
-            const uint32_t br = e * 4u, bv = e * uint32_t(sizeof(VT));
-            if (a.head) {
-                mbar_arrive_expect_tx(&mbar[b], 64u + bv);
-                bulk_copy_g2s(slot(b), a.head + int64_t(ci) * head_stride<VT>(), 64u + bv, &mbar[b], pf);
-            } else {
-                mbar_arrive_expect_tx(&mbar[b], br + bv);
-                bulk_copy_g2s(slot(b), a.prow + d.pbeg, br, &mbar[b], pf);
-                bulk_copy_g2s(slot(b) + 64, a.pval + d.pbeg, bv, &mbar[b], pf);
-            }
-        } else {
-            mbar_arrive(&mbar[b]);
-        }
-    };
-    // The chunks of iteration it sit in buffer it & 1, whose (it >> 1)-th
-    // completion that is: its phase parity is (it >> 1) & 1.
-    auto wait_buf = [&](int64_t it) {
-        return mbar_wait_bounded(&mbar[it & 1], uint32_t(it >> 1) & 1u, a.status, a.timeout_ns);
-    };
-
-    if (t == 0) {
-        mbar_init(&mbar[0], uint32_t(nt));
-        mbar_init(&mbar[1], uint32_t(nt));
-        fence_mbarrier_init();
-    }
-    __syncthreads();
-
-    // Prologue: i_{k0} (drawn by the caller) and its chunk; i_{k0+1} and its descriptor.
-    int32_t i_cur = 0, i_nxt = 0;
-    Col<XT> d_cur, d_nxt, d_prev;
-    d_cur.pbeg = d_nxt.pbeg = d_prev.pbeg = 0;
-    d_cur.cnt = d_nxt.cnt = d_prev.cnt = 0;
-    d_cur.invL = d_nxt.invL = d_prev.invL = XT(0);
-    XT h_prev = XT(0);   // the step of the previous iteration's column (still owed to one buffer)
-    if (own) {
-        i_cur = ldcg(sample_buf(a, k0) + j0);
-        d_cur = load_col(a.desc, i_cur, pf);
-        i_nxt = sample_index(uint32_t(j0), make_sample_key(a.seed, k0 + 1, a.n));
-        d_nxt = load_col(a.desc, i_nxt, pf);
-    }
-    fill(0, d_cur, i_cur, own);
-
-    constexpr int kT = kE / 2;   // tail entries [kE, kE + kT) fetched early into registers
-    for (int64_t it = 0; it < iters; ++it) {
-        const int64_t k = k0 + it;
-        const int b = int(it & 1);
-        // the chunks of this iteration's columns (filled during the previous iteration)
-        if (!wait_buf(it)) return;
-        const unsigned char *my = slot(b);
-        const XT *gk = gbuf(k);
-        XT *gn = gbuf(k + 1);
-
-        // ---------------- gather, step, x update (reads g_k)
-        // The loads go first (x_i, the gathers of g at the chunk's rows, the start
-        // of the column's tail); the sample of k+2 (integer work only: no
-        // shuffles or shared-memory traffic, which would queue behind the loads)
-        // is drawn while they are in flight.
-        XT h = XT(0);
-        double xi = 0.0;
-        int32_t i_nn = 0;
-        Col<XT> d_nn = d_nxt;
-        const int valid = own ? d_cur.cnt : 0;
-        if (own) {
-            xi = ldcg_hint(a.x + i_cur, pf);
-            int32_t row[kE];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 r4 = reinterpret_cast<const uint4 *>(my)[q];
-                row[4 * q + 0] = int32_t(r4.x);
-                row[4 * q + 1] = int32_t(r4.y);
-                row[4 * q + 2] = int32_t(r4.z);
-                row[4 * q + 3] = int32_t(r4.w);
-            }
-            constexpr int EPW = 16 / int(sizeof(VT));
-            // the step from the gradient (FP64), x_i and the counters
-            auto take_step = [&](XT grad) {
-                const double xn =
-                    coord_step(a.problem, xi, double(grad), double(d_cur.invL), a.inv_beta, a.lambda, a.kappa);
-                const double h64 = xn - xi;
-                h = XT(h64);
-                if (h64 != 0.0) {   // most steps are zero: x_i unchanged
-                    st_hint(a.x + i_cur, xn, pf);
-                    cnt.nonzero += 1;
-                    cnt.scattered += (unsigned long long)valid;
-                }
-            };
-            // every other form: FP64 or FP32 values of g in registers
-            auto full_path = [&]() {
-                XT gv[kE];
-#pragma unroll
-                for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
-                Chunk<kT, XT> tl;
-                if (valid > kE) ld_chunk_hint<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE, pf);
-                i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
-                d_nn = load_col(a.desc, i_nn, pf);
-                XT gt[kT];
-#pragma unroll
-                for (int e = 0; e < kT; ++e) gt[e] = (kE + e < valid) ? ldcg_hint(gk + tl.row[e], pl) : XT(0);
-                XT acc = XT(0);
-#pragma unroll
-                for (int w = 0; w < VW; ++w) {
-                    XT vw[EPW];
-                    decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
-#pragma unroll
-                    for (int q = 0; q < EPW; ++q)
-                        if (w * EPW + q < valid) acc = fma(vw[q], grad_map<GM>(gv[w * EPW + q]), acc);
-                }
-#pragma unroll
-                for (int e = 0; e < kT; ++e)
-                    if (kE + e < valid) acc = fma(tl.val[e], grad_map<GM>(gt[e]), acc);
-                for (int cs = kE + kT; cs < valid; cs += kE) {
-                    Chunk<kE, XT> tc;
-                    ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
-                    acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
-                }
-                // At x_i = 0 the LASSO step is 0 when |grad| <= lambda: tested in FP32
-                // against lambda rounded down (FP32 and BF16 forms) or on the FP64
-                // bit patterns as integers (FP64 form), with no FP64 instruction
-                bool zero_step = false;
-                if constexpr (GM == 0) {
-                    if constexpr (sizeof(XT) == 4)
-                        zero_step = a.problem == 0 && is_zero_bits(xi) && fabsf(float(acc)) <= lamf;
-                    else
-                        zero_step = a.problem == 0 && is_zero_bits(xi) && abs_le_bits(double(acc), a.lambda);
-                }
-                if (!zero_step) take_step(acc);
-            };
-            if constexpr (CERT) {
-                // FP64 form with the FP32 certificate of a zero LASSO step
-                // (ZeroCert): the first chunk's gathers stay in registers as FP64,
-                // the tail's bring only the high words of g (FP64 values of both
-                // across the certificate would spill).  A lane the certificate
-                // does not cover (x_i != 0, |grad| near lambda, the SVM dual)
-                // reads the column's entries past the first chunk again, from L2.
-                XT gv[kE];
-#pragma unroll
-                for (int e = 0; e < kE; ++e) gv[e] = (e < valid) ? ldcg_hint(gk + row[e], pl) : XT(0);
-                Chunk<kT, XT> tl;
-                if (valid > kE) ld_chunk_hint<kT>(tl, a.prow, a.pval, d_cur.pbeg + kE, pf);
-                i_nn = sample_index(uint32_t(j0), make_sample_key(a.seed, k + 2, a.n));
-                d_nn = load_col(a.desc, i_nn, pf);
-                uint32_t gth[kT];
-#pragma unroll
-                for (int e = 0; e < kT; ++e) gth[e] = (kE + e < valid) ? ldcg_hi_hint(gk + tl.row[e], pl) : 0u;
-                bool zero_step = false;
-                if (a.problem == 0 && is_zero_bits(xi)) {
-                    ZeroCert zc;
-#pragma unroll
-                    for (int w = 0; w < VW; ++w) {
-                        const uint4 u = reinterpret_cast<const uint4 *>(my + 64)[w];
-                        if (2 * w < valid) zc.add(u.y, hi_word(gv[2 * w]));
-                        if (2 * w + 1 < valid) zc.add(u.w, hi_word(gv[2 * w + 1]));
-                    }
-#pragma unroll
-                    for (int e = 0; e < kT; ++e)
-                        if (kE + e < valid) zc.add(hi_word(tl.val[e]), gth[e]);
-                    for (int cs = kE + kT; cs < valid; cs += kT) {
-                        Chunk<kT, XT> tc;
-                        ld_chunk_hint<kT>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
-                        uint32_t gc[kT];
-#pragma unroll
-                        for (int e = 0; e < kT; ++e) gc[e] = (cs + e < valid) ? ldcg_hi_hint(gk + tc.row[e], pl) : 0u;
-#pragma unroll
-                        for (int e = 0; e < kT; ++e)
-                            if (cs + e < valid) zc.add(hi_word(tc.val[e]), gc[e]);
-                    }
-                    zero_step = zc.below(valid, lamf);
-                }
-                if (!zero_step) {
-                    // FP64 sum over the whole column: the first chunk from the
-                    // slot and registers, the rest from memory
-                    XT acc = XT(0);
-#pragma unroll
-                    for (int w = 0; w < VW; ++w) {
-                        XT vw[EPW];
-                        decode_word<VT, XT>(reinterpret_cast<const uint4 *>(my + 64)[w], vw);
-#pragma unroll
-                        for (int q = 0; q < EPW; ++q)
-                            if (w * EPW + q < valid) acc = fma(vw[q], gv[w * EPW + q], acc);
-                    }
-                    for (int cs = kE; cs < valid; cs += kE) {
-                        Chunk<kE, XT> tc;
-                        ld_chunk_hint<kE>(tc, a.prow, a.pval, d_cur.pbeg + cs, pf);
-                        acc += chunk_dot_hint<kE, XT, XT, GM>(tc, gk, valid - cs, pl);
-                    }
-                    // the exact test on the FP64 sum (the bound may not have decided it)
-                    if (!(a.problem == 0 && is_zero_bits(xi) && abs_le_bits(acc, a.lambda))) take_step(acc);
-                }
-            } else {
-                full_path();
-            }
-            cnt.gathered += (unsigned long long)valid;
-        }
-
-        // ---------------- scatter into the other buffer (g_{k-1} -> g_{k+1})
-        // No barrier is needed before it: every gather of iteration k reads g_k,
-        // which nobody writes during iteration k.  The other buffer holds g_{k-1}
-        // and receives the steps of iterations k-1 and k.  The previous column's
-        // chunk sits in slot b^1, so it is re-scattered before that slot is refilled.
-        if (own && !is_zero_bits(h_prev)) slot_scatter<VT, XT>(a, slot(b ^ 1), d_prev, h_prev, gn, pf, pl);
-        if (own && !is_zero_bits(h)) slot_scatter<VT, XT>(a, my, d_cur, h, gn, pf, pl);
-        h_prev = h;
-        d_prev = d_cur;
-
-        // ---------------- the only grid barrier of the iteration: g_{k+1} complete
-        // Split: the release-arrive publishes x and the scatter; the bulk copies of
-        // the next columns (reads of A only, nothing to publish) are issued after
-        // it, so the release does not wait for them, and they overlap the wait.
-        // (The column's tail is not prefetched into L2: the extra TMA issue cost
-        // on the last block to arrive outweighed the shorter tail loads.)
-        // the barrier counter is 0 at launch and gains gridDim.x per iteration
-        const unsigned long long target = (unsigned long long)(it + 1) * gridDim.x;
-        grid_arrive(a.bar);
-        fence_proxy_async_shared();
-        fill(b ^ 1, d_nxt, i_nxt, own);
-        if (!grid_wait(a.bar, target, a.status, a.timeout_ns)) {
-            wait_buf(it + 1);   // the copies just issued land before the block leaves
-            return;
-        }
-        i_cur = i_nxt;
-        d_cur = d_nxt;
-        i_nxt = i_nn;
-        d_nxt = d_nn;
-    }
-    // Both buffers equal again: the last iteration's steps (still in slot
-    // (iters-1)&1) go into the buffer that holds g_{k0+iters-1}.
-    if (iters > 0 && own && !is_zero_bits(h_prev))
-        slot_scatter<VT, XT>(a, slot(int((iters - 1) & 1)), d_prev, h_prev, gbuf(k0 + iters - 1), pf, pl);
-    // the last fill (the chunks of i_{k0+iters}) lands before the block leaves
-    wait_buf(iters);
-    // S_{k0+iters} for the caller (the sample of the next launch).
-    if (own) sample_buf(a, k0 + iters)[j0] = i_cur;
-    flush_counters(cnt, a.counters);
 }
 
 // Scatter of a whole column read from memory (A evict-first, g evict-last).
@@ -1071,15 +807,15 @@ __device__ __forceinline__ void slot_scatter1(const IterArgs<VT, XT> &a, const u
     }
 }
 
-// The pipelined kernel's FP64 and FP32 forms ("wide" slots): one slot per thread
-// holds the column's first kE + wide_tail entries (one bulk copy of the column's
-// head, or two to four from the CSC arrays without heads), so the gathers of
-// entries kE .. kE + wide_tail - 1 need no dependent load; the slot is refilled after the grid
-// barrier's arrive (its scatter done), and the previous iteration's step is
-// scattered from memory.  At the bench workload this cut the FP64 iteration from
-// 18.6 to 16.4 us (24 entries) and the FP32 one from 12.7 to 11.8 us (32 entries);
-// the BF16 form (12.3 us double-buffered, 12.5 wide) keeps the double-buffered
-// kernel above.
+// The pipelined kernel ("wide" slots): one slot per thread holds the column's
+// first kE + wide_tail entries (one bulk copy of the column's head, or two to
+// four from the CSC arrays without heads), so the gathers of entries
+// kE .. kE + wide_tail - 1 need no dependent load; the slot is refilled after
+// the grid barrier's arrive (its scatter done), and the previous iteration's
+// step is scattered from memory.  Against the double-buffered form it replaced
+// (two slots of kE entries per thread, the next kE / 2 entries loaded beside the
+// first gathers), at the bench workload: FP64 18.6 -> 16.4 us per iteration (24
+// entries), FP32 12.7 -> 11.8 us and BF16 12.2 -> 11.9 us (32 entries).
 template <typename VT, typename XT, int GM = 0, bool ZC = false>
 __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe_wide(const IterArgs<VT, XT> a, int64_t k0, int64_t iters)
 {
@@ -1338,8 +1074,8 @@ __global__ void __launch_bounds__(kPipeMaxBlock, 1) k_fused_pipe_wide(const Iter
 // Pipelined kernel for tau larger than the grid: thread t of T owns positions
 // t, t + T, ..., t + (R-1) T of every iteration ("rounds").  Its work items
 // (k, r) form one stream: while item q is computed, the first chunk of item
-// q+1 arrives in the other shared-memory slot (TMA bulk copies, as in
-// k_fused_pipe) and the sample of item q+2 is drawn.  The residual is double
+// q+1 arrives in the other shared-memory slot (TMA bulk copies into
+// two slots of kE entries per thread) and the sample of item q+2 is drawn.  The residual is double
 // buffered (iteration k gathers from buffer k & 1, scatters into the other),
 // so the only grid barrier is at the end of an iteration.  The step of
 // position j in iteration k-1, still owed to the other buffer, is kept in
@@ -1942,25 +1678,13 @@ int Kernels<VT, XT>::pipe_max_blocks(int threads)
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    // FP64 and FP32 values: the wide-slot kernel (one slot per thread), BF16 the
-    // double-buffered one; the same grid serves every variant (gradient maps,
-    // zero-step certificate): the smallest co-resident grid of them
-    size_t bytes;
-    const void *fns[3];
-    int nf;
-    if constexpr (sizeof(VT) >= 4) {
-        bytes = pipe_smem_bytes1<VT>(threads);
-        fns[0] = (const void *)k_fused_pipe_wide<VT, XT, 0, false>;
-        fns[1] = (const void *)k_fused_pipe_wide<VT, XT, 1, false>;
-        fns[2] = (const void *)k_fused_pipe_wide<VT, XT, 0, true>;
-        nf = sizeof(XT) == 8 ? 3 : 2;
-    } else {
-        bytes = pipe_smem_bytes<VT>(threads);
-        fns[0] = (const void *)k_fused_pipe<VT, XT, 0, false>;
-        fns[1] = (const void *)k_fused_pipe<VT, XT, 1, false>;
-        fns[2] = nullptr;
-        nf = 2;
-    }
+    // the same grid serves every variant (gradient maps, zero-step certificate):
+    // the smallest co-resident grid of them
+    const size_t bytes = pipe_smem_bytes1<VT>(threads);
+    const void *fns[3] = {(const void *)k_fused_pipe_wide<VT, XT, 0, false>,
+                          (const void *)k_fused_pipe_wide<VT, XT, 1, false>,
+                          (const void *)k_fused_pipe_wide<VT, XT, 0, true>};
+    const int nf = sizeof(XT) == 8 ? 3 : 2;
     int best = -1;
     for (int f = 0; f < nf; ++f) {
         if (cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)) != cudaSuccess)
@@ -1978,19 +1702,11 @@ cudaError_t Kernels<VT, XT>::fused_pipe(const IterArgs<VT, XT> &a, const FusedSh
     if (iters <= 0 || a.tau <= 0) return cudaSuccess;
     IterArgs<VT, XT> args = a;
     void *params[] = {(void *)&args, (void *)&k0, (void *)&iters};
-    // the certificate applies to the FP64 form of LASSO (the FP32 forms test |grad| <= lambda exactly anyway);
-    // FP64 and FP32 values run the wide-slot kernel
-    const void *fn;
-    size_t bytes;
-    if constexpr (sizeof(VT) >= 4) {
-        fn = a.problem == 2 ? (const void *)k_fused_pipe_wide<VT, XT, 1, false>
-             : (sizeof(XT) == 8 && zero_cert && a.problem == 0) ? (const void *)k_fused_pipe_wide<VT, XT, 0, true>
-                                                               : (const void *)k_fused_pipe_wide<VT, XT, 0, false>;
-        bytes = pipe_smem_bytes1<VT>(sh.threads);
-    } else {
-        fn = a.problem == 2 ? (const void *)k_fused_pipe<VT, XT, 1, false> : (const void *)k_fused_pipe<VT, XT, 0, false>;
-        bytes = pipe_smem_bytes<VT>(sh.threads);
-    }
+    // the certificate applies to the FP64 form of LASSO (the FP32 forms test |grad| <= lambda exactly anyway)
+    const void *fn = a.problem == 2 ? (const void *)k_fused_pipe_wide<VT, XT, 1, false>
+                     : (sizeof(XT) == 8 && zero_cert && a.problem == 0) ? (const void *)k_fused_pipe_wide<VT, XT, 0, true>
+                                                                       : (const void *)k_fused_pipe_wide<VT, XT, 0, false>;
+    const size_t bytes = pipe_smem_bytes1<VT>(sh.threads);
     return cudaLaunchCooperativeKernel(fn, dim3(unsigned(sh.blocks)), dim3(unsigned(sh.threads)), params, bytes, st);
 }
 
