@@ -1,7 +1,8 @@
 """Every iteration kernel (pipelined, fused with several lane widths, two-kernel,
 pipelined rounds, streaming, warp-cooperative; the pipelined ones with and without the
 column heads, the pipelined one also with and without the FP32 certificate of zero
-steps) selected by hand through pcdm_set_tuning follows the oracle; the rounds kernel
+steps) selected by hand through pcdm_set_tuning follows the oracle; the pipelined kernel
+also on columns shorter and longer than its shared-memory slot; the rounds kernel
 also with several positions per thread (tau beyond the grid), the warp-cooperative one
 also with many positions per warp, empty columns and columns of several items."""
 import numpy as np
@@ -82,6 +83,34 @@ def test_streaming_kernel_on_long_and_short_columns(val_dtype, tol, per_col, thr
     refresh = 0 if val_dtype == "f64" else 16
     with Lasso.from_instance(inst, refresh_every=refresh) as s:
         s.set_tuning(4, 1, threads, 1)
+        for upto in (1, 3, 30):
+            s.step(tau, upto - s.iteration, 6)
+            ref.run(tau, upto - ref.k, 6, refresh_every=refresh)
+            assert _rel(s.x(), ref.x) <= tol, upto
+            assert _rel(s.residual(), ref.g) <= tol, upto
+        ok, it, rel = s.solve(tau, 6, 1e-8 if val_dtype == "f64" else 1e-6, 100_000)
+        assert ok
+
+
+@pytest.mark.parametrize("val_dtype,tol", [("f64", 1e-10), ("f32", 1e-5), ("bf16", 1e-5)])
+@pytest.mark.parametrize("per_col,choice", [(1, (0, 1, 64, 1)), (17, (0, 1, 128, 0)), (25, (0, 1, 448, 1)),
+                                            (33, (0, 1, 448, 0)), (33, (0, 1, 128, 1, 1)), (150, (0, 1, 448, 1)),
+                                            (150, (0, 1, 64, 0, 1))])
+def test_pipelined_kernel_on_long_and_short_columns(val_dtype, tol, per_col, choice):
+    # the pipelined kernel's slot holds a column's first 24 (FP64) or 32 (FP32, BF16) entries;
+    # the rest is read from memory in chunks of 16, in the gradient and in both scatters (this
+    # iteration's from the slot, the previous one's from memory).  1 entry: a single padded
+    # entry; 17: one entry past the first chunk; 25: one past the FP64 slot; 33: one past the
+    # FP32 / BF16 slot; 150: several chunks past it, the last one ragged.  With and without
+    # the column heads (one bulk copy, or two to four from the CSC arrays), FP64 also with the
+    # FP32 certificate of zero steps; ragged tau over blocks of 64 to 448 threads
+    inst = instances.per_col_instance(20_000, 4_000, per_col, nnz_star=200, val_dtype=val_dtype, seed=1027)
+    A = oracle.Csc(inst.m, inst.n, inst.col_ptr, inst.row_idx, inst.val64)
+    ref = oracle.State(A, inst.b, inst.lam)
+    tau = min(2048 + 5, inst.n)
+    refresh = 0 if val_dtype == "f64" else 16
+    with Lasso.from_instance(inst, refresh_every=refresh) as s:
+        s.set_tuning(*choice)
         for upto in (1, 3, 30):
             s.step(tau, upto - s.iteration, 6)
             ref.run(tau, upto - ref.k, 6, refresh_every=refresh)
